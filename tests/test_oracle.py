@@ -1,0 +1,346 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each test checks it against a
+closed form, an exact identity, brute-force finite differences, or an
+independently derived forward-mode result, chosen so that a dropped term, a
+wrong sign or index, or a transposed operand in the oracle fails one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_12672_b300 import synthetic as syn
+
+
+def _ortho(n=64, W=None, H=None):
+    return syn.View(W or n, H or n, ortho=True, ortho_height=1.0)
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("sigma", [0.3, 1.3, 7.0])
+def test_beer_lambert_constant_density(sigma):
+    """Absorption-only, constant density: 1 - A = exp(-sigma N dt) (Sec. 3.1,
+    Beer-Lambert segment opacity). Ortho +z through a 64^3 box: L = 1 and
+    N = 126 at step 0.5 voxel."""
+    n = 64
+    sigma = float(np.float32(sigma))
+    vol = np.full((n, n, n), sigma, np.float32)
+    img, N, S = oracle.render(vol, None, "absorption", _ortho(), [0, 0, 2.0], 0.5)
+    assert (N == 126).all()
+    dt = float(np.float32(0.5 / 63))
+    np.testing.assert_allclose(img[:, 0], 1 - np.exp(-sigma * 126 * dt), rtol=1e-13)
+    np.testing.assert_allclose(S, sigma * 126 * dt, rtol=1e-13)
+
+
+def test_beer_lambert_perspective_every_pixel():
+    """Same closed form per pixel for a perspective camera: each ray's
+    opacity is 1 - exp(-sigma N_ray dt) whatever its length."""
+    n = 16
+    sigma = 2.0
+    vol = np.full((n, n, n), sigma, np.float32)
+    view = syn.View(23, 17)
+    img, N, S = oracle.render(vol, None, "absorption", view, [0.7, 0.9, 1.8], 0.37)
+    dt = float(np.float32(np.float32(0.37) / np.float32(15)))
+    assert N.max() > 0 and (N == 0).any()
+    np.testing.assert_allclose(img[:, 0], 1 - np.exp(-sigma * N * dt), rtol=1e-13, atol=1e-15)
+
+
+def test_constant_tf_closed_form():
+    """Emission-absorption with constant density and a constant TF row
+    (rgb, tau): the Riemann sum of Eq. 1 with premultiplied emission gives
+    C = rgb (1 - exp(-tau N dt)) and A = 1 - exp(-tau N dt)."""
+    n = 12
+    vol = np.full((n, n, n), 0.37)
+    row = np.array([0.2, 0.5, 0.9, 3.0])
+    tf = np.tile(row, (7, 1))
+    view = syn.View(9, 11)
+    img, N, _ = oracle.render(vol, tf, "emission_absorption", view, [1.1, -0.4, 1.6], 0.5)
+    dt = float(np.float32(np.float32(0.5) / np.float32(11)))
+    A = 1 - np.exp(-row[3] * N * dt)
+    np.testing.assert_allclose(img[:, 3], A, rtol=1e-13, atol=1e-15)
+    for ch in range(3):
+        np.testing.assert_allclose(img[:, ch], row[ch] * A, rtol=1e-13, atol=1e-15)
+
+
+def test_front_to_back_order_two_layers():
+    """Two slabs of different colour along the view axis: front-to-back
+    blending (Eq. blend-forward) makes the front slab's colour dominate:
+    C = c_f (1 - e_f) + e_f c_b (1 - e_b), with e = exp(-tau N dt) per slab."""
+    n = 9  # box [-0.5, 0.5], spacing 1/8; vertices z = 0.5 .. -0.5
+    vol = np.zeros((n, n, n), np.float32)
+    vol[5:, :, :] = 1.0      # z >= 1/8 (front half as seen from +z) -> density 1
+    vol[:5, :, :] = 0.0
+    # TF: density 0 -> blue, tau 2; density 1 -> red, tau 5 (R = 2)
+    tf = np.array([[0, 0, 1, 2.0], [1, 0, 0, 5.0]])
+    view = syn.View(1, 1, ortho=True, ortho_height=0.5)
+    img, N, _ = oracle.render(vol, tf, "emission_absorption", view, [0, 0, 3.0], 0.5)
+    dt = float(np.float32(np.float32(0.5) / np.float32(8)))
+    # samples at z = 0.5 - i dt, i = 0..N-1; density along z (trilinear in z)
+    z = 0.5 - np.arange(N[0]) * dt
+    g = (z + 0.5) * 8
+    d = np.clip(g - 4, 0, 1)             # 0 below vertex 4, ramps to 1 at vertex 5
+    col = np.outer(1 - d, tf[0]) + np.outer(d, tf[1])
+    a = 1 - np.exp(-dt * col[:, 3])
+    C = np.zeros(3)
+    T = 1.0
+    for i in range(N[0]):
+        C += T * a[i] * col[i, :3]
+        T *= 1 - a[i]
+    np.testing.assert_allclose(img[0, :3], C, rtol=1e-13)
+    np.testing.assert_allclose(img[0, 3], 1 - T, rtol=1e-13)
+    assert img[0, 0] > img[0, 2]  # front (red) dominates
+
+
+def test_linear_ramp_riemann_sum():
+    """Density linear in z, ortho camera along -z: the optical depth is the
+    Riemann sum dt * sum_i d(z_i) with z_i = 1/2 - i dt (samples start at the
+    entry face and advance by dt, Alg. 1)."""
+    n = 33
+    zs = np.linspace(-0.5, 0.5, n)
+    a, b = 1.7, 0.4
+    vol = np.broadcast_to((a * zs + b)[:, None, None], (n, n, n)).astype(np.float64)
+    img, N, S = oracle.render(vol, None, "absorption", _ortho(n, 5, 5), [0, 0, 4.0], 0.7)
+    dt = float(np.float32(np.float32(0.7) / np.float32(32)))
+    Nn = int(N[0])
+    expect = dt * (Nn * (a * 0.5 + b) - a * dt * Nn * (Nn - 1) / 2)
+    np.testing.assert_allclose(S, expect, rtol=1e-13)
+
+
+def test_trilinear_reproduces_multilinear_fields():
+    """Trilinear interpolation on vertices at -ext/2 + j h reproduces any
+    function of the form (a + b x)(c + d y)(e + f z) + linear exactly
+    (Sec. 3.1: density at grid vertices, trilinear in between)."""
+    rng = np.random.default_rng(0)
+    nx, ny, nz = 9, 6, 13
+    h = 1.0 / 12
+    xs = -0.5 * (nx - 1) * h + np.arange(nx) * h
+    ys = -0.5 * (ny - 1) * h + np.arange(ny) * h
+    zs = -0.5 * (nz - 1) * h + np.arange(nz) * h
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    f = lambda x, y, z: (0.3 + 1.1 * x) * (0.7 - 0.4 * y) * (1.2 + 0.9 * z) + 0.2 * x - 0.5 * z
+    vol = f(X, Y, Z)
+    pts = np.stack([rng.uniform(xs[0], xs[-1], 200), rng.uniform(ys[0], ys[-1], 200),
+                    rng.uniform(zs[0], zs[-1], 200)], axis=1)
+    d = oracle.interpolate(vol, pts)
+    np.testing.assert_allclose(d, f(pts[:, 0], pts[:, 1], pts[:, 2]), rtol=1e-12, atol=1e-13)
+    # a non-multilinear field is NOT reproduced (sanity of the test itself)
+    d2 = oracle.interpolate(X ** 2, pts)
+    assert np.abs(d2 - pts[:, 0] ** 2).max() > 1e-5
+
+
+def test_ray_geometry_ortho_and_perspective():
+    """Camera convention: eye on +z looks down -z with right = +x, up = +y,
+    pixel row 0 at the top; perspective rays follow the pinhole formula
+    w ~ (sx tan aspect, sy tan, -1)."""
+    view = syn.View(8, 6, ortho=True, ortho_height=1.0)
+    N, q, geo = oracle.rays((64, 64, 64), view, [0, 0, 2.0], 0.5)
+    for p in [0, 5, 17, 47]:
+        px, py = p % 8, p // 8
+        sx = (2 * px + 1) / 8 - 1
+        sy = 1 - (2 * py + 1) / 6
+        np.testing.assert_allclose(geo[p, 2:5], [sx * 0.5 * 8 / 6, sy * 0.5, 0.5], rtol=1e-6)
+        np.testing.assert_allclose(geo[p, 5:8], [0, 0, -1])
+        np.testing.assert_allclose(geo[p, 0], 1.5, rtol=1e-7)
+    t = math.tan(math.radians(30))
+    view = syn.View(7, 5, tan_half_fov_y=t)
+    N, q, geo = oracle.rays((16, 16, 16), view, [0, 0, 2.5], 0.5, fp32=False)
+    for p in range(35):
+        px, py = p % 7, p // 7
+        v = np.array([((2 * px + 1) / 7 - 1) * t * 7 / 5, (1 - (2 * py + 1) / 5) * t, -1.0])
+        np.testing.assert_allclose(geo[p, 5:8], v / np.linalg.norm(v), rtol=1e-13, atol=1e-15)
+    # centre pixel of an odd image points at the box centre from any eye
+    e = np.array([0.8, -1.3, 1.9])
+    N, q, geo = oracle.rays((16, 16, 16), view, e, 0.5, fp32=False)
+    np.testing.assert_allclose(geo[17, 5:8], -e / np.linalg.norm(e), rtol=1e-13)
+
+
+def test_orbit_camera_convention():
+    """Orbit parameters (yaw, pitch, distance): yaw = pitch = 0 puts the eye on
+    +z; pitch = pi/2 on +y; |eye| = distance (Sec. 5.1 longitude/latitude)."""
+    e = oracle.orbit_eye([[0, 0, 2.5], [0, math.pi / 2, 3.0], [math.pi / 2, 0, 1.0],
+                          [0.3, -0.2, 2.0]])
+    np.testing.assert_allclose(e[0], [0, 0, 2.5], atol=1e-15)
+    np.testing.assert_allclose(e[1], [0, 3.0, 0], atol=1e-15)
+    np.testing.assert_allclose(e[2], [1.0, 0, 0], atol=1e-15)
+    assert abs(np.linalg.norm(e[3]) - 2.0) < 1e-14
+    # finite differences of the orbit map against its adjoint
+    p = np.array([[0.3, -0.2, 2.0]])
+    g = np.array([[0.3, -1.2, 0.7]])
+    ga = oracle.orbit_eye_backward(p, g)[0]
+    for k in range(3):
+        h = 1e-6
+        dp = np.zeros_like(p)
+        dp[0, k] = h
+        fd = ((oracle.orbit_eye(p + dp) - oracle.orbit_eye(p - dp)) * g).sum() / (2 * h)
+        assert abs(fd - ga[k]) < 1e-8
+
+
+def test_image_orientation_right_is_plus_x():
+    """A blob at +x appears in the right half of the image of a camera on +z
+    (and at +y in the top rows)."""
+    n = 32
+    vol = syn.gaussian_blobs(n, 1, seed=0, centre=(30, 30), scale_to=32, sigma=(2, 3))
+    # the single blob is centred at voxel ~ (30,30,30) of 32: +x, +y, +z corner
+    img, _, _ = oracle.render(vol, None, "absorption", syn.View(16, 16, ortho=True), [0, 0, 2], 0.5)
+    A = img[:, 0].reshape(16, 16)
+    assert A[:, 8:].sum() > 10 * A[:, :8].sum()
+    assert A[:8, :].sum() > 10 * A[8:, :].sum()
+
+
+# ---------------------------------------------------------- exact identities
+def test_absorption_transpose_identity():
+    """Absorption-only: the optical depth S = P v is linear in the volume
+    (Sec. 5.3: a linear problem). The adjoint with dL/dA = w / T_N returns
+    P^T w, so <P r, w> = <r, grad> for any volume r (dot-product test)."""
+    rng = np.random.default_rng(7)
+    n = 10
+    v = rng.uniform(0, 2, (n, n, n))
+    r = rng.normal(size=(n, n, n))
+    view = syn.View(13, 11)
+    eye = [0.9, 0.5, 1.7]
+    imgv, Nv, Sv = oracle.render(v, None, "absorption", view, eye, 0.6)
+    _, _, Sr = oracle.render(r, None, "absorption", view, eye, 0.6)
+    w = rng.normal(size=Sv.shape)
+    T = 1 - imgv[:, 0]
+    g = oracle.backward(v, None, "absorption", view, eye, 0.6, (w / np.where(T > 0, T, 1))[:, None],
+                        want=("volume",))["volume"]
+    lhs = float(np.dot(Sr, w))
+    rhs = float(np.sum(r * g))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+def test_inversion_equals_tape():
+    """Sec. 4.4: reconstructing (A_i, C_i) with Eq. inv-blend-forward gives the
+    same gradients as storing them, up to rounding, for moderate opacity."""
+    rng = np.random.default_rng(3)
+    n = 10
+    v = rng.uniform(0, 1, (n, n, n))
+    tf = syn.random_tf(6, seed=9, tau_max=4.0).astype(np.float64)
+    view = syn.View(9, 8)
+    eye = [0.6, 0.4, 1.9]
+    G = rng.normal(size=(72, 4))
+    a = oracle.backward(v, tf, "emission_absorption", view, eye, 0.5, G, invert=False)
+    b = oracle.backward(v, tf, "emission_absorption", view, eye, 0.5, G, invert=True)
+    for k in ("volume", "tf", "eye"):
+        np.testing.assert_allclose(b[k], a[k], rtol=1e-9, atol=1e-12 * np.abs(a[k]).max())
+
+
+# ------------------------------------------------ brute-force finite differences
+def _loss(img, G):
+    return float(np.sum(img * G))
+
+
+def _fd_setup(model, ortho=False, eye=(0.9, 0.6, 1.7), seed=11, R=5):
+    rng = np.random.default_rng(seed)
+    n = 8
+    v = rng.uniform(0.05, 0.95, (n, n, n))
+    tf = None
+    if model == "emission_absorption":
+        tf = rng.uniform(0.1, 1.0, (R, 4))
+        tf[:, 3] *= 6.0
+    view = syn.View(6, 5, ortho=ortho, ortho_height=1.3) if ortho else syn.View(6, 5)
+    nc = 4 if model == "emission_absorption" else 1
+    G = rng.normal(size=(30, nc))
+    return v, tf, view, np.array(eye), G
+
+
+@pytest.mark.parametrize("model", ["absorption", "emission_absorption"])
+def test_fd_volume_every_voxel(model):
+    """Central differences of L = <G, image> w.r.t. every voxel of an 8^3
+    volume equal the adjoint gradient (Alg. 2; Eq. simpleadjoint)."""
+    v, tf, view, eye, G = _fd_setup(model)
+    g = oracle.backward(v, tf, model, view, eye, 0.5, G, fp32=False, want=("volume",))["volume"]
+    h = 1e-6
+    fd = np.zeros_like(v)
+    for idx in np.ndindex(v.shape):
+        vp = v.copy(); vp[idx] += h
+        vm = v.copy(); vm[idx] -= h
+        fd[idx] = (_loss(oracle.render(vp, tf, model, view, eye, 0.5, fp32=False)[0], G)
+                   - _loss(oracle.render(vm, tf, model, view, eye, 0.5, fp32=False)[0], G)) / (2 * h)
+    scale = np.abs(g).max()
+    assert scale > 0
+    assert np.abs(fd - g).max() <= 1e-6 * scale
+    assert np.count_nonzero(np.abs(g) > 1e-3 * scale) > 50
+
+
+def test_fd_tf_every_entry():
+    """Central differences w.r.t. every TF entry (r, g, b, tau of each of the
+    R control points) equal the adjoint's T^ (Alg. 2, f_TF line)."""
+    model = "emission_absorption"
+    v, tf, view, eye, G = _fd_setup(model, R=5)
+    g = oracle.backward(v, tf, model, view, eye, 0.5, G, fp32=False, want=("tf",))["tf"]
+    h = 1e-6
+    fd = np.zeros_like(tf)
+    for idx in np.ndindex(tf.shape):
+        tp = tf.copy(); tp[idx] += h
+        tm = tf.copy(); tm[idx] -= h
+        fd[idx] = (_loss(oracle.render(v, tp, model, view, eye, 0.5, fp32=False)[0], G)
+                   - _loss(oracle.render(v, tm, model, view, eye, 0.5, fp32=False)[0], G)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-7 * np.abs(g).max())
+
+
+@pytest.mark.parametrize("model,ortho,eye", [
+    ("absorption", False, (0.9, 0.6, 1.7)),
+    ("emission_absorption", False, (0.9, 0.6, 1.7)),
+    ("emission_absorption", True, (-1.2, 0.5, 1.4)),
+    ("emission_absorption", False, (0.0, 2.2, 0.0)),      # looking along -y (fixed right)
+    ("emission_absorption", False, (0.1, 0.15, 0.3)),     # camera inside the box
+])
+def test_fd_eye(model, ortho, eye):
+    """Central differences w.r.t. the eye position equal the adjoint's camera
+    gradient, including the entry point's dependence on the camera."""
+    v, tf, view, eye, G = _fd_setup(model, ortho=ortho, eye=eye)
+    g = oracle.backward(v, tf, model, view, eye, 0.5, G, fp32=False, want=("eye",))["eye"]
+    h = 1e-6
+    for k in range(3):
+        ep = eye.copy(); ep[k] += h
+        em = eye.copy(); em[k] -= h
+        ip, Np, _ = oracle.render(v, tf, model, view, ep, 0.5, fp32=False)
+        im, Nm, _ = oracle.render(v, tf, model, view, em, 0.5, fp32=False)
+        assert (Np == Nm).all(), "N changed within the FD step: move the eye"
+        fd = (_loss(ip, G) - _loss(im, G)) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, np.abs(g).max()), (k, fd, g[k])
+
+
+def test_fd_step():
+    """Central differences w.r.t. the step size (Alg. 2: dt^ += i w.x^_i plus
+    the dependence of alpha on dt), with N held fixed."""
+    model = "emission_absorption"
+    v, tf, view, eye, G = _fd_setup(model)
+    step = 0.53
+    g = oracle.backward(v, tf, model, view, eye, step, G, fp32=False, want=("step",))["step"]
+    h = 1e-7
+    ip, Np, _ = oracle.render(v, tf, model, view, eye, step + h, fp32=False)
+    im, Nm, _ = oracle.render(v, tf, model, view, eye, step - h, fp32=False)
+    assert (Np == Nm).all()
+    fd = (_loss(ip, G) - _loss(im, G)) / (2 * h)
+    assert abs(fd - g) <= 1e-6 * max(1.0, abs(g))
+
+
+# --------------------------------------------------- forward mode vs adjoint
+@pytest.mark.parametrize("model,ortho", [("absorption", False), ("emission_absorption", False),
+                                         ("emission_absorption", True)])
+def test_dual_numbers_match_adjoint(model, ortho):
+    """Sec. 5.1: forward and adjoint differentiation give the same camera
+    gradient up to rounding. The dual-number render is an independent
+    derivation of d(image)/d(eye)."""
+    v, tf, view, eye, G = _fd_setup(model, ortho=ortho, eye=(1.1, -0.7, 1.5))
+    img, dimg = oracle.render_dual(v, tf, model, view, eye, 0.5)
+    img64, _, _ = oracle.render(v, tf, model, view, eye, 0.5, fp32=False)
+    np.testing.assert_allclose(img, img64, rtol=1e-13, atol=1e-15)
+    fwd = np.einsum("pc,pck->k", G, dimg)
+    adj = oracle.backward(v, tf, model, view, eye, 0.5, G, fp32=False, want=("eye",))["eye"]
+    np.testing.assert_allclose(adj, fwd, rtol=1e-10, atol=1e-12 * np.abs(fwd).max())
+
+
+def test_fp32_setup_close_to_fp64():
+    """The binary32 ray setup differs from the binary64 one by rounding only
+    (images agree to ~1e-6 where N agrees)."""
+    w = syn.workload("ea_256", scale=0.125)
+    img32, N32, _ = oracle.render(w.volumes[0], w.tf, w.model, w.views[0], w.eye[0], 0.5, fp32=True)
+    img64, N64, _ = oracle.render(w.volumes[0], w.tf, w.model, w.views[0], w.eye[0], 0.5, fp32=False)
+    same = N32 == N64
+    assert same.mean() > 0.99
+    assert np.abs(img32[same] - img64[same]).max() < 1e-4
