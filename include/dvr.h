@@ -1,0 +1,213 @@
+/*
+ * dvr.h - C ABI of the B300 differentiable direct volume renderer.
+ *
+ * The renderer computes the discretised emission-absorption integral of
+ * Weiss & Westermann, "Differentiable Direct Volume Rendering" (Eq. 1 and
+ * the Riemann sum of Sec. 3.1) by the per-ray front-to-back march of
+ * Alg. 1, and its adjoint (Alg. 2) in memory that does not grow with the
+ * number of steps (the inversion of Sec. 4.4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All array arguments named "device" are CUDA device pointers owned by
+ *   the caller. The library never allocates, frees or keeps them.
+ * - Every call is asynchronous and stream-ordered on `stream` (a
+ *   cudaStream_t passed as void*; NULL = the legacy default stream).
+ *   Host-side argument structs are read before the call returns.
+ * - Return value: DVR_OK (0) or a negative DVR_ERR_* code. On error nothing
+ *   was launched, and dvr_last_error() returns a message for the calling
+ *   host thread.
+ * - Gradient outputs are ACCUMULATED (+=), as in the "+=" of Alg. 2: the
+ *   caller zeroes them before the first call. A NULL gradient pointer
+ *   disables that gradient (the kernel variant without it is launched,
+ *   Sec. 4.4 "selected via template parameters").
+ * - Volume: density V at the vertices of a regular grid (Sec. 3.1),
+ *   layout [nz][ny][nx] (x fastest). The grid spans a box centred at the
+ *   origin; the longest axis has length 1, vertex j of axis a sits at
+ *   -ext_a/2 + j*h with h = 1/(max(nx,ny,nz)-1). Densities between
+ *   vertices are trilinear.
+ * - Step: `step_voxels` is the sample spacing in units of h; the world
+ *   step is dt = step_voxels / (max(nx,ny,nz) - 1).
+ * - Ray (Alg. 1, f_camera): the camera of a view sits at eye[v] (world
+ *   coordinates, device memory) and looks at the origin with world up +y
+ *   (right vector +x when the view axis is within 2^-13 rad of y). Pixel
+ *   (px, py), row 0 at the top, has image-plane coordinates
+ *   sx = (2px+1)/W - 1, sy = 1 - (2py+1)/H. Perspective: the ray leaves the
+ *   eye along normalize(f + sx*lens*W/H*r + sy*lens*u), lens = tan(fov_y/2).
+ *   Orthographic: the ray starts at eye + sx*lens/2*W/H*r + sy*lens/2*u with
+ *   direction f, lens = image-plane height in world units.
+ *   x_o is where the ray enters the box (or the ray origin if that is
+ *   inside), L the length inside, N = ceil(L/dt - 2^-10) samples at
+ *   x_i = x_o + i*dt*w, i = 0..N-1.
+ *   The ray setup is evaluated in binary32, every operation correctly
+ *   rounded and none fused, in this order (a.b is (a0 b0 + a1 b1) + a2 b2):
+ *     le = sqrt(e.e); f = -e/le; q = fx fx + fz fz;
+ *     r = (-fz/sqrt(q), 0, fx/sqrt(q))  (q >= 2^-26), else (1, 0, 0);
+ *     u = r x f, each component (r_i f_j) - (r_j f_i);
+ *     sx = (2px+1)/W - 1; sy = 1 - (2py+1)/H; aspect = W/H;
+ *     perspective: a = sx (lens aspect), b = sy lens, d = (f + a r) + b u,
+ *                  w = d/sqrt(d.d), o = e;
+ *     ortho: h = lens 0.5, a = sx (h aspect), b = sy h, o = (e + a r) + b u,
+ *            w = f;
+ *     per axis with w != 0: t0 = (-half - o)/w, t1 = (half - o)/w;
+ *     tn = max(0, near faces), tf = min(far faces), L = tf - tn,
+ *     N = ceil(L/dt - 2^-10), x_o = o + tn w;
+ *   half = ((n_a - 1)/(nmax - 1)) 0.5 and dt = step_voxels/(nmax - 1),
+ *   so the integer N does not depend on FMA contraction.
+ * - Models: DVR_ABSORPTION uses the density itself as absorption
+ *   (tau = d per world unit, no transfer function) and writes one channel,
+ *   the opacity A = 1 - exp(-sum_i dt d_i). DVR_EMISSION_ABSORPTION maps
+ *   d (clamped to [0,1]) through the transfer function, R control points at
+ *   densities r/(R-1), linear in between, each (r, g, b, tau); blends
+ *   C += (1-A) alpha_i rgb_i, A += (1-A) alpha_i with
+ *   alpha_i = 1 - exp(-dt tau_i) (Eq. blend-forward, premultiplied
+ *   emission) and writes four channels (C_r, C_g, C_b, A).
+ */
+#ifndef DVR_H
+#define DVR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DVR_ABI_VERSION 1
+
+/* exported from the shared library (which hides everything else) */
+#if defined(__GNUC__)
+#define DVR_API __attribute__((visibility("default")))
+#else
+#define DVR_API
+#endif
+
+/* status codes */
+#define DVR_OK 0
+#define DVR_ERR_ARG (-1)         /* invalid argument (null pointer, size, index) */
+#define DVR_ERR_DTYPE (-2)       /* unsupported storage type for this argument */
+#define DVR_ERR_CUDA (-3)        /* a CUDA runtime call or launch failed */
+#define DVR_ERR_UNSUPPORTED (-4) /* valid request this build does not implement */
+
+/* storage types */
+#define DVR_F32 0
+#define DVR_F16 1
+#define DVR_BF16 2
+
+/* optical models (Sec. 3.1; Sec. 5.3 absorption-only) */
+#define DVR_ABSORPTION 0
+#define DVR_EMISSION_ABSORPTION 1
+
+/* dvr_backward flags */
+/* accumulate the TF gradient with one global atomic per sample and
+ * channel ("adjoint-immediate", Sec. 5.2) instead of the default per-block
+ * shared-memory accumulation ("adjoint-delayed") */
+#define DVR_FLAG_TF_IMMEDIATE 1u
+
+/* One scalar volume. `data` is a device pointer to nx*ny*nz samples of
+ * `dtype`, layout [nz][ny][nx]; each of nx, ny, nz >= 2. */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t dtype;           /* DVR_F32, DVR_F16 or DVR_BF16 */
+    const void* data;
+} dvr_volume;
+
+/* Transfer function: `rgba` is a device pointer to R rows of
+ * (r, g, b, tau) in `dtype` (DVR_F32 or DVR_F16), R >= 2. Unused (may be
+ * NULL) for DVR_ABSORPTION. */
+typedef struct {
+    int32_t R;
+    int32_t dtype;
+    const void* rgba;
+} dvr_tf;
+
+/* Static description of one view. The view's pixels occupy
+ * [pixel_offset, pixel_offset + width*height) of the image / aux /
+ * grad_image arrays, row-major (row 0 at the top). */
+typedef struct {
+    int32_t width, height;   /* >= 1 */
+    int32_t ortho;           /* 0 perspective, 1 orthographic */
+    int32_t volume;          /* index into the volumes array */
+    float lens;              /* tan(fov_y/2), or ortho image height (world) */
+    int32_t reserved;        /* must be 0 */
+    int64_t pixel_offset;
+} dvr_view;
+
+/* ABI version (DVR_ABI_VERSION). */
+DVR_API int dvr_abi_version(void);
+
+/* Message for the last failing call on this host thread ("" if none). */
+DVR_API const char* dvr_last_error(void);
+
+/*
+ * Forward pass: Alg. 1 for every pixel of every view (one launch).
+ *
+ * volumes[n_volumes]   host array of volume descriptors (1 <= n_volumes <= 16)
+ * tf                   host pointer to the TF descriptor (EA model), else NULL
+ * model                DVR_ABSORPTION or DVR_EMISSION_ABSORPTION
+ * views[n_views]       host array, 1 <= n_views <= 4096
+ * eye                  device float[n_views][3], camera positions
+ * step_voxels          sample spacing in voxels, > 0
+ * image                device float[P][C], C = 4 (EA) or 1 (absorption),
+ *                      P = max over views of pixel_offset + width*height
+ * aux                  device float[P][2] or NULL: optical depth
+ *                      S = sum_i dt tau_i of each ray as an unevaluated sum
+ *                      hi + lo of two floats; dvr_backward needs it
+ * sample_count         device uint64[1] or NULL: the total number of
+ *                      samples taken is ADDED to it
+ * Errors: DVR_ERR_ARG for null/invalid descriptors or sizes, DVR_ERR_DTYPE
+ * for unsupported dtypes, DVR_ERR_CUDA if the launch fails.
+ */
+DVR_API int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
+                const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
+                float* image, float* aux, unsigned long long* sample_count, void* stream);
+
+/*
+ * Adjoint pass: Alg. 2 for every pixel of every view (one launch). Each
+ * ray re-marches back to front, reconstructs its transmittance from the
+ * stored optical depth (constant memory in the number of steps, Sec. 4.4),
+ * and accumulates:
+ *
+ * grad_volumes         host array [n_volumes] of device float pointers
+ *                      (each [nz][ny][nx] float32, or NULL), or NULL
+ * grad_tf              device float[R][4] or NULL (EA model only)
+ * grad_eye             device float[n_views][3] or NULL
+ * grad_step            device float[1] or NULL: dL/d(step_voxels)
+ *
+ * Inputs are those of the dvr_forward call that produced `aux` (same
+ * volumes, TF, views, eye, step), plus
+ * aux                  device float[P][2] written by dvr_forward
+ * grad_image           device float[P][C]: dL/d(image)
+ * flags                bitwise OR of DVR_FLAG_*
+ * Errors as dvr_forward.
+ */
+DVR_API int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
+                 const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
+                 const float* aux, const float* grad_image, float* const* grad_volumes,
+                 float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags, void* stream);
+
+/*
+ * L2 image loss and its gradient, the seed of Alg. 2 (first line):
+ * loss += scale * sum_j (image_j - target_j)^2 and
+ * grad_image_j = 2 * scale * (image_j - target_j), over n floats.
+ * image, target, grad_image: device float[n]; loss: device float[1] or NULL.
+ */
+DVR_API int dvr_loss_l2(const float* image, const float* target, int64_t n, float scale,
+                float* grad_image, float* loss, void* stream);
+
+/*
+ * Orbit camera (Sec. 5.1: camera on a sphere around the volume, given by
+ * longitude and latitude): eye = dist * (cos p sin y, sin p, cos p cos y)
+ * from params[v] = (yaw y, pitch p, distance dist), device float[n][3].
+ * dvr_orbit_eye writes eye (device float[n][3]); dvr_orbit_eye_backward
+ * ADDS the chain rule of dL/d(eye) into grad_params (device float[n][3]).
+ */
+DVR_API int dvr_orbit_eye(const float* params, int32_t n, float* eye, void* stream);
+DVR_API int dvr_orbit_eye_backward(const float* params, const float* grad_eye, int32_t n,
+                           float* grad_params, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DVR_H */

@@ -1,0 +1,78 @@
+"""ctypes view of the C ABI in include/dvr.h (argument marshalling only).
+
+The CUDA library `_lib/libdvr.so` is required: there is no CPU or
+PyTorch fallback. If it is missing it is built in-tree with nvcc; if that is
+impossible, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdvr.so")
+
+DVR_OK = 0
+DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
+DVR_ABSORPTION, DVR_EMISSION_ABSORPTION = 0, 1
+DVR_FLAG_TF_IMMEDIATE = 1
+
+# every symbol include/dvr.h declares
+SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_forward", "dvr_backward", "dvr_loss_l2",
+           "dvr_orbit_eye", "dvr_orbit_eye_backward")
+
+
+class DvrVolume(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("data", ctypes.c_void_p)]
+
+
+class DvrTF(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_int32), ("dtype", ctypes.c_int32), ("rgba", ctypes.c_void_p)]
+
+
+class DvrView(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("ortho", ctypes.c_int32),
+                ("volume", ctypes.c_int32), ("lens", ctypes.c_float), ("reserved", ctypes.c_int32),
+                ("pixel_offset", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libdvr.so (building it first if it does not exist)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            from . import build as _build
+            _build.build()
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, F, U32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
+                               ctypes.c_uint32)
+        lib.dvr_abi_version.restype = ctypes.c_int
+        lib.dvr_last_error.restype = ctypes.c_char_p
+        lib.dvr_forward.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P]
+        lib.dvr_backward.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, P, P, U32, P]
+        lib.dvr_loss_l2.argtypes = [P, P, I64, F, P, P, P]
+        lib.dvr_orbit_eye.argtypes = [P, I32, P, P]
+        lib.dvr_orbit_eye_backward.argtypes = [P, P, I32, P, P]
+        for name in ("dvr_forward", "dvr_backward", "dvr_loss_l2", "dvr_orbit_eye",
+                     "dvr_orbit_eye_backward"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+class DVRError(RuntimeError):
+    pass
+
+
+def check(rc: int, what: str):
+    if rc != DVR_OK:
+        msg = load().dvr_last_error().decode(errors="replace")
+        raise DVRError(f"{what} failed with code {rc}: {msg}")

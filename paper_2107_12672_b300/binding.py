@@ -1,0 +1,242 @@
+"""PyTorch-facing binding of the C ABI (marshalling only).
+
+Every step of the rendering and of its adjoint runs in the CUDA kernels of
+libdvr.so; this module only turns tensors into pointers, descriptors and
+the current stream, and allocates outputs with PyTorch.
+
+    image, aux = forward(volumes, tf, "emission_absorption", views, eye, 0.5)
+    grads = backward(volumes, tf, "emission_absorption", views, eye, 0.5, aux, grad_image,
+                     want=("tf", "eye"))
+    image = render(volume, tf, eye, views, 0.5, "emission_absorption")   # autograd
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _abi
+from .synthetic import View
+
+__all__ = ["View", "Scene", "forward", "backward", "loss_l2", "orbit_eye", "orbit_eye_backward",
+           "render", "orbit_camera", "split_views", "MODELS"]
+
+MODELS = {"absorption": _abi.DVR_ABSORPTION, "emission_absorption": _abi.DVR_EMISSION_ABSORPTION}
+_DTYPES = {torch.float32: _abi.DVR_F32, torch.float16: _abi.DVR_F16, torch.bfloat16: _abi.DVR_BF16}
+
+
+def _model(m) -> int:
+    return MODELS[m] if isinstance(m, str) else int(m)
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _require_cuda(t, name):
+    if t is None:
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+@dataclass
+class Scene:
+    """Descriptor arrays for one set of volumes, TF and views."""
+    volumes: list
+    tf: torch.Tensor | None
+    model: int
+    views: list
+    vol_desc: ctypes.Array
+    tf_desc: _abi.DvrTF | None
+    view_desc: ctypes.Array
+    pixels: int
+    channels: int
+    offsets: list
+
+    @staticmethod
+    def make(volumes, tf, model, views) -> "Scene":
+        if isinstance(volumes, torch.Tensor):
+            volumes = [volumes]
+        model = _model(model)
+        vd = (_abi.DvrVolume * len(volumes))()
+        for i, v in enumerate(volumes):
+            _require_cuda(v, f"volume {i}")
+            if v.dim() != 3:
+                raise ValueError("a volume is a 3-D tensor [nz][ny][nx]")
+            if v.dtype not in _DTYPES:
+                raise ValueError(f"volume dtype {v.dtype} unsupported")
+            nz, ny, nx = v.shape
+            vd[i] = _abi.DvrVolume(nx, ny, nz, _DTYPES[v.dtype], v.data_ptr())
+        td = None
+        if model == _abi.DVR_EMISSION_ABSORPTION:
+            _require_cuda(tf, "tf")
+            if tf.dim() != 2 or tf.shape[1] != 4:
+                raise ValueError("the transfer function is a [R][4] tensor")
+            if tf.dtype not in (torch.float32, torch.float16):
+                raise ValueError("TF dtype must be float32 or float16")
+            td = _abi.DvrTF(tf.shape[0], _DTYPES[tf.dtype], tf.data_ptr())
+        wd = (_abi.DvrView * len(views))()
+        off = 0
+        offsets = []
+        for i, w in enumerate(views):
+            lens = w.ortho_height if w.ortho else w.tan_half_fov_y
+            wd[i] = _abi.DvrView(int(w.width), int(w.height), int(bool(w.ortho)),
+                                 int(getattr(w, "volume_index", 0)), float(lens), 0, off)
+            offsets.append(off)
+            off += int(w.width) * int(w.height)
+        ch = 4 if model == _abi.DVR_EMISSION_ABSORPTION else 1
+        return Scene(list(volumes), tf, model, list(views), vd, td, wd, off, ch, offsets)
+
+    def tf_ref(self):
+        return ctypes.byref(self.tf_desc) if self.tf_desc is not None else None
+
+
+def forward(volumes, tf, model, views, eye, step_voxels, *, scene: Scene | None = None, image=None,
+            aux=None, sample_count=None, stream=None):
+    """Alg. 1 for all views in one launch. Returns (image [P][C], aux [P][2])."""
+    sc = scene or Scene.make(volumes, tf, model, views)
+    dev = sc.volumes[0].device
+    _require_cuda(eye, "eye")
+    if eye.dtype != torch.float32 or eye.numel() != 3 * len(sc.views):
+        raise ValueError("eye must be float32 [n_views][3]")
+    if image is None:
+        image = torch.empty((sc.pixels, sc.channels), device=dev, dtype=torch.float32)
+    if aux is None:
+        aux = torch.empty((sc.pixels, 2), device=dev, dtype=torch.float32)
+    rc = _abi.load().dvr_forward(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
+                                 len(sc.views), _ptr(eye), float(step_voxels), _ptr(image), _ptr(aux),
+                                 _ptr(sample_count), _stream_ptr(stream))
+    _abi.check(rc, "dvr_forward")
+    return image, aux
+
+
+def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, want=("volume", "tf", "eye"),
+             scene: Scene | None = None, grads: dict | None = None, tf_immediate=False, stream=None):
+    """Alg. 2 for all views in one launch. Returns a dict with float32
+    gradients for the requested parameters ("volume" -> list, "tf", "eye",
+    "step"); buffers passed in `grads` are accumulated into."""
+    sc = scene or Scene.make(volumes, tf, model, views)
+    dev = sc.volumes[0].device
+    g = dict(grads or {})
+    if "volume" in want and "volume" not in g:
+        g["volume"] = [torch.zeros(v.shape, device=dev, dtype=torch.float32) for v in sc.volumes]
+    if "tf" in want and sc.model == _abi.DVR_EMISSION_ABSORPTION and "tf" not in g:
+        g["tf"] = torch.zeros((sc.tf.shape[0], 4), device=dev, dtype=torch.float32)
+    if "eye" in want and "eye" not in g:
+        g["eye"] = torch.zeros((len(sc.views), 3), device=dev, dtype=torch.float32)
+    if "step" in want and "step" not in g:
+        g["step"] = torch.zeros(1, device=dev, dtype=torch.float32)
+    gv = None
+    if "volume" in g:
+        gv = (ctypes.c_void_p * len(sc.volumes))(*[_ptr(t) for t in g["volume"]])
+    flags = _abi.DVR_FLAG_TF_IMMEDIATE if tf_immediate else 0
+    rc = _abi.load().dvr_backward(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
+                                  len(sc.views), _ptr(eye), float(step_voxels), _ptr(aux),
+                                  _ptr(grad_image), gv, _ptr(g.get("tf")), _ptr(g.get("eye")),
+                                  _ptr(g.get("step")), flags, _stream_ptr(stream))
+    _abi.check(rc, "dvr_backward")
+    return g
+
+
+def loss_l2(image, target, scale=1.0, *, grad_image=None, loss=None, stream=None):
+    """L2 loss seed of Alg. 2: loss += scale*sum((x-y)^2), grad = 2 scale (x-y)."""
+    if grad_image is None:
+        grad_image = torch.empty_like(image)
+    rc = _abi.load().dvr_loss_l2(_ptr(image), _ptr(target), image.numel(), float(scale),
+                                 _ptr(grad_image), _ptr(loss), _stream_ptr(stream))
+    _abi.check(rc, "dvr_loss_l2")
+    return grad_image
+
+
+def orbit_eye(params, *, eye=None, stream=None):
+    """Eye positions [n][3] from orbit parameters (yaw, pitch, distance) [n][3]."""
+    _require_cuda(params, "params")
+    if eye is None:
+        eye = torch.empty_like(params)
+    rc = _abi.load().dvr_orbit_eye(_ptr(params), params.shape[0], _ptr(eye), _stream_ptr(stream))
+    _abi.check(rc, "dvr_orbit_eye")
+    return eye
+
+
+def orbit_eye_backward(params, grad_eye, *, grad_params=None, stream=None):
+    if grad_params is None:
+        grad_params = torch.zeros_like(params)
+    rc = _abi.load().dvr_orbit_eye_backward(_ptr(params), _ptr(grad_eye), params.shape[0],
+                                            _ptr(grad_params), _stream_ptr(stream))
+    _abi.check(rc, "dvr_orbit_eye_backward")
+    return grad_params
+
+
+def split_views(image, scene_or_views):
+    """Split a flat [P][C] image into per-view [H][W][C] tensors."""
+    views = scene_or_views.views if isinstance(scene_or_views, Scene) else scene_or_views
+    out, off = [], 0
+    for w in views:
+        n = w.width * w.height
+        out.append(image[off:off + n].view(w.height, w.width, -1))
+        off += n
+    return out
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, spec, eye, tf, *volumes):
+        model, views, step, tf_immediate = spec
+        sc = Scene.make(list(volumes), tf, model, views)
+        image, aux = forward(None, None, None, None, eye, step, scene=sc)
+        ctx.spec = spec
+        ctx.save_for_backward(eye, tf, aux, *volumes)
+        return image
+
+    @staticmethod
+    def backward(ctx, grad_image):
+        model, views, step, tf_immediate = ctx.spec
+        eye, tf, aux, *volumes = ctx.saved_tensors
+        sc = Scene.make(volumes, tf, model, views)
+        want = []
+        if ctx.needs_input_grad[1]:
+            want.append("eye")
+        if tf is not None and ctx.needs_input_grad[2]:
+            want.append("tf")
+        if any(ctx.needs_input_grad[3:]):
+            want.append("volume")
+        g = backward(None, None, None, None, eye, step, aux, grad_image.contiguous(), want=tuple(want),
+                     scene=sc, tf_immediate=tf_immediate)
+        gvol = g.get("volume") or [None] * len(volumes)
+        gvol = [gv if need else None for gv, need in zip(gvol, ctx.needs_input_grad[3:])]
+        return (None, g.get("eye"), g.get("tf"), *gvol)
+
+
+def render(volumes, tf, eye, views, step_voxels, model="emission_absorption", tf_immediate=False):
+    """Differentiable render of all views: image [P][C] (C = 4 or 1).
+    Gradients flow to eye, tf and the volumes (Alg. 2)."""
+    if isinstance(volumes, torch.Tensor):
+        volumes = [volumes]
+    return _RenderFn.apply((_model(model), list(views), float(step_voxels), bool(tf_immediate)),
+                           eye, tf, *volumes)
+
+
+class _OrbitFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, params):
+        ctx.save_for_backward(params)
+        return orbit_eye(params.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_eye):
+        (params,) = ctx.saved_tensors
+        return orbit_eye_backward(params.contiguous(), grad_eye.contiguous())
+
+
+def orbit_camera(params):
+    """Differentiable eye positions from (yaw, pitch, distance) [n][3]."""
+    return _OrbitFn.apply(params)

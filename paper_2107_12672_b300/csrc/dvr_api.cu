@@ -1,0 +1,244 @@
+// The C ABI (include/dvr.h): argument checks, packing of the launch
+// parameters, and dispatch to the kernels. Nothing here allocates device
+// memory or computes any part of the rendering.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+
+#include "dvr.h"
+#include "dvr_launch.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(DVR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+struct Common {
+    int dtype = 0;
+    int channels = 1;
+    long long pixels = 0;   // P
+};
+
+int check_common(const dvr_volume* vols, int nvol, const dvr_tf* tf, int model, const dvr_view* views,
+                 int nviews, const float* eye, float step, Common& c)
+{
+    if (model != DVR_ABSORPTION && model != DVR_EMISSION_ABSORPTION)
+        return fail(DVR_ERR_ARG, "model %d is not DVR_ABSORPTION or DVR_EMISSION_ABSORPTION", model);
+    if (!vols || nvol < 1 || nvol > dvr::kMaxVolumes)
+        return fail(DVR_ERR_ARG, "n_volumes %d outside [1, %d] or volumes is NULL", nvol, dvr::kMaxVolumes);
+    if (!views || nviews < 1 || nviews > 4096)
+        return fail(DVR_ERR_ARG, "n_views %d outside [1, 4096] or views is NULL", nviews);
+    if (!eye) return fail(DVR_ERR_ARG, "eye is NULL");
+    if (!(step >= 0x1p-10f) || !std::isfinite(step))
+        return fail(DVR_ERR_ARG, "step_voxels %g must be finite and >= 2^-10", (double)step);
+    c.dtype = vols[0].dtype;
+    for (int i = 0; i < nvol; ++i) {
+        const dvr_volume& v = vols[i];
+        if (!v.data) return fail(DVR_ERR_ARG, "volume %d: data is NULL", i);
+        if (v.nx < 2 || v.ny < 2 || v.nz < 2)
+            return fail(DVR_ERR_ARG, "volume %d: every dimension must be >= 2 (got %d x %d x %d)", i, v.nx, v.ny, v.nz);
+        if ((double)v.nx * v.ny * v.nz >= 4294967296.0)
+            return fail(DVR_ERR_ARG, "volume %d: more than 2^32 - 1 voxels", i);
+        if (v.dtype != DVR_F32 && v.dtype != DVR_F16 && v.dtype != DVR_BF16)
+            return fail(DVR_ERR_DTYPE, "volume %d: dtype %d unsupported", i, v.dtype);
+        if (v.dtype != c.dtype)
+            return fail(DVR_ERR_DTYPE, "volume %d: all volumes of one call must share a dtype", i);
+        if (!aligned(v.data, v.dtype == DVR_F32 ? 4 : 2))
+            return fail(DVR_ERR_ARG, "volume %d: data is not aligned to its element size", i);
+    }
+    if (model == DVR_EMISSION_ABSORPTION) {
+        if (!tf || !tf->rgba) return fail(DVR_ERR_ARG, "emission-absorption needs a transfer function");
+        if (tf->R < 2 || tf->R > dvr::kMaxTF)
+            return fail(DVR_ERR_ARG, "TF has %d rows; 2..%d supported", tf->R, dvr::kMaxTF);
+        if (tf->dtype != DVR_F32 && tf->dtype != DVR_F16)
+            return fail(DVR_ERR_DTYPE, "TF dtype %d unsupported (DVR_F32 or DVR_F16)", tf->dtype);
+        if (!aligned(tf->rgba, tf->dtype == DVR_F32 ? 16 : 2))
+            return fail(DVR_ERR_ARG, "TF rows are not aligned (16 bytes for DVR_F32)");
+        c.channels = 4;
+    }
+    c.pixels = 0;
+    for (int i = 0; i < nviews; ++i) {
+        const dvr_view& w = views[i];
+        if (w.width < 1 || w.height < 1 || w.width > 65536 || w.height > 65536)
+            return fail(DVR_ERR_ARG, "view %d: size %d x %d outside [1, 65536]", i, w.width, w.height);
+        if (w.volume < 0 || w.volume >= nvol)
+            return fail(DVR_ERR_ARG, "view %d: volume index %d outside [0, %d)", i, w.volume, nvol);
+        if (w.ortho != 0 && w.ortho != 1) return fail(DVR_ERR_ARG, "view %d: ortho must be 0 or 1", i);
+        if (!(w.lens > 0.f) || !std::isfinite(w.lens))
+            return fail(DVR_ERR_ARG, "view %d: lens %g must be finite and > 0", i, (double)w.lens);
+        if (w.pixel_offset < 0) return fail(DVR_ERR_ARG, "view %d: negative pixel_offset", i);
+        if (w.reserved != 0) return fail(DVR_ERR_ARG, "view %d: reserved field must be 0", i);
+        const long long end = w.pixel_offset + (long long)w.width * w.height;
+        if (end > c.pixels) c.pixels = end;
+    }
+    return DVR_OK;
+}
+
+// Fill the launch parameters for views [v0, v1).
+void pack(dvr::Params& p, const dvr_volume* vols, int nvol, const dvr_tf* tf, const dvr_view* views,
+          int v0, int v1, const float* eye, float step)
+{
+    memset(&p, 0, sizeof(p));
+    for (int i = 0; i < nvol; ++i) {
+        p.vol[i].data = vols[i].data;
+        p.vol[i].n[0] = vols[i].nx;
+        p.vol[i].n[1] = vols[i].ny;
+        p.vol[i].n[2] = vols[i].nz;
+        int m = vols[i].nx > vols[i].ny ? vols[i].nx : vols[i].ny;
+        p.vol[i].nmax = vols[i].nz > m ? vols[i].nz : m;
+    }
+    int tiles = 0;
+    for (int i = v0; i < v1; ++i) {
+        const dvr_view& w = views[i];
+        dvr::ViewDesc& d = p.view[i - v0];
+        d.width = w.width;
+        d.height = w.height;
+        d.ortho = w.ortho;
+        d.volume = w.volume;
+        d.lens = w.lens;
+        d.tiles_x = (w.width + dvr::kTileW - 1) / dvr::kTileW;
+        d.pixel_offset = w.pixel_offset;
+        p.tile_start[i - v0] = tiles;
+        tiles += d.tiles_x * ((w.height + dvr::kTileH - 1) / dvr::kTileH);
+    }
+    p.tile_start[v1 - v0] = tiles;
+    p.total_tiles = tiles;
+    p.n_views = v1 - v0;
+    p.view_base = v0;
+    p.step_voxels = step;
+    p.eye = eye;
+    if (tf) {
+        p.R = tf->R;
+        p.tf_dtype = tf->dtype;
+        p.tf = tf->rgba;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int dvr_abi_version(void) { return DVR_ABI_VERSION; }
+
+const char* dvr_last_error(void) { return g_err; }
+
+int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
+                const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
+                float* image, float* aux, unsigned long long* sample_count, void* stream)
+{
+    g_err[0] = 0;
+    Common c;
+    int rc = check_common(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, c);
+    if (rc) return rc;
+    if (!image) return fail(DVR_ERR_ARG, "image is NULL");
+    if (!aligned(image, c.channels == 4 ? 16 : 4)) return fail(DVR_ERR_ARG, "image is not 16-byte aligned");
+    if (aux && !aligned(aux, 8)) return fail(DVR_ERR_ARG, "aux is not 8-byte aligned");
+    dvr::Params p;
+    for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
+        const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
+        pack(p, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
+             step_voxels);
+        p.image = image;
+        p.aux = aux;
+        p.sample_count = sample_count;
+        cudaError_t e = dvr::launch_forward(p, model, c.dtype, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dvr_forward launch");
+    }
+    return DVR_OK;
+}
+
+int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
+                 const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
+                 const float* aux, const float* grad_image, float* const* grad_volumes,
+                 float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags, void* stream)
+{
+    g_err[0] = 0;
+    if (flags & ~DVR_FLAG_TF_IMMEDIATE) return fail(DVR_ERR_ARG, "unknown flag bits 0x%x", flags);
+    Common c;
+    int rc = check_common(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, c);
+    if (rc) return rc;
+    if (!aux || !grad_image) return fail(DVR_ERR_ARG, "aux and grad_image are required");
+    if (!aligned(aux, 8)) return fail(DVR_ERR_ARG, "aux is not 8-byte aligned");
+    if (!aligned(grad_image, c.channels == 4 ? 16 : 4))
+        return fail(DVR_ERR_ARG, "grad_image is not 16-byte aligned");
+    if (model != DVR_EMISSION_ABSORPTION && grad_tf)
+        return fail(DVR_ERR_ARG, "grad_tf needs the emission-absorption model");
+    bool gvol = false;
+    if (grad_volumes)
+        for (int i = 0; i < n_volumes; ++i) gvol |= grad_volumes[i] != nullptr;
+    const int tfm = grad_tf ? ((flags & DVR_FLAG_TF_IMMEDIATE) ? dvr::kTFImmediate : dvr::kTFDelayed)
+                            : dvr::kTFNone;
+    const bool pos = grad_eye != nullptr || grad_step != nullptr;
+    if (!gvol && tfm == dvr::kTFNone && !pos) return DVR_OK;   // nothing requested
+    // the scattering kernel variant is chosen per launch: when any volume
+    // takes a gradient, every rendered volume needs a buffer
+    if (gvol)
+        for (int i = 0; i < n_views; ++i)
+            if (!grad_volumes[views[i].volume])
+                return fail(DVR_ERR_ARG, "view %d renders volume %d, which has no gradient buffer "
+                            "while another volume has one", i, views[i].volume);
+    dvr::Params p;
+    for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
+        const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
+        pack(p, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
+             step_voxels);
+        if (grad_volumes)
+            for (int i = 0; i < n_volumes; ++i) p.vol[i].grad = grad_volumes[i];
+        p.aux = const_cast<float*>(aux);
+        p.grad_image = grad_image;
+        p.grad_tf = grad_tf;
+        p.grad_eye = grad_eye;
+        p.grad_step = grad_step;
+        cudaError_t e = dvr::launch_backward(p, model, c.dtype, gvol, tfm, pos, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dvr_backward launch");
+    }
+    return DVR_OK;
+}
+
+int dvr_loss_l2(const float* image, const float* target, int64_t n, float scale, float* grad_image,
+                float* loss, void* stream)
+{
+    g_err[0] = 0;
+    if (n < 0) return fail(DVR_ERR_ARG, "n < 0");
+    if (n == 0) return DVR_OK;
+    if (!image || !target || !grad_image) return fail(DVR_ERR_ARG, "image, target and grad_image are required");
+    cudaError_t e = dvr::launch_loss_l2(image, target, n, scale, grad_image, loss, (cudaStream_t)stream);
+    return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_loss_l2 launch");
+}
+
+int dvr_orbit_eye(const float* params, int32_t n, float* eye, void* stream)
+{
+    g_err[0] = 0;
+    if (n < 1 || !params || !eye) return fail(DVR_ERR_ARG, "need n >= 1 and non-null params, eye");
+    cudaError_t e = dvr::launch_orbit_eye(params, n, eye, (cudaStream_t)stream);
+    return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_orbit_eye launch");
+}
+
+int dvr_orbit_eye_backward(const float* params, const float* grad_eye, int32_t n, float* grad_params,
+                           void* stream)
+{
+    g_err[0] = 0;
+    if (n < 1 || !params || !grad_eye || !grad_params)
+        return fail(DVR_ERR_ARG, "need n >= 1 and non-null params, grad_eye, grad_params");
+    cudaError_t e = dvr::launch_orbit_eye_backward(params, grad_eye, n, grad_params, (cudaStream_t)stream);
+    return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_orbit_eye_backward launch");
+}
+
+}  // extern "C"

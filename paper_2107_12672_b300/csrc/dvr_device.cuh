@@ -1,0 +1,341 @@
+// Device building blocks of the B300 renderer: launch parameters, the ray
+// setup f_camera, sample positions, trilinear f_interpolate and the
+// transfer function f_TF (Alg. 1; Sec. 3.1). Shared by the forward and the
+// adjoint kernels so that both re-evaluate each sample with the same
+// instructions.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dvr.h"
+
+namespace dvr {
+
+constexpr int kMaxVolumes = 16;
+constexpr int kMaxViewsPerLaunch = 512;
+constexpr int kWarps = 4;            // warps per block
+constexpr int kTileW = 8;            // a warp renders an 8 x 4 pixel tile
+constexpr int kTileH = 4;
+constexpr int kMaxTF = 1024;         // transfer-function rows staged in shared memory
+
+struct VolumeDesc {
+    const void* data;
+    float* grad;                     // adjoint only, may be null
+    int n[3];
+    int nmax;
+};
+
+struct ViewDesc {
+    int width, height, ortho, volume;
+    float lens;
+    int tiles_x;
+    long long pixel_offset;
+};
+
+struct Params {
+    VolumeDesc vol[kMaxVolumes];
+    ViewDesc view[kMaxViewsPerLaunch];
+    int tile_start[kMaxViewsPerLaunch + 1];  // prefix sum of warp tiles per view
+    int n_views;
+    int total_tiles;
+    int view_base;                   // index of view[0] in the caller's arrays
+    int R;
+    int tf_dtype;
+    float step_voxels;
+    const void* tf;
+    const float* eye;                // [caller views][3]
+    float* image;
+    float* aux;
+    const float* grad_image;
+    float* grad_tf;
+    float* grad_eye;
+    float* grad_step;
+    unsigned long long* sample_count;
+};
+
+// ---------------------------------------------------------------- storage
+template <typename T> struct Load;
+template <> struct Load<float> {
+    static __device__ __forceinline__ float get(const float* p) { return __ldg(p); }
+};
+template <> struct Load<__half> {
+    static __device__ __forceinline__ float get(const __half* p) { return __half2float(__ldg(p)); }
+};
+template <> struct Load<__nv_bfloat16> {
+    static __device__ __forceinline__ float get(const __nv_bfloat16* p) {
+        return __bfloat162float(__ldg(p));
+    }
+};
+
+// --------------------------------------------------------------- the ray
+struct Ray {
+    float o[3], w[3], xo[3];
+    float f[3], r[3], u[3];
+    float el, ql, dl, su, sv;
+    float tn;
+    int N, axis, degenerate;
+};
+
+struct Grid {
+    float half[3];
+    float dt;
+    float inv_h;                     // max(n) - 1
+    int n[3];
+};
+
+__device__ __forceinline__ void make_grid(const VolumeDesc& v, float step, Grid& g)
+{
+    const float den = (float)(v.nmax - 1);
+    g.inv_h = den;
+    g.dt = __fdiv_rn(step, den);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = v.n[a];
+        g.half[a] = __fmul_rn(__fdiv_rn((float)(v.n[a] - 1), den), 0.5f);
+    }
+}
+
+// f_camera: binary32, each operation correctly rounded and unfused, in the
+// order the C ABI header states (the integer N must not depend on FMA
+// contraction or on the compiler's choices).
+__device__ __forceinline__ void ray_setup(const float e[3], int px, int py, const ViewDesc& vw,
+                                          const Grid& g, Ray& R)
+{
+    const float e2 = __fadd_rn(__fadd_rn(__fmul_rn(e[0], e[0]), __fmul_rn(e[1], e[1])),
+                               __fmul_rn(e[2], e[2]));
+    R.el = __fsqrt_rn(e2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) R.f[a] = __fdiv_rn(-e[a], R.el);
+    const float q2 = __fadd_rn(__fmul_rn(R.f[0], R.f[0]), __fmul_rn(R.f[2], R.f[2]));
+    if (q2 < 0x1p-26f) {
+        R.degenerate = 1;
+        R.ql = 0.f;
+        R.r[0] = 1.f; R.r[1] = 0.f; R.r[2] = 0.f;
+    } else {
+        R.degenerate = 0;
+        R.ql = __fsqrt_rn(q2);
+        R.r[0] = __fdiv_rn(-R.f[2], R.ql);
+        R.r[1] = 0.f;
+        R.r[2] = __fdiv_rn(R.f[0], R.ql);
+    }
+    R.u[0] = __fsub_rn(__fmul_rn(R.r[1], R.f[2]), __fmul_rn(R.r[2], R.f[1]));
+    R.u[1] = __fsub_rn(__fmul_rn(R.r[2], R.f[0]), __fmul_rn(R.r[0], R.f[2]));
+    R.u[2] = __fsub_rn(__fmul_rn(R.r[0], R.f[1]), __fmul_rn(R.r[1], R.f[0]));
+
+    const float sx = __fsub_rn(__fdiv_rn((float)(2 * px + 1), (float)vw.width), 1.0f);
+    const float sy = __fsub_rn(1.0f, __fdiv_rn((float)(2 * py + 1), (float)vw.height));
+    const float aspect = __fdiv_rn((float)vw.width, (float)vw.height);
+    if (!vw.ortho) {
+        R.su = __fmul_rn(sx, __fmul_rn(vw.lens, aspect));
+        R.sv = __fmul_rn(sy, vw.lens);
+        float d[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            d[a] = __fadd_rn(__fadd_rn(R.f[a], __fmul_rn(R.su, R.r[a])), __fmul_rn(R.sv, R.u[a]));
+        R.dl = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])),
+                                    __fmul_rn(d[2], d[2])));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R.w[a] = __fdiv_rn(d[a], R.dl);
+            R.o[a] = e[a];
+        }
+    } else {
+        const float hh = __fmul_rn(vw.lens, 0.5f);
+        R.su = __fmul_rn(sx, __fmul_rn(hh, aspect));
+        R.sv = __fmul_rn(sy, hh);
+        R.dl = 1.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R.o[a] = __fadd_rn(__fadd_rn(e[a], __fmul_rn(R.su, R.r[a])), __fmul_rn(R.sv, R.u[a]));
+            R.w[a] = R.f[a];
+        }
+    }
+    float tn = 0.f, tf = __int_as_float(0x7f800000);
+    int axis = -1;
+    bool hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (R.w[a] != 0.f) {
+            const float t0 = __fdiv_rn(__fsub_rn(-g.half[a], R.o[a]), R.w[a]);
+            const float t1 = __fdiv_rn(__fsub_rn(g.half[a], R.o[a]), R.w[a]);
+            const float tnear = t0 < t1 ? t0 : t1;
+            const float tfar = t0 < t1 ? t1 : t0;
+            if (tnear > tn) { tn = tnear; axis = a; }
+            if (tfar < tf) tf = tfar;
+        } else if (R.o[a] < -g.half[a] || R.o[a] > g.half[a]) {
+            hit = false;
+        }
+    }
+    R.tn = tn;
+    R.axis = axis;
+    R.N = 0;
+    if (hit && tf > tn) {
+        const float L = __fsub_rn(tf, tn);
+        const float q = __fdiv_rn(L, g.dt);
+        const float nq = ceilf(__fsub_rn(q, 0x1p-10f));
+        R.N = nq > 0.f ? (int)nq : 0;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) R.xo[a] = __fadd_rn(R.o[a], __fmul_rn(tn, R.w[a]));
+}
+
+// Sample positions in grid coordinates, g_i = G0 + i*Gd, each term carried
+// as an unevaluated float pair so that g_i is within one rounding of the
+// exact (x_o + i dt w + half) * inv_h, however long the ray.
+struct March {
+    float g0h[3], g0l[3], gdh[3], gdl[3];
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void make_march(const Ray& R, const Grid& g, March& m)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float sh, sl;
+        two_sum(R.xo[a], g.half[a], sh, sl);
+        m.g0h[a] = sh * g.inv_h;
+        m.g0l[a] = __fmaf_rn(sh, g.inv_h, -m.g0h[a]) + sl * g.inv_h;
+        const float ph = R.w[a] * g.dt;
+        const float pl = __fmaf_rn(R.w[a], g.dt, -ph);
+        m.gdh[a] = ph * g.inv_h;
+        m.gdl[a] = __fmaf_rn(ph, g.inv_h, -m.gdh[a]) + pl * g.inv_h;
+    }
+}
+
+__device__ __forceinline__ float march_coord(const March& m, int a, float fi)
+{
+    return __fmaf_rn(fi, m.gdh[a], m.g0h[a]) + __fmaf_rn(fi, m.gdl[a], m.g0l[a]);
+}
+
+// Trilinear interpolation at grid coordinate g (clamped to the box).
+struct Cell {
+    uint32_t base;                   // index of corner (0,0,0)
+    float fx, fy, fz;
+    bool in[3];                      // false where g was clamped
+    float v[8];                      // corner values, bit i: x, y, z
+};
+
+template <typename VT>
+__device__ __forceinline__ float trilinear(const VT* __restrict__ vol, const Grid& G, const float gc[3],
+                                           Cell& c)
+{
+    int j[3];
+    float fr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float hi = (float)(G.n[a] - 1);
+        c.in[a] = (gc[a] >= 0.f) && (gc[a] <= hi);
+        const float gg = fminf(fmaxf(gc[a], 0.f), hi);
+        j[a] = min((int)gg, G.n[a] - 2);
+        fr[a] = gg - (float)j[a];
+    }
+    c.fx = fr[0]; c.fy = fr[1]; c.fz = fr[2];
+    const uint32_t sx = 1u, sy = (uint32_t)G.n[0], sz = (uint32_t)G.n[0] * (uint32_t)G.n[1];
+    c.base = (uint32_t)j[0] + sy * (uint32_t)j[1] + sz * (uint32_t)j[2];
+    const VT* p = vol + c.base;
+    c.v[0] = Load<VT>::get(p);
+    c.v[1] = Load<VT>::get(p + sx);
+    c.v[2] = Load<VT>::get(p + sy);
+    c.v[3] = Load<VT>::get(p + sy + sx);
+    c.v[4] = Load<VT>::get(p + sz);
+    c.v[5] = Load<VT>::get(p + sz + sx);
+    c.v[6] = Load<VT>::get(p + sz + sy);
+    c.v[7] = Load<VT>::get(p + sz + sy + sx);
+    const float c00 = fmaf(c.fx, c.v[1] - c.v[0], c.v[0]);
+    const float c10 = fmaf(c.fx, c.v[3] - c.v[2], c.v[2]);
+    const float c01 = fmaf(c.fx, c.v[5] - c.v[4], c.v[4]);
+    const float c11 = fmaf(c.fx, c.v[7] - c.v[6], c.v[6]);
+    const float c0 = fmaf(c.fy, c10 - c00, c00);
+    const float c1 = fmaf(c.fy, c11 - c01, c01);
+    return fmaf(c.fz, c1 - c0, c0);
+}
+
+// d(density)/d(grid coordinate), zero along clamped axes.
+__device__ __forceinline__ void trilinear_grad(const Cell& c, float dg[3])
+{
+    const float e00 = c.v[1] - c.v[0], e10 = c.v[3] - c.v[2];
+    const float e01 = c.v[5] - c.v[4], e11 = c.v[7] - c.v[6];
+    const float ex0 = fmaf(c.fy, e10 - e00, e00);
+    const float ex1 = fmaf(c.fy, e11 - e01, e01);
+    const float gx = fmaf(c.fz, ex1 - ex0, ex0);
+    const float c00 = fmaf(c.fx, e00, c.v[0]);
+    const float c10 = fmaf(c.fx, e10, c.v[2]);
+    const float c01 = fmaf(c.fx, e01, c.v[4]);
+    const float c11 = fmaf(c.fx, e11, c.v[6]);
+    const float gy = fmaf(c.fz, (c11 - c01) - (c10 - c00), c10 - c00);
+    const float c0 = fmaf(c.fy, c10 - c00, c00);
+    const float c1 = fmaf(c.fy, c11 - c01, c01);
+    const float gz = c1 - c0;
+    dg[0] = c.in[0] ? gx : 0.f;
+    dg[1] = c.in[1] ? gy : 0.f;
+    dg[2] = c.in[2] ? gz : 0.f;
+}
+
+// f_TF from the shared-memory copy: R rows at densities r/(R-1), linear in
+// between, density clamped to [0, 1].
+struct TFSample {
+    float4 c;                        // r, g, b, tau
+    int k;
+    float fr;
+    bool slope;
+};
+
+__device__ __forceinline__ void tf_lookup(const float4* __restrict__ tf, int R, float d, TFSample& s)
+{
+    s.slope = (d >= 0.f) && (d <= 1.f);
+    const float dc = fminf(fmaxf(d, 0.f), 1.f);
+    const float u = dc * (float)(R - 1);
+    s.k = min((int)u, R - 2);
+    s.fr = u - (float)s.k;
+    const float4 a = tf[s.k];
+    const float4 b = tf[s.k + 1];
+    s.c.x = fmaf(s.fr, b.x - a.x, a.x);
+    s.c.y = fmaf(s.fr, b.y - a.y, a.y);
+    s.c.z = fmaf(s.fr, b.z - a.z, a.z);
+    s.c.w = fmaf(s.fr, b.w - a.w, a.w);
+}
+
+// Stage the TF (float or half rows) into shared memory as float4.
+__device__ __forceinline__ void stage_tf(const Params& p, float4* tf_s)
+{
+    for (int r = threadIdx.x; r < p.R; r += blockDim.x) {
+        float4 v;
+        if (p.tf_dtype == DVR_F32) {
+            v = __ldg(reinterpret_cast<const float4*>(p.tf) + r);
+        } else {
+            const __half* h = reinterpret_cast<const __half*>(p.tf) + 4 * r;
+            v = make_float4(__half2float(h[0]), __half2float(h[1]), __half2float(h[2]),
+                            __half2float(h[3]));
+        }
+        tf_s[r] = v;
+    }
+}
+
+// Warp tile -> (view, pixel) mapping.
+__device__ __forceinline__ int find_view(const Params& p, int tile)
+{
+    int lo = 0, hi = p.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.tile_start[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace dvr

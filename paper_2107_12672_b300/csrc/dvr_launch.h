@@ -1,0 +1,25 @@
+// Host-side launchers of the renderer's kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dvr_device.cuh"
+
+namespace dvr {
+
+// Variants of the adjoint kernel (template parameters, Sec. 4.4).
+enum TFMode { kTFNone = 0, kTFDelayed = 1, kTFImmediate = 2 };
+
+cudaError_t launch_forward(const Params& p, int model, int vol_dtype, cudaStream_t stream);
+cudaError_t launch_backward(const Params& p, int model, int vol_dtype, bool grad_volume,
+                            int tf_mode, bool grad_position, cudaStream_t stream);
+cudaError_t launch_loss_l2(const float* image, const float* target, long long n, float scale,
+                           float* grad_image, float* loss, cudaStream_t stream);
+cudaError_t launch_orbit_eye(const float* params, int n, float* eye, cudaStream_t stream);
+cudaError_t launch_orbit_eye_backward(const float* params, const float* grad_eye, int n,
+                                      float* grad_params, cudaStream_t stream);
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+}  // namespace dvr

@@ -1,0 +1,131 @@
+"""The C-ABI library: it loads, exports every symbol include/dvr.h declares,
+its ctypes mirror matches the header's struct layout, and argument errors
+are reported without touching a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2107_12672_b300 import _abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dvr.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"DVR_API\s+[\w\s\*]+?\b(dvr_\w+)\s*\(", src)))
+
+
+def test_header_declares_what_binding_lists():
+    assert _declared() == sorted(_abi.SYMBOLS)
+
+
+def test_library_loads_and_exports_every_symbol():
+    lib = _abi.load()
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert lib.dvr_abi_version() == 1
+    out = subprocess.run(["nm", "-D", "--defined-only", _abi.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (dvr_\w+)", out))
+    assert set(_declared()) <= exported
+    # everything else stays hidden
+    assert exported == set(_declared())
+
+
+def test_struct_layout_matches_header(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "dvr.h"\n'
+        "int main(void){\n"
+        'printf("%zu %zu %zu\\n", sizeof(dvr_volume), offsetof(dvr_volume, dtype), offsetof(dvr_volume, data));\n'
+        'printf("%zu %zu\\n", sizeof(dvr_tf), offsetof(dvr_tf, rgba));\n'
+        'printf("%zu %zu %zu %zu\\n", sizeof(dvr_view), offsetof(dvr_view, volume), offsetof(dvr_view, lens),'
+        " offsetof(dvr_view, pixel_offset));\n"
+        "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    lines = subprocess.check_output([str(exe)], text=True).split("\n")
+    V, T, W = _abi.DvrVolume, _abi.DvrTF, _abi.DvrView
+    assert lines[0].split() == [str(ctypes.sizeof(V)), str(V.dtype.offset), str(V.data.offset)]
+    assert lines[1].split() == [str(ctypes.sizeof(T)), str(T.rgba.offset)]
+    assert lines[2].split() == [str(ctypes.sizeof(W)), str(W.volume.offset), str(W.lens.offset),
+                                str(W.pixel_offset.offset)]
+
+
+def _call_forward(vols, nvol, tf, model, views, nviews, eye=1, step=0.5, image=16):
+    lib = _abi.load()
+    return lib.dvr_forward(vols, nvol, tf, model, views, nviews, eye, step, image, None, None, None)
+
+
+def _one_volume(nx=8, dtype=_abi.DVR_F32, data=4096):
+    v = (_abi.DvrVolume * 1)()
+    v[0] = _abi.DvrVolume(nx, nx, nx, dtype, data)
+    return v
+
+
+def _one_view(w=4, h=4, volume=0, lens=0.4, ortho=0):
+    a = (_abi.DvrView * 1)()
+    a[0] = _abi.DvrView(w, h, ortho, volume, lens, 0, 0)
+    return a
+
+
+@pytest.mark.parametrize("case,code", [
+    ("null_volumes", _abi.DVR_OK - 1),
+    ("bad_model", -1),
+    ("small_volume", -1),
+    ("bad_dtype", -2),
+    ("bad_view_volume", -1),
+    ("bad_lens", -1),
+    ("tiny_step", -1),
+    ("null_image", -1),
+    ("ea_without_tf", -1),
+    ("misaligned_image", -1),
+])
+def test_argument_errors_need_no_gpu(case, code):
+    """Invalid arguments are rejected on the host before any CUDA call."""
+    vols, view = _one_volume(), _one_view()
+    lib = _abi.load()
+    if case == "null_volumes":
+        rc = _call_forward(None, 1, None, 0, view, 1)
+    elif case == "bad_model":
+        rc = _call_forward(vols, 1, None, 7, view, 1)
+    elif case == "small_volume":
+        rc = _call_forward(_one_volume(nx=1), 1, None, 0, view, 1)
+    elif case == "bad_dtype":
+        rc = _call_forward(_one_volume(dtype=9), 1, None, 0, view, 1)
+    elif case == "bad_view_volume":
+        rc = _call_forward(vols, 1, None, 0, _one_view(volume=3), 1)
+    elif case == "bad_lens":
+        rc = _call_forward(vols, 1, None, 0, _one_view(lens=-1.0), 1)
+    elif case == "tiny_step":
+        rc = _call_forward(vols, 1, None, 0, view, 1, step=1e-6)
+    elif case == "null_image":
+        rc = _call_forward(vols, 1, None, 0, view, 1, image=None)
+    elif case == "ea_without_tf":
+        rc = _call_forward(vols, 1, None, 1, view, 1)
+    elif case == "misaligned_image":
+        tf = _abi.DvrTF(4, 0, 4096)
+        rc = _call_forward(vols, 1, ctypes.byref(tf), 1, view, 1, image=4100)
+    assert rc == code
+    assert lib.dvr_last_error().decode()
+
+
+def test_backward_rejects_unknown_flags():
+    lib = _abi.load()
+    rc = lib.dvr_backward(_one_volume(), 1, None, 0, _one_view(), 1, 16, 0.5, 64, 64, None, None,
+                          None, None, 0x80, None)
+    assert rc == -1 and b"flag" in lib.dvr_last_error()
+
+
+def test_no_oracle_in_the_product_path():
+    """The library and its binding never import, load or include the oracle."""
+    pkg = os.path.join(ROOT, "paper_2107_12672_b300")
+    banned = re.compile(r"(import\s+oracle|from\s+oracle|liboracle|dvr_oracle|ora_\w+\()")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not banned.search(text), f

@@ -1,0 +1,275 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Inputs come from the seeded generators only; the adjoint seeds dL/d(image)
+are seeded random arrays given to both sides. Tolerances (per element,
+relative to the element or to the array's scale): images 1e-5, gradients
+1e-3. Sample counts are integers decided by the same binary32 ray setup on
+both sides and must match exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2107_12672_b300 as dvr
+from paper_2107_12672_b300 import synthetic as syn
+from tests.gpu_helpers import (GRAD_RTOL, IMAGE_RTOL, as_oracle_volume, assert_close, pixel_offsets,
+                               seeded_grad_image, to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_gpu(w, vol_dtype=torch.float32, tf_dtype=torch.float32, grad_seed=5, want=("volume", "tf", "eye"),
+             tf_immediate=False):
+    vols = [to_dev(v, vol_dtype) for v in w.volumes]
+    tf = to_dev(w.tf, tf_dtype) if w.tf is not None else None
+    eye = to_dev(w.eye)
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    img, aux = dvr.forward(vols, tf, w.model, w.views, eye, w.step_voxels, sample_count=count)
+    nc = img.shape[1]
+    G = seeded_grad_image(img.shape[0], nc, grad_seed)
+    g = dvr.backward(vols, tf, w.model, w.views, eye, w.step_voxels, aux, to_dev(G), want=want,
+                     tf_immediate=tf_immediate)
+    torch.cuda.synchronize()
+    return vols, tf, img.cpu().numpy(), int(count.item()), G, g
+
+
+def _oracle(w, vols, tf, G, want=("volume", "tf", "eye")):
+    vols64 = [as_oracle_volume(v) for v in vols]
+    tf64 = as_oracle_volume(tf) if tf is not None else None
+    offs, P = pixel_offsets(w.views)
+    nc = 4 if w.model == "emission_absorption" else 1
+    img = np.zeros((P, nc))
+    Ntot = 0
+    gv = [np.zeros(v.shape) for v in vols64]
+    gt = np.zeros_like(tf64) if tf64 is not None else None
+    ge = np.zeros((len(w.views), 3))
+    for k, view in enumerate(w.views):
+        n = view.width * view.height
+        vol = vols64[view.volume_index]
+        im, N, _ = oracle.render(vol, tf64, w.model, view, w.eye[k], w.step_voxels)
+        img[offs[k]:offs[k] + n] = im
+        Ntot += int(N.sum())
+        ow = tuple(x for x in want if x != "step")
+        g = oracle.backward(vol, tf64, w.model, view, w.eye[k], w.step_voxels, G[offs[k]:offs[k] + n], want=ow)
+        if "volume" in g:
+            gv[view.volume_index] += g["volume"]
+        if "tf" in g and gt is not None:
+            gt += g["tf"]
+        if "eye" in g:
+            ge[k] = g["eye"]
+    return img, Ntot, {"volume": gv, "tf": gt, "eye": ge}
+
+
+def _compare(w, gpu, ref, want, image_rtol=IMAGE_RTOL, grad_rtol=GRAD_RTOL):
+    vols, tf, img, count, G, g = gpu
+    rimg, rN, rg = ref
+    assert count == rN, "sample counts differ: the ray setup is not bit-identical"
+    errs = {"image": assert_close(img, rimg, image_rtol, "image")}
+    if "volume" in want:
+        for i, (a, b) in enumerate(zip(g["volume"], rg["volume"])):
+            errs[f"volume{i}"] = assert_close(a.cpu().numpy(), b, grad_rtol, f"grad volume {i}")
+    if "tf" in want and tf is not None:
+        errs["tf"] = assert_close(g["tf"].cpu().numpy(), rg["tf"], grad_rtol, "grad tf")
+    if "eye" in want:
+        errs["eye"] = assert_close(g["eye"].cpu().numpy(), rg["eye"], grad_rtol, "grad eye")
+    return errs
+
+
+# ------------------------------------------------------------------ workloads
+def test_absorption_64_full_size():
+    """64^3 Gaussian blobs, ortho +z, 64x64, step 0.5: image and the
+    gradient w.r.t. all 262144 densities at full size."""
+    w = syn.workload("absorption_64")
+    want = ("volume", "eye")
+    gpu = _run_gpu(w, want=want)
+    ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
+    _compare(w, gpu, ref, want)
+
+
+@pytest.mark.parametrize("scale,size", [(0.25, None), (0.25, (131, 97)), (0.125, (8, 4)), (0.125, (1, 1))])
+def test_ea_reduced(scale, size):
+    """Emission-absorption value noise with a 16-row TF and a perspective
+    camera, at sizes spanning several tiles and ragged tails."""
+    w = syn.workload("ea_256", scale=scale)
+    if size is not None:
+        w.views = [syn.View(size[0], size[1])]
+    want = ("volume", "tf", "eye")
+    gpu = _run_gpu(w, want=want)
+    ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
+    _compare(w, gpu, ref, want)
+
+
+def test_ea_256_full_size():
+    """The 256^3 / 512^2 emission-absorption workload at full size: every
+    pixel, and the TF and eye gradients (global sums over all rays)."""
+    w = syn.workload("ea_256")
+    want = ("tf", "eye")
+    gpu = _run_gpu(w, want=want)
+    ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
+    _compare(w, gpu, ref, want)
+
+
+def test_multiview_uneven_one_launch():
+    """64 Fibonacci views of uneven sizes and two volumes in one launch."""
+    w = syn.workload("tomo_256x64", scale=1 / 16)
+    w.volumes.append(syn.gaussian_blobs(w.volumes[0].shape[0], 4, seed=44))
+    for k, v in enumerate(w.views):
+        v.volume_index = k % 2
+    want = ("volume", "eye")
+    gpu = _run_gpu(w, want=want)
+    ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
+    _compare(w, gpu, ref, want)
+
+
+@pytest.mark.parametrize("vdt,tdt", [(torch.bfloat16, torch.float16), (torch.float16, torch.float32)])
+def test_reduced_precision_storage(vdt, tdt):
+    """BF16/FP16 volume and FP16 TF storage with FP32 arithmetic: the oracle
+    takes the same rounded values, so FP32 tolerances hold."""
+    w = syn.workload("ea_bf16_512", scale=1 / 8)
+    w.views = w.views[:3]
+    w.eye = w.eye[:3]
+    want = ("volume", "tf", "eye")
+    gpu = _run_gpu(w, vol_dtype=vdt, tf_dtype=tdt, want=want)
+    ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
+    _compare(w, gpu, ref, want)
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("eye,ortho", [
+    ((0.0, 2.4, 0.0), False),          # looking straight down -y: fixed right vector
+    ((0.12, -0.08, 0.2), False),       # camera inside the volume
+    ((0.0, 0.0, 3.0), True),           # axis-aligned ortho: N exactly integral
+    ((5.0, 0.0, 0.0), False),          # far camera, grazing rays at the box faces
+    ((0.0, 0.0, -0.9), True),          # ortho from -z
+])
+def test_camera_edge_cases(eye, ortho):
+    w = syn.workload("ea_256", scale=0.0625)
+    w.views = [syn.View(37, 29, ortho=ortho, ortho_height=1.2)]
+    w.eye = np.array([eye], dtype=np.float32)
+    want = ("volume", "tf", "eye")
+    gpu = _run_gpu(w, want=want)
+    ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
+    _compare(w, gpu, ref, want)
+
+
+def test_rays_that_miss_the_volume():
+    """An orthographic image plane four times wider than the box: most rays
+    miss (N = 0, zero pixel, no gradient), the rest match the oracle."""
+    w = syn.workload("ea_256", scale=0.0625)
+    w.views = [syn.View(24, 20, ortho=True, ortho_height=4.0)]
+    w.eye = np.array([[0.3, 0.2, 2.5]], dtype=np.float32)
+    want = ("volume", "tf", "eye")
+    gpu = _run_gpu(w, want=want)
+    ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
+    _compare(w, gpu, ref, want)
+    img = gpu[2]
+    assert (np.abs(img).sum(1) == 0).mean() > 0.5
+
+
+def test_tf_immediate_equals_delayed():
+    """The adjoint-immediate and adjoint-delayed TF accumulations (Sec. 5.2)
+    give the same gradient."""
+    w = syn.workload("ea_256", scale=0.125)
+    a = _run_gpu(w, want=("tf",))
+    b = _run_gpu(w, want=("tf",), tf_immediate=True)
+    assert_close(b[5]["tf"].cpu().numpy(), a[5]["tf"].cpu().numpy(), 1e-5, "immediate vs delayed")
+
+
+def test_step_gradient():
+    """dL/d(step_voxels) against central differences of the oracle (N fixed)."""
+    w = syn.workload("ea_256", scale=0.125)
+    step = 0.53
+    w.step_voxels = step
+    vols = [to_dev(w.volumes[0])]
+    tf = to_dev(w.tf)
+    eye = to_dev(w.eye)
+    img, aux = dvr.forward(vols, tf, w.model, w.views, eye, step)
+    G = seeded_grad_image(img.shape[0], 4, 9)
+    g = dvr.backward(vols, tf, w.model, w.views, eye, step, aux, to_dev(G), want=("step",))
+    gs = float(g["step"].item())
+    ref = oracle.backward(as_oracle_volume(vols[0]), as_oracle_volume(tf), w.model, w.views[0], w.eye[0],
+                          step, G, want=("step",))["step"]
+    assert abs(gs - ref) <= GRAD_RTOL * abs(ref)
+
+
+def test_orbit_camera_kernels():
+    rng = np.random.default_rng(0)
+    prm = np.stack([rng.uniform(-3, 3, 50), rng.uniform(-1.4, 1.4, 50), rng.uniform(1, 4, 50)], 1)
+    prm = prm.astype(np.float32)
+    eye = dvr.orbit_eye(to_dev(prm)).cpu().numpy()
+    np.testing.assert_allclose(eye, oracle.orbit_eye(prm), rtol=2e-6, atol=2e-6)
+    ge = rng.normal(size=(50, 3)).astype(np.float32)
+    gp = dvr.orbit_eye_backward(to_dev(prm), to_dev(ge)).cpu().numpy()
+    np.testing.assert_allclose(gp, oracle.orbit_eye_backward(prm, ge), rtol=1e-5, atol=2e-5)
+
+
+def test_loss_l2_kernel():
+    rng = np.random.default_rng(1)
+    for n in (1, 7, 4096, 100003):
+        x = rng.normal(size=n).astype(np.float32)
+        y = rng.normal(size=n).astype(np.float32)
+        loss = torch.zeros(1, device="cuda")
+        g = dvr.loss_l2(to_dev(x), to_dev(y), 0.25, loss=loss).cpu().numpy()
+        np.testing.assert_allclose(g, 0.5 * (x.astype(np.float64) - y), rtol=1e-6, atol=1e-7)
+        ref = 0.25 * ((x.astype(np.float64) - y) ** 2).sum()
+        assert abs(loss.item() - ref) <= 1e-5 * ref
+
+
+def test_autograd_render_matches_raw_backward():
+    """render() as a torch.autograd.Function: gradients equal dvr.backward."""
+    w = syn.workload("ea_256", scale=0.125)
+    vol = to_dev(w.volumes[0]).requires_grad_(True)
+    tf = to_dev(w.tf).requires_grad_(True)
+    eye = to_dev(w.eye).requires_grad_(True)
+    img = dvr.render(vol, tf, eye, w.views, w.step_voxels, w.model)
+    G = to_dev(seeded_grad_image(img.shape[0], 4, 3))
+    (img * G).sum().backward()
+    _, aux = dvr.forward([vol.detach()], tf.detach(), w.model, w.views, eye.detach(), w.step_voxels)
+    g = dvr.backward([vol.detach()], tf.detach(), w.model, w.views, eye.detach(), w.step_voxels, aux, G)
+    for a, b in ((vol.grad, g["volume"][0]), (tf.grad, g["tf"]), (eye.grad, g["eye"])):
+        assert_close(a.cpu().numpy(), b.cpu().numpy(), 1e-5, "autograd")
+
+
+def test_orbit_chain_gradient():
+    """Gradient w.r.t. (yaw, pitch, distance) through the orbit kernels and the
+    renderer, against the oracle's chain of the same two maps. The eye is
+    rounded differently on both sides, so a ray whose N sits on a rounding
+    boundary may differ; the camera gradient sums all rays and stays within
+    the gradient tolerance."""
+    w = syn.workload("ea_256", scale=0.25)
+    prm = to_dev(w.orbit.astype(np.float32)).requires_grad_(True)
+    vol = to_dev(w.volumes[0])
+    tf = to_dev(w.tf)
+    eye = dvr.orbit_camera(prm)
+    img = dvr.render(vol, tf, eye, w.views, w.step_voxels, w.model)
+    G = seeded_grad_image(img.shape[0], 4, 21)
+    (img * to_dev(G)).sum().backward()
+    p64 = w.orbit.astype(np.float32).astype(np.float64)
+    e64 = oracle.orbit_eye(p64)[0]
+    ge = oracle.backward(as_oracle_volume(vol), as_oracle_volume(tf), w.model, w.views[0], e64,
+                         w.step_voxels, G, fp32=False, want=("eye",))["eye"]
+    ref = oracle.orbit_eye_backward(p64, ge[None])[0]
+    assert_close(prm.grad.cpu().numpy()[0], ref, GRAD_RTOL, "orbit chain")
+
+
+def test_memory_constant_in_step_count():
+    """The adjoint keeps no per-step state: peak device memory of a
+    forward+backward is the same at step 0.5, 0.25 and 0.125 voxel."""
+    w = syn.workload("ea_256", scale=0.25)
+    vols = [to_dev(w.volumes[0])]
+    tf = to_dev(w.tf)
+    eye = to_dev(w.eye)
+    peaks = []
+    for step in (0.5, 0.25, 0.125):
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        img, aux = dvr.forward(vols, tf, w.model, w.views, eye, step)
+        G = torch.ones_like(img)
+        dvr.backward(vols, tf, w.model, w.views, eye, step, aux, G, want=("volume", "tf", "eye"))
+        torch.cuda.synchronize()
+        peaks.append(torch.cuda.max_memory_allocated())
+        del img, aux, G
+    assert peaks[0] == peaks[1] == peaks[2]
