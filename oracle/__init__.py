@@ -55,7 +55,7 @@ def _load():
         lib.ora_render.argtypes = [P, I, I, I, P, I, I, I, I, I, D, P, D, I, P, L, P, P, P]
         lib.ora_rays.argtypes = [I, I, I, I, I, I, D, P, D, I, P, P, P]
         lib.ora_interpolate.argtypes = [P, I, I, I, P, L, P]
-        lib.ora_backward.argtypes = [P, I, I, I, P, I, I, I, I, I, D, P, D, I, P, L, P, I, P, P, P, P]
+        lib.ora_backward.argtypes = [P, I, I, I, P, I, I, I, I, I, D, P, D, I, P, L, P, I, P, P, P, P, D, P, P]
         lib.ora_render_dual.argtypes = [P, I, I, I, P, I, I, I, I, I, D, P, D, P, L, P, P]
         lib.ora_orbit_eye.argtypes = [P, L, P]
         lib.ora_orbit_eye_backward.argtypes = [P, L, P, P]
@@ -135,10 +135,18 @@ def render(volume, tf, model, view, eye, step, fp32=True, pix=None):
 
 
 def backward(volume, tf, model, view, eye, step, grad_image, fp32=True, pix=None,
-             invert=False, want=("volume", "tf", "eye", "step")):
+             invert=False, want=("volume", "tf", "eye", "step"), margin=0.0):
     """Alg. 2 for one view with the stored-state tape (invert=False) or the
     inversion of Eq. inv-blend-forward (invert=True). Returns a dict of
-    binary64 gradients for the requested parameters."""
+    binary64 gradients for the requested parameters.
+
+    With margin > 0, ambiguity bounds for a binary32 evaluation of the
+    same samples (the kernel's precision) are returned as
+    out["volume_ambiguity"] (per voxel) and out["eye_ambiguity"] (3): how
+    far a correct gradient may move when samples closer to a kink of the
+    piecewise-linear TF, or to a cell face, than binary32 rounding (times
+    `margin`) take the other one-sided derivative.
+    """
     c = _Common(volume, tf, model, view, eye, step, fp32)
     p, n = _pix(pix)
     total = n if p is not None else c.W * c.H
@@ -148,8 +156,14 @@ def backward(volume, tf, model, view, eye, step, grad_image, fp32=True, pix=None
     gt = np.zeros((c.R, 4)) if ("tf" in want and c.model == EMISSION_ABSORPTION) else None
     ge = np.zeros(3) if "eye" in want else None
     gs = np.zeros(1) if "step" in want else None
+    amb = np.zeros_like(c.vol) if (gv is not None and margin > 0) else None
+    amb_e = np.zeros(3) if (ge is not None and margin > 0) else None
     _load().ora_backward(*c.head(), c.fp32, _p(p), n, _p(gi), int(bool(invert)),
-                         _p(gv), _p(gt), _p(ge), _p(gs))
+                         _p(gv), _p(gt), _p(ge), _p(gs), float(margin), _p(amb), _p(amb_e))
+    if amb is not None:
+        out["volume_ambiguity"] = amb
+    if amb_e is not None:
+        out["eye_ambiguity"] = amb_e
     if gv is not None:
         out["volume"] = gv
     if gt is not None:

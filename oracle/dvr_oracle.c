@@ -256,7 +256,29 @@ typedef struct {
     double wt[8], dg[3];
     int k, slope;
     double fr;
+    double ge;        /* binary32 error bound of the grid coordinates (ambiguity bounds only) */
 } sample_t;
+
+static double grid_error(const void* smp, const grid_t* G, double margin)
+{
+    const sample_t* sm = (const sample_t*)smp;
+    double gmax = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        double g = fabs((sm->x[a] + G->half[a]) * G->inv_h);
+        if (g > gmax) gmax = g;
+    }
+    return margin * ldexp(1.0, ilogb(gmax) - 23);
+}
+
+static double density_error(const void* smp, const double* V, double margin)
+{
+    const sample_t* sm = (const sample_t*)smp;
+    double vmax = 0.0, gsum = 0.0;
+    for (int c = 0; c < 8; ++c)
+        if (fabs(V[sm->idx[c]]) > vmax) vmax = fabs(V[sm->idx[c]]);
+    for (int a = 0; a < 3; ++a) gsum += fabs(sm->dg[a]);
+    return gsum * sm->ge + margin * 4.0 * 0x1p-24 * vmax;
+}
 
 static void eval_sample(const scene_t* s, const ray_t* ry, int i, sample_t* sm)
 {
@@ -376,6 +398,59 @@ int ora_interpolate(const double* V, int nx, int ny, int nz, const double* x, in
     return 0;
 }
 
+/*
+ * For each axis a where the grid coordinate of x lies within `delta` of an
+ * integer (a face between two cells, or a box face where the coordinate is
+ * clamped), the jump of d(density)/d(g_a) across that face; 0 elsewhere.
+ */
+static void face_jumps(const double* V, const grid_t* G, const double x[3], double delta, double jump[3])
+{
+    double g[3];
+    for (int a = 0; a < 3; ++a) g[a] = (x[a] + G->half[a]) * G->inv_h;
+    for (int a = 0; a < 3; ++a) {
+        jump[a] = 0.0;
+        double f = floor(g[a] + 0.5);
+        if (fabs(g[a] - f) >= delta) continue;
+        int face = (int)f;            /* vertex index of the face along axis a */
+        double slope[2];              /* normal derivative in cells face-1 and face */
+        for (int sd = 0; sd < 2; ++sd) {
+            int cell = face - 1 + sd;
+            if (cell < 0 || cell > G->n[a] - 2) { slope[sd] = 0.0; continue; }
+            /* other two axes: trilinear weights at x (clamped) */
+            double pt[3] = {x[0], x[1], x[2]};
+            int j[3];
+            double fr[3];
+            for (int b = 0; b < 3; ++b) {
+                double gb = (pt[b] + G->half[b]) * G->inv_h;
+                if (gb < 0.0) gb = 0.0;
+                if (gb > (double)(G->n[b] - 1)) gb = (double)(G->n[b] - 1);
+                int jj = (int)floor(gb);
+                if (jj > G->n[b] - 2) jj = G->n[b] - 2;
+                j[b] = jj;
+                fr[b] = gb - (double)jj;
+            }
+            j[a] = cell;
+            double sum = 0.0;
+            for (int c = 0; c < 8; ++c) {
+                int bb[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+                double w = bb[a] ? 1.0 : -1.0;
+                for (int o = 0; o < 3; ++o)
+                    if (o != a) w *= bb[o] ? fr[o] : 1.0 - fr[o];
+                long idx = ((long)(j[2] + bb[2]) * G->n[1] + (j[1] + bb[1])) * (long)G->n[0] + (j[0] + bb[0]);
+                sum += w * V[idx];
+            }
+            slope[sd] = sum;
+        }
+        jump[a] = fabs(slope[1] - slope[0]);
+    }
+}
+
+/* binary32 error bound of a sample's grid coordinates: one ulp of the
+ * largest coordinate (times margin). */
+static double grid_error(const void* smp, const grid_t* G, double margin);
+/* binary32 error bound of a sample's density. */
+static double density_error(const void* smp, const double* V, double margin);
+
 static inline void atomic_add(double* p, double v)
 {
 #pragma omp atomic
@@ -448,10 +523,25 @@ static void camera_adjoint(const cam_t* c, const ray_t* r, const double xo_hat[3
  * invert = 1: it is reconstructed from (A_{i+1}, C_{i+1}) with
  *             Eq. inv-blend-forward (paper's alpha form).
  */
+/*
+ * margin > 0: ambiguity bounds for a binary32 evaluation of the same
+ * samples. f_TF is piecewise linear, so d(f_TF)/dd jumps at every control
+ * point (and at the clamp ends 0 and 1), and the normal derivative of the
+ * trilinear density jumps at every cell face. A binary32 evaluation puts
+ * the grid coordinate g within one ulp of max|g| (the double-float sample
+ * positions round twice by half an ulp), the density within |grad d| times
+ * that plus four ulps of the largest corner value, and u = d (R-1) within
+ * one more ulp; `margin` multiplies these error bounds. A sample closer to
+ * a kink than its bound may legitimately take either one-sided derivative:
+ *   amb_vol: w_c * |d^_left - d^_right| summed at its 8 corners (TF kinks);
+ *   amb_eye: the change of x^_i from either kind of kink, chained through
+ *            the camera adjoint, summed in absolute value.
+ */
 int ora_backward(const double* V, int nx, int ny, int nz, const double* tf, int R, int model,
                  int W, int H, int ortho, double lens, const double* eye, double step, int fp32,
                  const int64_t* pix, int64_t npix, const double* grad_image, int invert,
-                 double* grad_vol, double* grad_tf, double* grad_eye, double* grad_step)
+                 double* grad_vol, double* grad_tf, double* grad_eye, double* grad_step,
+                 double margin, double* amb_vol, double* amb_eye)
 {
     scene_t s;
     setup_scene(&s, V, nx, ny, nz, tf, R, model, W, H, ortho, lens, eye, step, fp32);
@@ -460,7 +550,7 @@ int ora_backward(const double* V, int nx, int ny, int nz, const double* tf, int 
     const double dt = s.G.dt;
 #pragma omp parallel
     {
-        double eye_acc[3] = {0, 0, 0}, step_acc = 0.0;
+        double eye_acc[3] = {0, 0, 0}, step_acc = 0.0, amb_acc[3] = {0, 0, 0};
         /* per-thread TF sums, added to grad_tf once at the end */
         double* tf_acc = grad_tf ? (double*)calloc((size_t)4 * R, sizeof(double)) : NULL;
         double* tapeA = NULL;
@@ -493,6 +583,7 @@ int ora_backward(const double* V, int nx, int ny, int nz, const double* tf, int 
             sample_t sm;
             for (int i = ry.N - 1; i >= 0; --i) {
                 eval_sample(&s, &ry, i, &sm);
+                sm.ge = margin > 0.0 ? grid_error(&sm, &s.G, margin) : 0.0;
                 double A0, C0[3];
                 double Cs[3];
                 for (int ch = 0; ch < 3; ++ch) Cs[ch] = sm.alpha * sm.c[ch];
@@ -523,7 +614,7 @@ int ora_backward(const double* V, int nx, int ny, int nz, const double* tf, int 
                 dt_hat += a_hat * sm.tau * e;
                 c_hat[3] = tau_hat;
                 /* f_TF adjoint */
-                double d_hat;
+                double d_hat, d_jump = 0.0;
                 if (model == ORA_EMISSION_ABSORPTION) {
                     if (tf_acc) {
                         for (int ch = 0; ch < 4; ++ch) {
@@ -535,6 +626,25 @@ int ora_backward(const double* V, int nx, int ny, int nz, const double* tf, int 
                     if (sm.slope)
                         for (int ch = 0; ch < 4; ++ch)
                             d_hat += (double)(R - 1) * (tf[4 * (sm.k + 1) + ch] - tf[4 * sm.k + ch]) * c_hat[ch];
+                    if ((amb_vol || amb_eye) && margin > 0.0) {
+                        double u = sm.d * (double)(R - 1);
+                        double kn = floor(u + 0.5);
+                        double eu = (R - 1) * density_error(&sm, V, margin) + margin * 0x1p-23 * fabs(u);
+                        if (kn >= 0.0 && kn <= (double)(R - 1) && fabs(u - kn) < eu) {
+                            int knot = (int)kn;
+                            double side[2] = {0.0, 0.0};   /* segments knot-1 and knot */
+                            for (int sd = 0; sd < 2; ++sd) {
+                                int seg = knot - 1 + sd;
+                                if (seg < 0 || seg > R - 2) continue;
+                                for (int ch = 0; ch < 4; ++ch)
+                                    side[sd] += (double)(R - 1) * (tf[4 * (seg + 1) + ch] - tf[4 * seg + ch]) * c_hat[ch];
+                            }
+                            double jump = fabs(side[1] - side[0]);
+                            d_jump = jump;
+                            if (amb_vol)
+                                for (int c = 0; c < 8; ++c) atomic_add(&amb_vol[sm.idx[c]], sm.wt[c] * jump);
+                        }
+                    }
                 } else {
                     d_hat = tau_hat;
                 }
@@ -550,6 +660,29 @@ int ora_backward(const double* V, int nx, int ny, int nz, const double* tf, int 
                     xi_w += (double)i * ry.w[a] * x_hat;
                 }
                 dt_hat += xi_w;
+                if (amb_eye && margin > 0.0) {
+                    /* change of x^_i if the TF kink or a cell face is taken
+                     * from the other side */
+                    double dx[3];
+                    int any = 0;
+                    double dgn[3];
+                    face_jumps(V, &s.G, sm.x, sm.ge, dgn);
+                    for (int a = 0; a < 3; ++a) {
+                        dx[a] = (fabs(sm.dg[a] * d_jump) + fabs(dgn[a] * d_hat)) * s.G.inv_h;
+                        any |= dx[a] != 0.0;
+                    }
+                    if (any) {
+                        /* the camera adjoint is linear: bound each axis' part */
+                        for (int a = 0; a < 3; ++a) {
+                            if (dx[a] == 0.0) continue;
+                            double xo1[3] = {0, 0, 0}, w1[3] = {0, 0, 0}, eh[3];
+                            xo1[a] = dx[a];
+                            w1[a] = ti * dx[a];
+                            camera_adjoint(&s.cam, &ry, xo1, w1, eh);
+                            for (int b = 0; b < 3; ++b) amb_acc[b] += fabs(eh[b]);
+                        }
+                    }
+                }
                 A1 = A0;
                 for (int ch = 0; ch < 3; ++ch) C1[ch] = C0[ch];
             }
@@ -562,6 +695,8 @@ int ora_backward(const double* V, int nx, int ny, int nz, const double* tf, int 
         }
         if (grad_eye)
             for (int a = 0; a < 3; ++a) atomic_add(&grad_eye[a], eye_acc[a]);
+        if (amb_eye)
+            for (int a = 0; a < 3; ++a) atomic_add(&amb_eye[a], amb_acc[a]);
         if (tf_acc) {
             for (int j = 0; j < 4 * R; ++j) atomic_add(&grad_tf[j], tf_acc[j]);
             free(tf_acc);

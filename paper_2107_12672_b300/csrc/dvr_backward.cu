@@ -11,10 +11,17 @@
 // colour adjoint is constant along the ray (Eq. adj-blend-forward).
 //
 // Gradients (all "+=", Alg. 2):
-//  - TF: per-warp shared-memory copies, summed per block and added to
-//    global memory once per block ("adjoint-delayed", Sec. 5.2), or one
-//    global atomic per sample ("adjoint-immediate");
-//  - volume: 8 corner weights times d^ per sample, global atomic adds;
+//  - TF ("adjoint-delayed", Sec. 5.2): for R <= 32 every lane owns a copy
+//    of the TF gradient in shared memory, laid out [row][channel][lane] so
+//    that the per-sample updates are conflict-free plain adds; for larger R
+//    each lane sums in registers while its samples stay in one TF segment
+//    and adds the sums to a per-warp copy with shared atomics when the
+//    segment changes. The copies are summed per block and added to global
+//    memory once per block. The ablation "adjoint-immediate" adds every
+//    sample's contribution to global memory directly;
+//  - volume: the 8 corner contributions are summed in registers while the
+//    ray stays in one cell and added to global memory with atomics when it
+//    leaves the cell (Sec. 4.4: "on exit of the current cell");
 //  - eye / step: x^_o, w^ summed in registers along the ray (Alg. 2 last
 //    loop line), chained through f_camera per ray, warp-reduced, one atomic
 //    per warp.
@@ -87,31 +94,77 @@ __device__ __forceinline__ void camera_adjoint(const Ray& R, int ortho, const fl
     for (int a = 0; a < 3; ++a) e_hat[a] -= (f_hat[a] - R.f[a] * ff) * inv;
 }
 
+// Register run of TF-gradient contributions: rows k (weight 1 - fr) and
+// k + 1 (weight fr), channels r, g, b, tau.
+struct TFRun {
+    int k;
+    float a[8];
+};
+
+__device__ __forceinline__ void tf_run_flush(float* rows, TFRun& r)
+{
+    if (r.k >= 0) {
+        float* b = rows + 4 * r.k;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) atomicAdd(b + j, r.a[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r.a[j] = 0.f;
+}
+
+// Register run of volume-gradient contributions to the 8 corners of one cell.
+struct CellRun {
+    uint32_t base;
+    float a[8];
+};
+
+__device__ __forceinline__ void cell_run_flush(float* g, uint32_t sy, uint32_t sz, CellRun& r)
+{
+    if (r.base != 0xffffffffu) {
+        float* q = g + r.base;
+        atomicAdd(q, r.a[0]);
+        atomicAdd(q + 1, r.a[1]);
+        atomicAdd(q + sy, r.a[2]);
+        atomicAdd(q + sy + 1, r.a[3]);
+        atomicAdd(q + sz, r.a[4]);
+        atomicAdd(q + sz + 1, r.a[5]);
+        atomicAdd(q + sz + sy, r.a[6]);
+        atomicAdd(q + sz + sy + 1, r.a[7]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r.a[j] = 0.f;
+}
+
 template <int MODEL, typename VT, bool GVOL, int TFM, bool POS>
 __global__ void __launch_bounds__(kWarps * 32)
 backward_kernel(const __grid_constant__ Params p)
 {
     constexpr bool EA = MODEL == DVR_EMISSION_ABSORPTION;
     extern __shared__ float4 smem[];
-    float4* tf_s = smem;                       // [R]
-    float* tfg = reinterpret_cast<float*>(smem + p.R);   // [kWarps][R][4]
+    float4* tf_s = smem;                                   // [R]
+    float* tfg = reinterpret_cast<float*>(smem + p.R);     // TF gradient copies
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     if (EA) {
         stage_tf(p, tf_s);
-        if (TFM == kTFDelayed)
-            for (int j = threadIdx.x; j < kWarps * p.R * 4; j += blockDim.x) tfg[j] = 0.f;
+        if (TFM == kTFPrivate || TFM == kTFWarp) {
+            const int n = (TFM == kTFPrivate ? 32 : 1) * kWarps * p.R * 4;
+            for (int j = threadIdx.x; j < n; j += blockDim.x) tfg[j] = 0.f;
+        }
         __syncthreads();
     }
+    // kTFPrivate: this lane's copy, element (row, ch) at [(row*4 + ch)*32]
+    float* my_tfp = tfg + warp * p.R * 128 + lane;
+    // kTFWarp: this warp's copy, [row][ch]
     float* my_tfg = tfg + warp * p.R * 4;
     const float Rm1 = (float)(p.R - 1);
 
-    for (int tile = blockIdx.x * kWarps + warp; tile < p.total_tiles; tile += gridDim.x * kWarps) {
+    const int tile = blockIdx.x * kWarps + warp;
+    if (tile < p.total_tiles) {
         const int v = find_view(p, tile);
         const ViewDesc& vw = p.view[v];
-        const int local = tile - p.tile_start[v];
-        const int px = (local % vw.tiles_x) * kTileW + (lane & (kTileW - 1));
-        const int py = (local / vw.tiles_x) * kTileH + (lane / kTileW);
+        int px, py;
+        tile_pixel(vw, tile - p.tile_start[v], lane, px, py);
         const bool valid = px < vw.width && py < vw.height;
         const VolumeDesc& vd = p.vol[vw.volume];
         const VT* __restrict__ vol = reinterpret_cast<const VT*>(vd.data);
@@ -144,6 +197,15 @@ backward_kernel(const __grid_constant__ Params p)
         const float dconst = EA ? 0.f : Ah * expf(-(sh + sl)) * G.dt;   // absorption: d^_i
         float gs[3] = {0.f, 0.f, 0.f}, gi[3] = {0.f, 0.f, 0.f};
         float dt_hat = 0.f;
+        TFRun tr;
+        tr.k = -1;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tr.a[j] = 0.f;
+        CellRun cr;
+        cr.base = 0xffffffffu;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cr.a[j] = 0.f;
+        const uint32_t vsy = (uint32_t)G.n[0], vsz = vsy * (uint32_t)G.n[1];
 
         for (int i = N - 1; i >= 0; --i) {
             const float fi = (float)i;
@@ -170,9 +232,34 @@ backward_kernel(const __grid_constant__ Params p)
                 const float tau_hat = a_hat * G.dt * ea;
                 if (POS) dt_hat = fmaf(a_hat * s.c.w, ea, dt_hat);
                 const float h0 = Ta * Ch0, h1 = Ta * Ch1, h2 = Ta * Ch2;   // rgb^
-                if (TFM != kTFNone) {
+                if (TFM == kTFPrivate) {
                     const float w0 = 1.f - s.fr, w1 = s.fr;
-                    float* b0 = (TFM == kTFDelayed ? my_tfg : p.grad_tf) + 4 * s.k;
+                    float* q = my_tfp + s.k * 128;
+                    q[0] += w0 * h0;
+                    q[32] += w0 * h1;
+                    q[64] += w0 * h2;
+                    q[96] += w0 * tau_hat;
+                    q[128] += w1 * h0;
+                    q[160] += w1 * h1;
+                    q[192] += w1 * h2;
+                    q[224] += w1 * tau_hat;
+                } else if (TFM == kTFWarp) {
+                    if (s.k != tr.k) {
+                        tf_run_flush(my_tfg, tr);
+                        tr.k = s.k;
+                    }
+                    const float w0 = 1.f - s.fr, w1 = s.fr;
+                    tr.a[0] = fmaf(w0, h0, tr.a[0]);
+                    tr.a[1] = fmaf(w0, h1, tr.a[1]);
+                    tr.a[2] = fmaf(w0, h2, tr.a[2]);
+                    tr.a[3] = fmaf(w0, tau_hat, tr.a[3]);
+                    tr.a[4] = fmaf(w1, h0, tr.a[4]);
+                    tr.a[5] = fmaf(w1, h1, tr.a[5]);
+                    tr.a[6] = fmaf(w1, h2, tr.a[6]);
+                    tr.a[7] = fmaf(w1, tau_hat, tr.a[7]);
+                } else if (TFM == kTFImmediate) {
+                    const float w0 = 1.f - s.fr, w1 = s.fr;
+                    float* b0 = p.grad_tf + 4 * s.k;
                     atomicAdd(b0 + 0, w0 * h0);
                     atomicAdd(b0 + 1, w0 * h1);
                     atomicAdd(b0 + 2, w0 * h2);
@@ -194,20 +281,22 @@ backward_kernel(const __grid_constant__ Params p)
                 if (POS) dt_hat = fmaf(Ah, d, dt_hat);   // times T_N below
             }
             if (GVOL) {
+                if (c.base != cr.base) {
+                    cell_run_flush(gvol, vsy, vsz, cr);
+                    cr.base = c.base;
+                }
                 const float a0 = d_hat * (1.f - c.fz), a1 = d_hat * c.fz;
                 const float b00 = a0 * (1.f - c.fy), b01 = a0 * c.fy;
                 const float b10 = a1 * (1.f - c.fy), b11 = a1 * c.fy;
                 const float ox = 1.f - c.fx;
-                float* q = gvol + c.base;
-                const uint32_t sy = (uint32_t)G.n[0], sz = sy * (uint32_t)G.n[1];
-                atomicAdd(q, b00 * ox);
-                atomicAdd(q + 1, b00 * c.fx);
-                atomicAdd(q + sy, b01 * ox);
-                atomicAdd(q + sy + 1, b01 * c.fx);
-                atomicAdd(q + sz, b10 * ox);
-                atomicAdd(q + sz + 1, b10 * c.fx);
-                atomicAdd(q + sz + sy, b11 * ox);
-                atomicAdd(q + sz + sy + 1, b11 * c.fx);
+                cr.a[0] = fmaf(b00, ox, cr.a[0]);
+                cr.a[1] = fmaf(b00, c.fx, cr.a[1]);
+                cr.a[2] = fmaf(b01, ox, cr.a[2]);
+                cr.a[3] = fmaf(b01, c.fx, cr.a[3]);
+                cr.a[4] = fmaf(b10, ox, cr.a[4]);
+                cr.a[5] = fmaf(b10, c.fx, cr.a[5]);
+                cr.a[6] = fmaf(b11, ox, cr.a[6]);
+                cr.a[7] = fmaf(b11, c.fx, cr.a[7]);
             }
             if (POS) {
                 float dg[3];
@@ -220,6 +309,9 @@ backward_kernel(const __grid_constant__ Params p)
                 }
             }
         }
+
+        if (TFM == kTFWarp) tf_run_flush(my_tfg, tr);
+        if (GVOL) cell_run_flush(gvol, vsy, vsz, cr);
 
         if (POS) {
             if (!EA) dt_hat *= expf(-(sh + sl));          // absorption: T_N sum_i A^ d_i
@@ -245,7 +337,18 @@ backward_kernel(const __grid_constant__ Params p)
         }
     }
 
-    if (EA && TFM == kTFDelayed) {
+    if (EA && TFM == kTFPrivate) {
+        __syncthreads();
+        // warp w sums entries j = w, w + kWarps, ...: each lane reads its own
+        // column (conflict-free), then a warp reduction
+        for (int j = warp; j < p.R * 4; j += kWarps) {
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) s += tfg[w * p.R * 128 + j * 32 + lane];
+            s = warp_sum(s);
+            if (lane == 0 && s != 0.f) atomicAdd(p.grad_tf + j, s);
+        }
+    } else if (EA && TFM == kTFWarp) {
         __syncthreads();
         for (int j = threadIdx.x; j < p.R * 4; j += blockDim.x) {
             float s = 0.f;
@@ -260,25 +363,24 @@ template <int MODEL, typename VT, bool GVOL, int TFM, bool POS>
 static cudaError_t launch_one(const Params& p, cudaStream_t stream)
 {
     auto k = backward_kernel<MODEL, VT, GVOL, TFM, POS>;
-    const size_t smem = MODEL == DVR_EMISSION_ABSORPTION
-        ? sizeof(float4) * (size_t)p.R * (TFM == kTFDelayed ? 1 + kWarps : 1) : 0;
+    size_t smem = 0;
+    if (MODEL == DVR_EMISSION_ABSORPTION) {
+        smem = sizeof(float4) * (size_t)p.R;
+        if (TFM == kTFPrivate) smem += sizeof(float) * 4 * 32 * kWarps * (size_t)p.R;
+        if (TFM == kTFWarp) smem += sizeof(float) * 4 * kWarps * (size_t)p.R;
+    }
     // opt in to more than 48 KB of dynamic shared memory, once per device
     static unsigned long long configured = 0;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !(configured >> dev & 1ull)) {
         cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(sizeof(float4) * kMaxTF * (1 + kWarps)));
+                                               (int)(sizeof(float4) * kMaxTF * (1 + kWarps)
+                                                     + sizeof(float) * 4 * 32 * kWarps * kPrivateMaxR));
         if (err != cudaSuccess) return err;
         configured |= 1ull << dev;
     }
-    int occ = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kWarps * 32, smem);
-    if (err != cudaSuccess) return err;
-    const int need = (p.total_tiles + kWarps - 1) / kWarps;
-    int blocks = sm_count() * (occ > 0 ? occ : 1);
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
+    const int blocks = (p.total_tiles + kWarps - 1) / kWarps;   // one tile per warp
     k<<<blocks, kWarps * 32, smem, stream>>>(p);
     return cudaGetLastError();
 }
@@ -297,8 +399,9 @@ static cudaError_t pick_tf(const Params& p, int tfm, bool pos, cudaStream_t s)
         return pick_pos<MODEL, VT, GVOL, kTFNone>(p, pos, s);
     } else {
         if (tfm == kTFNone) return pick_pos<MODEL, VT, GVOL, kTFNone>(p, pos, s);
-        if (tfm == kTFDelayed) return pick_pos<MODEL, VT, GVOL, kTFDelayed>(p, pos, s);
-        return pick_pos<MODEL, VT, GVOL, kTFImmediate>(p, pos, s);
+        if (tfm == kTFImmediate) return pick_pos<MODEL, VT, GVOL, kTFImmediate>(p, pos, s);
+        if (p.R <= kPrivateMaxR) return pick_pos<MODEL, VT, GVOL, kTFPrivate>(p, pos, s);
+        return pick_pos<MODEL, VT, GVOL, kTFWarp>(p, pos, s);
     }
 }
 

@@ -320,6 +320,26 @@ __device__ __forceinline__ void stage_tf(const Params& p, float4* tf_s)
     }
 }
 
+// Tiles are issued centre-out: rank r of n maps to c, c+1, c-1, c+2, ...
+// (c = (n-1)/2), rows first, so the long rays through the middle of the
+// view start first and short ones fill the end of the launch.
+__device__ __forceinline__ int center_out(int r, int n)
+{
+    const int c = (n - 1) >> 1;
+    const int k = (r + 1) >> 1;
+    return (r & 1) ? c + k : c - k;
+}
+
+// Pixel of this lane in warp tile `local` of a view.
+__device__ __forceinline__ void tile_pixel(const ViewDesc& vw, int local, int lane, int& px, int& py)
+{
+    const int tiles_y = (vw.height + kTileH - 1) / kTileH;
+    const int tx = center_out(local % vw.tiles_x, vw.tiles_x);
+    const int ty = center_out(local / vw.tiles_x, tiles_y);
+    px = tx * kTileW + (lane & (kTileW - 1));
+    py = ty * kTileH + (lane / kTileW);
+}
+
 // Warp tile -> (view, pixel) mapping.
 __device__ __forceinline__ int find_view(const Params& p, int tile)
 {

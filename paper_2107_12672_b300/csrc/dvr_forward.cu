@@ -26,9 +26,8 @@ forward_kernel(const __grid_constant__ Params p)
     for (int tile = blockIdx.x * kWarps + warp; tile < p.total_tiles; tile += gridDim.x * kWarps) {
         const int v = find_view(p, tile);
         const ViewDesc& vw = p.view[v];
-        const int local = tile - p.tile_start[v];
-        const int px = (local % vw.tiles_x) * kTileW + (lane & (kTileW - 1));
-        const int py = (local / vw.tiles_x) * kTileH + (lane / kTileW);
+        int px, py;
+        tile_pixel(vw, tile - p.tile_start[v], lane, px, py);
         const bool valid = px < vw.width && py < vw.height;
         const VolumeDesc& vd = p.vol[vw.volume];
         const VT* __restrict__ vol = reinterpret_cast<const VT*>(vd.data);

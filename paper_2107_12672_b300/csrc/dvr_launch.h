@@ -7,8 +7,12 @@
 
 namespace dvr {
 
-// Variants of the adjoint kernel (template parameters, Sec. 4.4).
-enum TFMode { kTFNone = 0, kTFDelayed = 1, kTFImmediate = 2 };
+// Variants of the adjoint kernel (template parameters, Sec. 4.4). The API
+// asks for kTFNone, kTFDelayed or kTFImmediate; "delayed" runs as
+// kTFPrivate (per-lane shared-memory copies) when R <= kPrivateMaxR, else
+// as kTFWarp (per-warp copies with shared atomics).
+enum TFMode { kTFNone = 0, kTFDelayed = 1, kTFImmediate = 2, kTFPrivate = 3, kTFWarp = 4 };
+constexpr int kPrivateMaxR = 32;
 
 cudaError_t launch_forward(const Params& p, int model, int vol_dtype, cudaStream_t stream);
 cudaError_t launch_backward(const Params& p, int model, int vol_dtype, bool grad_volume,

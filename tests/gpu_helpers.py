@@ -22,9 +22,27 @@ def rel_err(gpu, ref):
     return float((np.abs(gpu - ref) / (np.abs(ref) + scale)).max())
 
 
-def assert_close(gpu, ref, rtol, what=""):
-    e = rel_err(gpu, ref)
-    assert e <= rtol, f"{what}: max relative error {e:.3e} > {rtol:.1e}"
+# The oracle bounds what binary32 rounding may change at kinks (TF control
+# points, cell faces); the parity tests take twice its error model.
+
+FP32_MARGIN = 2.0
+
+
+def assert_close(gpu, ref, rtol, what="", slack=None):
+    """|gpu - ref| <= rtol (|ref| + max|ref|) + slack, elementwise; `slack` is
+    the oracle's bound on what the choice of one-sided derivatives at TF
+    kinks may change."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = np.abs(ref).max()
+    excess = np.abs(gpu - ref) - (slack if slack is not None else 0.0)
+    err = np.maximum(excess, 0.0) / (np.abs(ref) + scale) if scale > 0 else np.maximum(excess, 0.0)
+    e = float(err.max())
+    if e > rtol:
+        i = np.unravel_index(int(np.argmax(err)), err.shape)
+        sl = 0.0 if slack is None else float(np.asarray(slack)[i])
+        raise AssertionError(f"{what}: max relative error {e:.3e} > {rtol:.1e} at {i}: gpu {gpu[i]:.7g} "
+                             f"ref {ref[i]:.7g} scale {scale:.4g} kink slack {sl:.3g}")
     return e
 
 

@@ -344,3 +344,34 @@ def test_fp32_setup_close_to_fp64():
     same = N32 == N64
     assert same.mean() > 0.99
     assert np.abs(img32[same] - img64[same]).max() < 1e-4
+
+
+def test_kink_ambiguity_bounds_one_sided_derivatives():
+    """At a TF control point the derivative of f_TF jumps (piecewise-linear
+    TF, Sec. 3.1). With every sample exactly on a knot (constant density
+    0.5, R = 5: u = 2), the central difference w.r.t. a voxel averages the
+    two one-sided derivatives, so it must lie within the reported ambiguity
+    of the adjoint's one-sided value; away from knots the ambiguity is 0."""
+    n = 6
+    v = np.full((n, n, n), 0.5)
+    tf = np.array([[0.1, 0.2, 0.3, 1.0], [0.4, 0.1, 0.9, 3.0], [0.2, 0.8, 0.5, 2.0],
+                   [0.9, 0.3, 0.1, 6.0], [0.5, 0.5, 0.5, 1.5]])
+    view = syn.View(4, 3)
+    eye = np.array([0.7, 0.5, 1.9])
+    G = np.random.default_rng(2).normal(size=(12, 4))
+    g = oracle.backward(v, tf, "emission_absorption", view, eye, 0.5, G, fp32=False,
+                        want=("volume",), margin=1e6)
+    amb = g["volume_ambiguity"]
+    assert amb.max() > 0
+    h = 1e-7
+    for idx in [(3, 3, 3), (2, 3, 2), (3, 2, 3)]:
+        vp = v.copy(); vp[idx] += h
+        vm = v.copy(); vm[idx] -= h
+        fd = (_loss(oracle.render(vp, tf, "emission_absorption", view, eye, 0.5, fp32=False)[0], G)
+              - _loss(oracle.render(vm, tf, "emission_absorption", view, eye, 0.5, fp32=False)[0], G)) / (2 * h)
+        assert abs(fd - g["volume"][idx]) <= amb[idx] * 0.5 + 1e-6 * np.abs(g["volume"]).max()
+        assert abs(fd - g["volume"][idx]) >= amb[idx] * 0.5 - 1e-6 * np.abs(g["volume"]).max()
+    v2 = np.full((n, n, n), 0.4)     # u = 1.6: no knot nearby
+    g2 = oracle.backward(v2, tf, "emission_absorption", view, eye, 0.5, G, fp32=False,
+                         want=("volume",), margin=1.0)
+    assert g2["volume_ambiguity"].max() == 0
