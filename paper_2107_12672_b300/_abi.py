@@ -11,7 +11,9 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libdvr.so")
+# DVR_LIBRARY may name another build of the same library (e.g. to compare
+# kernel variants); by default the in-tree build is loaded.
+LIB_PATH = os.environ.get("DVR_LIBRARY") or os.path.join(_HERE, "_lib", "libdvr.so")
 
 DVR_OK = 0
 DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
@@ -49,6 +51,8 @@ def load() -> ctypes.CDLL:
         if _lib is not None:
             return _lib
         if not os.path.exists(LIB_PATH):
+            if os.environ.get("DVR_LIBRARY"):
+                raise DVRError(f"DVR_LIBRARY={LIB_PATH} does not exist")
             from . import build as _build
             _build.build()
         lib = ctypes.CDLL(LIB_PATH)

@@ -136,7 +136,7 @@ __device__ __forceinline__ void cell_run_flush(float* g, uint32_t sy, uint32_t s
 }
 
 template <int MODEL, typename VT, bool GVOL, int TFM, bool POS>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, DVR_BWD_MIN_BLOCKS)
 backward_kernel(const __grid_constant__ Params p)
 {
     constexpr bool EA = MODEL == DVR_EMISSION_ABSORPTION;
@@ -207,11 +207,25 @@ backward_kernel(const __grid_constant__ Params p)
         for (int j = 0; j < 8; ++j) cr.a[j] = 0.f;
         const uint32_t vsy = (uint32_t)G.n[0], vsz = vsy * (uint32_t)G.n[1];
 
+        // software pipeline with same-cell reuse as in the forward march,
+        // in reverse order
+        MCell n1, n2;
+        float last_v[8];
+        if (N > 0) {
+            fetch_sample_reuse<VT>(vol, G, m, N - 1, 0xffffffffu, n1);
+            fetch_sample_reuse<VT>(vol, G, m, N - 2, n1.c.base, n2);
+        }
         for (int i = N - 1; i >= 0; --i) {
             const float fi = (float)i;
-            const float gc[3] = {march_coord(m, 0, fi), march_coord(m, 1, fi), march_coord(m, 2, fi)};
-            Cell c;
-            const float d = trilinear<VT>(vol, G, gc, c);
+            MCell cur = n1;
+            cell_resolve(cur, last_v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) last_v[k] = cur.c.v[k];
+            n1 = n2;
+            fetch_sample_reuse<VT>(vol, G, m, i - 2, n1.c.base, n2);
+            const Cell& c = cur.c;
+            float dg[3];
+            const float d = POS ? cell_value_grad(c, dg) : cell_value(c);
             float d_hat;
             if (EA) {
                 TFSample s;
@@ -233,6 +247,8 @@ backward_kernel(const __grid_constant__ Params p)
                 if (POS) dt_hat = fmaf(a_hat * s.c.w, ea, dt_hat);
                 const float h0 = Ta * Ch0, h1 = Ta * Ch1, h2 = Ta * Ch2;   // rgb^
                 if (TFM == kTFPrivate) {
+                    // the lane's own copy: plain adds, no two lanes share a
+                    // bank (measured faster than shared-memory reductions)
                     const float w0 = 1.f - s.fr, w1 = s.fr;
                     float* q = my_tfp + s.k * 128;
                     q[0] += w0 * h0;
@@ -269,13 +285,8 @@ backward_kernel(const __grid_constant__ Params p)
                     atomicAdd(b0 + 6, w1 * h2);
                     atomicAdd(b0 + 7, w1 * tau_hat);
                 }
-                if (s.slope) {
-                    const float4 ta = tf_s[s.k], tb = tf_s[s.k + 1];
-                    d_hat = Rm1 * fmaf(tb.w - ta.w, tau_hat,
-                                       fmaf(tb.z - ta.z, h2, fmaf(tb.y - ta.y, h1, (tb.x - ta.x) * h0)));
-                } else {
-                    d_hat = 0.f;
-                }
+                d_hat = s.slope ? Rm1 * fmaf(s.dc.w, tau_hat, fmaf(s.dc.z, h2, fmaf(s.dc.y, h1, s.dc.x * h0)))
+                                : 0.f;
             } else {
                 d_hat = dconst;
                 if (POS) dt_hat = fmaf(Ah, d, dt_hat);   // times T_N below
@@ -299,8 +310,6 @@ backward_kernel(const __grid_constant__ Params p)
                 cr.a[7] = fmaf(b11, c.fx, cr.a[7]);
             }
             if (POS) {
-                float dg[3];
-                trilinear_grad(c, dg);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     const float t = dg[a] * d_hat;

@@ -21,6 +21,15 @@ constexpr int kTileW = 8;            // a warp renders an 8 x 4 pixel tile
 constexpr int kTileH = 4;
 constexpr int kMaxTF = 1024;         // transfer-function rows staged in shared memory
 
+// Minimum resident blocks per SM the compiler must allow (register budget
+// of __launch_bounds__), chosen by measurement.
+#ifndef DVR_FWD_MIN_BLOCKS
+#define DVR_FWD_MIN_BLOCKS 1
+#endif
+#ifndef DVR_BWD_MIN_BLOCKS
+#define DVR_BWD_MIN_BLOCKS 1
+#endif
+
 struct VolumeDesc {
     const void* data;
     float* grad;                     // adjoint only, may be null
@@ -216,7 +225,10 @@ __device__ __forceinline__ float march_coord(const March& m, int a, float fi)
     return __fmaf_rn(fi, m.gdh[a], m.g0h[a]) + __fmaf_rn(fi, m.gdl[a], m.g0l[a]);
 }
 
-// Trilinear interpolation at grid coordinate g (clamped to the box).
+// Trilinear interpolation at grid coordinate g (clamped to the box), split
+// into locating the cell and loading its 8 corners (cell_fetch) and the
+// interpolation itself (cell_value), so that a march can issue the loads of
+// the next sample before it interpolates the current one.
 struct Cell {
     uint32_t base;                   // index of corner (0,0,0)
     float fx, fy, fz;
@@ -225,7 +237,7 @@ struct Cell {
 };
 
 template <typename VT>
-__device__ __forceinline__ float trilinear(const VT* __restrict__ vol, const Grid& G, const float gc[3],
+__device__ __forceinline__ void cell_fetch(const VT* __restrict__ vol, const Grid& G, const float gc[3],
                                            Cell& c)
 {
     int j[3];
@@ -250,6 +262,10 @@ __device__ __forceinline__ float trilinear(const VT* __restrict__ vol, const Gri
     c.v[5] = Load<VT>::get(p + sz + sx);
     c.v[6] = Load<VT>::get(p + sz + sy);
     c.v[7] = Load<VT>::get(p + sz + sy + sx);
+}
+
+__device__ __forceinline__ float cell_value(const Cell& c)
+{
     const float c00 = fmaf(c.fx, c.v[1] - c.v[0], c.v[0]);
     const float c10 = fmaf(c.fx, c.v[3] - c.v[2], c.v[2]);
     const float c01 = fmaf(c.fx, c.v[5] - c.v[4], c.v[4]);
@@ -259,31 +275,92 @@ __device__ __forceinline__ float trilinear(const VT* __restrict__ vol, const Gri
     return fmaf(c.fz, c1 - c0, c0);
 }
 
-// d(density)/d(grid coordinate), zero along clamped axes.
-__device__ __forceinline__ void trilinear_grad(const Cell& c, float dg[3])
+// Density and its derivative w.r.t. the grid coordinate (zero along clamped
+// axes), sharing the lerps of cell_value.
+__device__ __forceinline__ float cell_value_grad(const Cell& c, float dg[3])
 {
     const float e00 = c.v[1] - c.v[0], e10 = c.v[3] - c.v[2];
     const float e01 = c.v[5] - c.v[4], e11 = c.v[7] - c.v[6];
-    const float ex0 = fmaf(c.fy, e10 - e00, e00);
-    const float ex1 = fmaf(c.fy, e11 - e01, e01);
-    const float gx = fmaf(c.fz, ex1 - ex0, ex0);
     const float c00 = fmaf(c.fx, e00, c.v[0]);
     const float c10 = fmaf(c.fx, e10, c.v[2]);
     const float c01 = fmaf(c.fx, e01, c.v[4]);
     const float c11 = fmaf(c.fx, e11, c.v[6]);
-    const float gy = fmaf(c.fz, (c11 - c01) - (c10 - c00), c10 - c00);
-    const float c0 = fmaf(c.fy, c10 - c00, c00);
-    const float c1 = fmaf(c.fy, c11 - c01, c01);
-    const float gz = c1 - c0;
-    dg[0] = c.in[0] ? gx : 0.f;
-    dg[1] = c.in[1] ? gy : 0.f;
-    dg[2] = c.in[2] ? gz : 0.f;
+    const float y0 = c10 - c00, y1 = c11 - c01;
+    const float c0 = fmaf(c.fy, y0, c00);
+    const float c1 = fmaf(c.fy, y1, c01);
+    const float ex0 = fmaf(c.fy, e10 - e00, e00);
+    const float ex1 = fmaf(c.fy, e11 - e01, e01);
+    dg[0] = c.in[0] ? fmaf(c.fz, ex1 - ex0, ex0) : 0.f;
+    dg[1] = c.in[1] ? fmaf(c.fz, y1 - y0, y0) : 0.f;
+    dg[2] = c.in[2] ? c1 - c0 : 0.f;
+    return fmaf(c.fz, c1 - c0, c0);
+}
+
+template <typename VT>
+__device__ __forceinline__ void fetch_sample(const VT* __restrict__ vol, const Grid& G, const March& m,
+                                             int i, Cell& c)
+{
+    const float fi = (float)i;
+    const float gc[3] = {march_coord(m, 0, fi), march_coord(m, 1, fi), march_coord(m, 2, fi)};
+    cell_fetch<VT>(vol, G, gc, c);
+}
+
+// The march's fetch of sample i when the previous sample (in march order)
+// lies in cell `prev_base`: if sample i is in the same cell, no corner is
+// loaded (the lane sits out the warp's load instructions, which then touch
+// fewer cache sectors) and c.reuse is set; cell_resolve later copies the
+// corners from the previous sample once those have arrived.
+struct MCell {
+    Cell c;
+    bool reuse;
+};
+
+template <typename VT>
+__device__ __forceinline__ void fetch_sample_reuse(const VT* __restrict__ vol, const Grid& G, const March& m,
+                                                   int i, uint32_t prev_base, MCell& mc)
+{
+    const float fi = (float)i;
+    const float gc[3] = {march_coord(m, 0, fi), march_coord(m, 1, fi), march_coord(m, 2, fi)};
+    Cell& c = mc.c;
+    int j[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float hi = (float)(G.n[a] - 1);
+        c.in[a] = (gc[a] >= 0.f) && (gc[a] <= hi);
+        const float gg = fminf(fmaxf(gc[a], 0.f), hi);
+        j[a] = min((int)gg, G.n[a] - 2);
+        (a == 0 ? c.fx : (a == 1 ? c.fy : c.fz)) = gg - (float)j[a];
+    }
+    const uint32_t sy = (uint32_t)G.n[0], sz = (uint32_t)G.n[0] * (uint32_t)G.n[1];
+    c.base = (uint32_t)j[0] + sy * (uint32_t)j[1] + sz * (uint32_t)j[2];
+    mc.reuse = c.base == prev_base;
+    if (!mc.reuse) {
+        const VT* p = vol + c.base;
+        c.v[0] = Load<VT>::get(p);
+        c.v[1] = Load<VT>::get(p + 1);
+        c.v[2] = Load<VT>::get(p + sy);
+        c.v[3] = Load<VT>::get(p + sy + 1);
+        c.v[4] = Load<VT>::get(p + sz);
+        c.v[5] = Load<VT>::get(p + sz + 1);
+        c.v[6] = Load<VT>::get(p + sz + sy);
+        c.v[7] = Load<VT>::get(p + sz + sy + 1);
+    }
+}
+
+// Corners of a fetched sample: its own loads, or those of the previous one.
+__device__ __forceinline__ void cell_resolve(MCell& mc, const float last_v[8])
+{
+    if (mc.reuse) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) mc.c.v[k] = last_v[k];
+    }
 }
 
 // f_TF from the shared-memory copy: R rows at densities r/(R-1), linear in
 // between, density clamped to [0, 1].
 struct TFSample {
     float4 c;                        // r, g, b, tau
+    float4 dc;                       // row k+1 - row k
     int k;
     float fr;
     bool slope;
@@ -298,10 +375,11 @@ __device__ __forceinline__ void tf_lookup(const float4* __restrict__ tf, int R, 
     s.fr = u - (float)s.k;
     const float4 a = tf[s.k];
     const float4 b = tf[s.k + 1];
-    s.c.x = fmaf(s.fr, b.x - a.x, a.x);
-    s.c.y = fmaf(s.fr, b.y - a.y, a.y);
-    s.c.z = fmaf(s.fr, b.z - a.z, a.z);
-    s.c.w = fmaf(s.fr, b.w - a.w, a.w);
+    s.dc = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
+    s.c.x = fmaf(s.fr, s.dc.x, a.x);
+    s.c.y = fmaf(s.fr, s.dc.y, a.y);
+    s.c.z = fmaf(s.fr, s.dc.z, a.z);
+    s.c.w = fmaf(s.fr, s.dc.w, a.w);
 }
 
 // Stage the TF (float or half rows) into shared memory as float4.

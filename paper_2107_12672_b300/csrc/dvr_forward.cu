@@ -1,5 +1,5 @@
 // Forward pass (Alg. 1): one thread per ray, one warp per 8 x 4 pixel tile,
-// all views of the launch in one grid. For each sample: position, trilinear
+// all views of the launch in one grid, tiles issued centre-out. For each sample: position, trilinear
 // density, TF lookup from shared memory, Beer-Lambert opacity and
 // front-to-back blending (Eq. blend-forward) in registers. The ray's optical
 // depth S = sum dt tau_i is accumulated as an unevaluated float pair and
@@ -11,7 +11,7 @@
 namespace dvr {
 
 template <int MODEL, typename VT>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, DVR_FWD_MIN_BLOCKS)
 forward_kernel(const __grid_constant__ Params p)
 {
     __shared__ float4 tf_s[MODEL == DVR_EMISSION_ABSORPTION ? kMaxTF : 1];
@@ -45,11 +45,25 @@ forward_kernel(const __grid_constant__ Params p)
 
         float sh = 0.f, sl = 0.f;    // optical depth, hi + lo
         float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+        // software pipeline: the corners of samples i+1 and i+2 are in
+        // flight while sample i is composited (positions past the ray end are
+        // clamped to the box, so the extra fetches stay in bounds); a sample
+        // in the same cell as its predecessor loads nothing
+        MCell n1, n2;
+        float last_v[8];
+        if (N > 0) {
+            fetch_sample_reuse<VT>(vol, G, m, 0, 0xffffffffu, n1);
+            fetch_sample_reuse<VT>(vol, G, m, 1, n1.c.base, n2);
+        }
         for (int i = 0; i < N; ++i) {
-            const float fi = (float)i;
-            const float gc[3] = {march_coord(m, 0, fi), march_coord(m, 1, fi), march_coord(m, 2, fi)};
-            Cell c;
-            const float d = trilinear<VT>(vol, G, gc, c);
+            MCell cur = n1;
+            cell_resolve(cur, last_v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) last_v[k] = cur.c.v[k];
+            n1 = n2;
+            fetch_sample_reuse<VT>(vol, G, m, i + 2, n1.c.base, n2);
+            const Cell& c = cur.c;
+            const float d = cell_value(c);
             float x;
             if (MODEL == DVR_EMISSION_ABSORPTION) {
                 TFSample s;
