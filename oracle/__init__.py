@@ -52,11 +52,11 @@ def _load():
         I = ctypes.c_int
         L = ctypes.c_int64
         D = ctypes.c_double
-        lib.ora_render.argtypes = [P, I, I, I, P, I, I, I, I, I, D, P, D, I, P, L, P, P, P]
+        lib.ora_render.argtypes = [P, I, I, I, I, P, I, I, I, I, I, D, P, D, I, P, L, P, P, P]
         lib.ora_rays.argtypes = [I, I, I, I, I, I, D, P, D, I, P, P, P]
         lib.ora_interpolate.argtypes = [P, I, I, I, P, L, P]
-        lib.ora_backward.argtypes = [P, I, I, I, P, I, I, I, I, I, D, P, D, I, P, L, P, I, P, P, P, P, D, P, P]
-        lib.ora_render_dual.argtypes = [P, I, I, I, P, I, I, I, I, I, D, P, D, P, L, P, P]
+        lib.ora_backward.argtypes = [P, I, I, I, I, P, I, I, I, I, I, D, P, D, I, P, L, P, I, P, P, P, P, D, P, P]
+        lib.ora_render_dual.argtypes = [P, I, I, I, I, P, I, I, I, I, I, D, P, D, P, L, P, P]
         lib.ora_orbit_eye.argtypes = [P, L, P]
         lib.ora_orbit_eye_backward.argtypes = [P, L, P, P]
         lib.ora_threads.restype = I
@@ -84,9 +84,12 @@ def _f32val(x):
 class _Common:
     def __init__(self, volume, tf, model, view, eye, step, fp32):
         vol = np.asarray(volume)
-        if vol.dtype != np.float64:
+        # float32 volumes are read as they are (their values are exact in
+        # binary64); anything else is widened to binary64
+        if vol.dtype != np.float32 and vol.dtype != np.float64:
             vol = vol.astype(np.float64)
         self.vol = np.ascontiguousarray(vol)
+        self.vf32 = int(self.vol.dtype == np.float32)
         self.nz, self.ny, self.nx = self.vol.shape
         self.model = MODELS[model] if isinstance(model, str) else int(model)
         if self.model == EMISSION_ABSORPTION:
@@ -107,7 +110,7 @@ class _Common:
         self.nc = 4 if self.model == EMISSION_ABSORPTION else 1
 
     def head(self):
-        return (_p(self.vol), self.nx, self.ny, self.nz, _p(self.tf), self.R, self.model,
+        return (_p(self.vol), self.vf32, self.nx, self.ny, self.nz, _p(self.tf), self.R, self.model,
                 self.W, self.H, self.ortho, self.lens, _p(self.eye), self.step)
 
 
@@ -152,11 +155,11 @@ def backward(volume, tf, model, view, eye, step, grad_image, fp32=True, pix=None
     total = n if p is not None else c.W * c.H
     gi = _f64(grad_image).reshape(total, c.nc)
     out = {}
-    gv = np.zeros_like(c.vol) if "volume" in want else None
+    gv = np.zeros(c.vol.shape) if "volume" in want else None
     gt = np.zeros((c.R, 4)) if ("tf" in want and c.model == EMISSION_ABSORPTION) else None
     ge = np.zeros(3) if "eye" in want else None
     gs = np.zeros(1) if "step" in want else None
-    amb = np.zeros_like(c.vol) if (gv is not None and margin > 0) else None
+    amb = np.zeros(c.vol.shape) if (gv is not None and margin > 0) else None
     amb_e = np.zeros(3) if (ge is not None and margin > 0) else None
     _load().ora_backward(*c.head(), c.fp32, _p(p), n, _p(gi), int(bool(invert)),
                          _p(gv), _p(gt), _p(ge), _p(gs), float(margin), _p(amb), _p(amb_e))

@@ -57,7 +57,14 @@ typedef struct {
     double half[3];    /* half extent of the box along each axis */
     double inv_h;      /* grid units per world unit, max(n) - 1 */
     double dt;         /* step in world units */
+    int vf32;          /* volume samples stored as float (else double) */
 } grid_t;
+
+/* density of vertex i (float samples are widened exactly) */
+static inline double vget(const void* V, const grid_t* G, long i)
+{
+    return G->vf32 ? (double)((const float*)V)[i] : ((const double*)V)[i];
+}
 
 /* Camera of one view. */
 typedef struct {
@@ -80,6 +87,7 @@ static inline double rnd(int fp32, double x) { return fp32 ? (double)(float)x : 
 static void make_grid(int nx, int ny, int nz, double step, int fp32, grid_t* G)
 {
     G->n[0] = nx; G->n[1] = ny; G->n[2] = nz;
+    G->vf32 = 0;
     int nm = nx > ny ? nx : ny;
     if (nz > nm) nm = nz;
     G->inv_h = (double)(nm - 1);
@@ -181,7 +189,7 @@ static void camera_ray(const cam_t* c, const grid_t* G, int px, int py, int fp32
  * the derivative of the density w.r.t. the grid coordinate (zero along an
  * axis where x was clamped to the box).
  */
-static double interpolate(const double* V, const grid_t* G, const double x[3],
+static double interpolate(const void* V, const grid_t* G, const double x[3],
                           long idx[8], double wt[8], double dg[3])
 {
     int j[3];
@@ -203,7 +211,7 @@ static double interpolate(const double* V, const grid_t* G, const double x[3],
         int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
         idx[c] = ((long)(j[2] + cz) * G->n[1] + (j[1] + cy)) * (long)G->n[0] + (j[0] + cx);
         wt[c] = (cx ? fr[0] : 1.0 - fr[0]) * (cy ? fr[1] : 1.0 - fr[1]) * (cz ? fr[2] : 1.0 - fr[2]);
-        val[c] = V[idx[c]];
+        val[c] = vget(V, G, idx[c]);
         d += wt[c] * val[c];
     }
     for (int a = 0; a < 3; ++a) {
@@ -242,7 +250,7 @@ static void transfer(const double* tf, int R, double d, double out[4], int* k, d
 }
 
 typedef struct {
-    const double* V;
+    const void* V;
     const double* tf;
     int R, model;
     grid_t G;
@@ -270,12 +278,12 @@ static double grid_error(const void* smp, const grid_t* G, double margin)
     return margin * ldexp(1.0, ilogb(gmax) - 23);
 }
 
-static double density_error(const void* smp, const double* V, double margin)
+static double density_error(const void* smp, const void* V, const grid_t* G, double margin)
 {
     const sample_t* sm = (const sample_t*)smp;
     double vmax = 0.0, gsum = 0.0;
     for (int c = 0; c < 8; ++c)
-        if (fabs(V[sm->idx[c]]) > vmax) vmax = fabs(V[sm->idx[c]]);
+        if (fabs(vget(V, G, sm->idx[c])) > vmax) vmax = fabs(vget(V, G, sm->idx[c]));
     for (int a = 0; a < 3; ++a) gsum += fabs(sm->dg[a]);
     return gsum * sm->ge + margin * 4.0 * 0x1p-24 * vmax;
 }
@@ -326,12 +334,13 @@ static double march(const scene_t* s, const ray_t* ry, double out[4], double* ta
     return S;
 }
 
-static void setup_scene(scene_t* s, const double* V, int nx, int ny, int nz, const double* tf, int R,
-                        int model, int W, int H, int ortho, double lens, const double* eye,
+static void setup_scene(scene_t* s, const void* V, int vf32, int nx, int ny, int nz, const double* tf,
+                        int R, int model, int W, int H, int ortho, double lens, const double* eye,
                         double step, int fp32)
 {
     s->V = V; s->tf = tf; s->R = R; s->model = model;
     make_grid(nx, ny, nz, step, fp32, &s->G);
+    s->G.vf32 = vf32;
     s->cam.width = W; s->cam.height = H; s->cam.ortho = ortho; s->cam.lens = lens;
     for (int a = 0; a < 3; ++a) s->cam.eye[a] = eye[a];
 }
@@ -344,12 +353,12 @@ static int channels(int model) { return model == ORA_EMISSION_ABSORPTION ? 4 : 1
  * (4 channels RGBA, or 1 channel A for the absorption model), the sample
  * count N and the optical depth S.
  */
-int ora_render(const double* V, int nx, int ny, int nz, const double* tf, int R, int model,
+int ora_render(const void* V, int vf32, int nx, int ny, int nz, const double* tf, int R, int model,
                int W, int H, int ortho, double lens, const double* eye, double step, int fp32,
                const int64_t* pix, int64_t npix, double* image, int32_t* nsamp, double* depth)
 {
     scene_t s;
-    setup_scene(&s, V, nx, ny, nz, tf, R, model, W, H, ortho, lens, eye, step, fp32);
+    setup_scene(&s, V, vf32, nx, ny, nz, tf, R, model, W, H, ortho, lens, eye, step, fp32);
     int64_t total = pix ? npix : (int64_t)W * H;
     int nc = channels(model);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -372,7 +381,8 @@ int ora_rays(int nx, int ny, int nz, int W, int H, int ortho, double lens, const
              double step, int fp32, int32_t* nsamp, double* q, double* geo /* [W*H][8] */)
 {
     scene_t s;
-    setup_scene(&s, NULL, nx, ny, nz, NULL, 2, 0, W, H, ortho, lens, eye, step, fp32);
+    setup_scene(&s, NULL, 0, nx, ny, nz, NULL, 2, 0, W, H, ortho, lens, eye, step, fp32);
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < (int64_t)W * H; ++p) {
         ray_t ry;
         camera_ray(&s.cam, &s.G, (int)(p % W), (int)(p / W), fp32, &ry);
@@ -403,7 +413,7 @@ int ora_interpolate(const double* V, int nx, int ny, int nz, const double* x, in
  * integer (a face between two cells, or a box face where the coordinate is
  * clamped), the jump of d(density)/d(g_a) across that face; 0 elsewhere.
  */
-static void face_jumps(const double* V, const grid_t* G, const double x[3], double delta, double jump[3])
+static void face_jumps(const void* V, const grid_t* G, const double x[3], double delta, double jump[3])
 {
     double g[3];
     for (int a = 0; a < 3; ++a) g[a] = (x[a] + G->half[a]) * G->inv_h;
@@ -437,7 +447,7 @@ static void face_jumps(const double* V, const grid_t* G, const double x[3], doub
                 for (int o = 0; o < 3; ++o)
                     if (o != a) w *= bb[o] ? fr[o] : 1.0 - fr[o];
                 long idx = ((long)(j[2] + bb[2]) * G->n[1] + (j[1] + bb[1])) * (long)G->n[0] + (j[0] + bb[0]);
-                sum += w * V[idx];
+                sum += w * vget(V, G, idx);
             }
             slope[sd] = sum;
         }
@@ -449,7 +459,7 @@ static void face_jumps(const double* V, const grid_t* G, const double x[3], doub
  * largest coordinate (times margin). */
 static double grid_error(const void* smp, const grid_t* G, double margin);
 /* binary32 error bound of a sample's density. */
-static double density_error(const void* smp, const double* V, double margin);
+static double density_error(const void* smp, const void* V, const grid_t* G, double margin);
 
 static inline void atomic_add(double* p, double v)
 {
@@ -537,14 +547,14 @@ static void camera_adjoint(const cam_t* c, const ray_t* r, const double xo_hat[3
  *   amb_eye: the change of x^_i from either kind of kink, chained through
  *            the camera adjoint, summed in absolute value.
  */
-int ora_backward(const double* V, int nx, int ny, int nz, const double* tf, int R, int model,
+int ora_backward(const void* V, int vf32, int nx, int ny, int nz, const double* tf, int R, int model,
                  int W, int H, int ortho, double lens, const double* eye, double step, int fp32,
                  const int64_t* pix, int64_t npix, const double* grad_image, int invert,
                  double* grad_vol, double* grad_tf, double* grad_eye, double* grad_step,
                  double margin, double* amb_vol, double* amb_eye)
 {
     scene_t s;
-    setup_scene(&s, V, nx, ny, nz, tf, R, model, W, H, ortho, lens, eye, step, fp32);
+    setup_scene(&s, V, vf32, nx, ny, nz, tf, R, model, W, H, ortho, lens, eye, step, fp32);
     int64_t total = pix ? npix : (int64_t)W * H;
     int nc = channels(model);
     const double dt = s.G.dt;
@@ -629,7 +639,7 @@ int ora_backward(const double* V, int nx, int ny, int nz, const double* tf, int 
                     if ((amb_vol || amb_eye) && margin > 0.0) {
                         double u = sm.d * (double)(R - 1);
                         double kn = floor(u + 0.5);
-                        double eu = (R - 1) * density_error(&sm, V, margin) + margin * 0x1p-23 * fabs(u);
+                        double eu = (R - 1) * density_error(&sm, V, &s.G, margin) + margin * 0x1p-23 * fabs(u);
                         if (kn >= 0.0 && kn <= (double)(R - 1) && fabs(u - kn) < eu) {
                             int knot = (int)kn;
                             double side[2] = {0.0, 0.0};   /* segments knot-1 and knot */
@@ -729,12 +739,12 @@ static inline dual dneg(dual a) { dual r; r.v = -a.v; for (int k = 0; k < 3; ++k
  * Ray setup in binary64 (the integer N and the slab face are taken from the
  * values). Outputs image [npix][nc] and dimage [npix][nc][3].
  */
-int ora_render_dual(const double* V, int nx, int ny, int nz, const double* tf, int R, int model,
+int ora_render_dual(const void* V, int vf32, int nx, int ny, int nz, const double* tf, int R, int model,
                     int W, int H, int ortho, double lens, const double* eye, double step,
                     const int64_t* pix, int64_t npix, double* image, double* dimage)
 {
     scene_t s;
-    setup_scene(&s, V, nx, ny, nz, tf, R, model, W, H, ortho, lens, eye, step, 0);
+    setup_scene(&s, V, vf32, nx, ny, nz, tf, R, model, W, H, ortho, lens, eye, step, 0);
     const grid_t* G = &s.G;
     int64_t total = pix ? npix : (int64_t)W * H;
     int nc = channels(model);
@@ -820,7 +830,7 @@ int ora_render_dual(const double* V, int nx, int ny, int nz, const double* tf, i
                 dual wt = dc(1.0);
                 for (int a = 0; a < 3; ++a) wt = dmul(wt, b[a] ? fr[a] : dsub(dc(1.0), fr[a]));
                 long idx = ((long)(j[2] + b[2]) * G->n[1] + (j[1] + b[1])) * (long)G->n[0] + (j[0] + b[0]);
-                d = dadd(d, dmul(wt, dc(V[idx])));
+                d = dadd(d, dmul(wt, dc(vget(V, G, idx))));
             }
             dual col[4];
             if (model == ORA_EMISSION_ABSORPTION) {

@@ -45,12 +45,13 @@ def _rng(seed: int) -> np.random.Generator:
 
 def gaussian_blobs(n: int, count: int, seed: int, sigma=(4.0, 10.0),
                    amplitude=(0.5, 2.0), centre=None, scale_to: int = 64,
-                   dtype=np.float32) -> np.ndarray:
+                   dtype=np.float32, device=None):
     """Sum of `count` isotropic Gaussians on an n^3 grid, layout [z][y][x].
 
     Centres are drawn U[centre] in voxels (default [n/4, 3n/4]); sigma and
     centre ranges are given for a 64^3 grid and scaled by n/scale_to, so the
-    same seed gives the same shapes at every resolution.
+    same seed gives the same shapes at every resolution. With a torch
+    `device` the sum is formed there in float32 (large volumes).
     """
     rng = _rng(seed)
     s = n / float(scale_to)
@@ -59,6 +60,14 @@ def gaussian_blobs(n: int, count: int, seed: int, sigma=(4.0, 10.0),
     sg = rng.uniform(sigma[0], sigma[1], size=count) * s
     a = rng.uniform(amplitude[0], amplitude[1], size=count)
     idx = np.arange(n, dtype=np.float64)
+    if device is not None:
+        import torch
+        out = torch.zeros((n, n, n), dtype=torch.float32, device=device)
+        for k in range(count):
+            g = [torch.from_numpy(np.exp(-((idx - c[k, d]) ** 2) / (2 * sg[k] ** 2))).to(device, torch.float32)
+                 for d in range(3)]
+            out += float(a[k]) * (g[2][:, None, None] * (g[1][None, :, None] * g[0][None, None, :]))
+        return out
     out = np.zeros((n, n, n), dtype=np.float64)
     for k in range(count):
         gx = np.exp(-((idx - c[k, 0]) ** 2) / (2 * sg[k] ** 2))
@@ -222,7 +231,28 @@ def workload(name: str, scale: float = 1.0) -> Workload:
                         ("volume", "tf", "camera"), target={"tf": random_tf(64, seed=105)},
                         note="512^3 BF16 value noise, 64-point FP16 TF, 16 views 1024^2, "
                              "step 0.25 voxel")
+    if name == "ea_fp16_1024":
+        # volumes are left to the caller (device generation, see large_volume)
+        n = sz(1024)
+        tf = random_tf(32, seed=6, tau_max=50.0)
+        w = sz(2048)
+        views = [View(w, w) for _ in range(32)]
+        eye = (fibonacci_sphere(32) * 2.5).astype(np.float32)
+        return Workload(name, "emission_absorption", [], tf, views, eye, None, 0.25,
+                        ("volume", "tf", "camera"), target={"n": n},
+                        note="1024^3 FP16 value noise plus 32 Gaussian blobs, 32-point TF, "
+                             "32 views 2048^2, step 0.25 voxel (~4000 steps on axis-aligned rays)")
     raise KeyError(name)
 
 
-WORKLOADS = ("absorption_64", "ea_256", "tomo_256x64", "ea_bf16_512")
+def large_volume(n: int, seed: int = 6, device="cuda"):
+    """n^3 value noise plus 32 Gaussian blobs (scaled to [0, 1]) formed on a
+    torch device in float32 (the 1024^3 workload)."""
+    v = value_noise(n, seed=seed, device=device)
+    b = gaussian_blobs(n, 32, seed=seed + 100, device=device)
+    b.mul_(1.0 / float(b.max()))
+    v.mul_(0.5).add_(b, alpha=0.5)
+    return v
+
+
+WORKLOADS = ("absorption_64", "ea_256", "tomo_256x64", "ea_bf16_512", "ea_fp16_1024")

@@ -51,8 +51,9 @@ def to_dev(a, dtype=torch.float32):
 
 
 def as_oracle_volume(t):
-    """The exact values the device holds (after BF16/FP16 rounding)."""
-    return t.detach().to(torch.float64).cpu().numpy()
+    """The exact values the device holds (after BF16/FP16 rounding), as
+    float32 (exact for those types; the oracle reads them without widening)."""
+    return t.detach().to(torch.float32).cpu().numpy()
 
 
 def seeded_grad_image(pixels, channels, seed):
