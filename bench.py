@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--tf-immediate", action="store_true", help="adjoint-immediate TF accumulation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the BF16/FP16 storage comparison")
     return ap.parse_args()
 
 
@@ -82,9 +84,53 @@ def profiled_traffic(kernel: str):
     return float(m.group(1))
 
 
+class _NVML:
+    """Read-only NVML queries (clocks and clock-event reasons) through the
+    driver's libnvidia-ml, for the GPU this process uses."""
+    SM = 1          # NVML_CLOCK_SM
+
+    def __init__(self, index):
+        import ctypes
+        import torch
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        rc = self.lib.nvmlInit_v2()
+        if rc != 0:
+            raise RuntimeError(f"nvmlInit_v2 returned {rc}")
+        self.h = ctypes.c_void_p()
+        bus = None
+        p = torch.cuda.get_device_properties(index)
+        if hasattr(p, "pci_bus_id") and hasattr(p, "pci_domain_id") and hasattr(p, "pci_device_id"):
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+        rc = -1
+        if bus is not None:
+            rc = self.lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(self.h))
+        if rc != 0:
+            rc = self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h))
+        if rc != 0:
+            raise RuntimeError(f"no NVML handle for device {index} (bus {bus}): {rc}")
+        reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self._reasons = reasons or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def clock(self):
+        v = self.ct.c_uint()
+        self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, self.ct.byref(v))
+        return v.value
+
+    def max_clock(self):
+        v = self.ct.c_uint()
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, self.ct.byref(v))
+        return v.value
+
+    def reasons(self):
+        v = self.ct.c_ulonglong()
+        self._reasons(self.h, self.ct.byref(v))
+        return v.value
+
+
 class Clocks:
-    """SM clock and throttle-reason sampling (NVML, every ~5 ms) in a thread
-    during the timed region; falls back to nvidia-smi if NVML is missing."""
+    """SM clock and clock-event-reason sampling (NVML, every ~5 ms) in a
+    thread during the timed region."""
     REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
                "sw_power_cap": 0x4}
 
@@ -95,28 +141,29 @@ class Clocks:
         self.thread = None
         self.max_mhz = None
         self.t0 = None
+        self.error = None
 
-    def _run(self):
-        import pynvml
-        h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
-        self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
-        while not self.stop_flag:
-            sm = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
-            r = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
-            if self.t0 is not None:
-                self.samples.append((sm, r))
-            time.sleep(0.005)
+    def _run(self, nv):
+        try:
+            self.max_mhz = nv.max_clock()
+            while not self.stop_flag:
+                sm, r = nv.clock(), nv.reasons()
+                if self.t0 is not None:
+                    self.samples.append((sm, r))
+                time.sleep(0.005)
+        except Exception as e:      # reported in the JSON line instead of the clocks
+            self.error = f"{type(e).__name__}: {e}"[:200]
 
     def start(self):
         try:
             import threading
-            import pynvml
-            pynvml.nvmlInit()
-            self.thread = threading.Thread(target=self._run, daemon=True)
+            nv = _NVML(self.index)
+            self.thread = threading.Thread(target=self._run, args=(nv,), daemon=True)
             self.thread.start()
             time.sleep(0.02)          # the sampler is running before the timed region starts
-        except Exception:
+        except Exception as e:
             self.thread = None
+            self.error = f"{type(e).__name__}: {e}"[:200]
 
     def mark(self):
         """Start of the timed region: samples from here on are kept."""
@@ -124,11 +171,11 @@ class Clocks:
 
     def stop(self):
         if self.thread is None:
-            return None
+            return {"error": self.error} if self.error else None
         self.stop_flag = True
         self.thread.join(timeout=2)
         if not self.samples:
-            return None
+            return {"error": self.error or "no samples"}
         sm = [s for s, _ in self.samples]
         reasons = sorted({n for _, r in self.samples for n, bit in self.REASONS.items() if r & bit})
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": self.max_mhz, "reasons": reasons,
@@ -137,9 +184,11 @@ class Clocks:
 
 # ------------------------------------------------------------ the workload
 class Workload:
-    """Device-resident inputs of one replica plus everything the step needs."""
+    """Device-resident inputs of one replica of a named workload plus the
+    buffers a step needs. Storage dtypes of the volume and the TF can be
+    changed (the FP32 form is the plain one)."""
 
-    def __init__(self, name, device, tf_immediate=False):
+    def __init__(self, name, device, tf_immediate=False, vol_dtype="float32", tf_dtype="float32"):
         import torch
 
         import paper_2107_12672_b300 as dvr
@@ -148,40 +197,75 @@ class Workload:
         self.torch = torch
         w = syn.workload(name)
         self.w = w
+        self.name = name
         self.device = device
-        self.vol = [torch.as_tensor(v).to(device) for v in w.volumes]
-        self.tf = torch.as_tensor(w.tf).to(device).contiguous()
-        self.params = torch.as_tensor(w.orbit.astype(np.float32)).to(device).contiguous()
+        vdt = getattr(torch, vol_dtype)
+        tdt = getattr(torch, tf_dtype)
+        if name == "ea_fp16_1024":
+            w.volumes = [None]
+            self.vol = [syn.large_volume(w.target["n"], device=device).to(vdt)]
+        else:
+            self.vol = [torch.as_tensor(v).to(device=device, dtype=vdt) for v in w.volumes]
+        self.ea = w.model == "emission_absorption"
+        self.tf = torch.as_tensor(w.tf).to(device=device, dtype=tdt).contiguous() if self.ea else None
         self.scene = dvr.Scene.make(self.vol, self.tf, w.model, w.views)
-        self.eye = torch.empty((len(w.views), 3), device=device)
+        self.orbit = w.orbit is not None
+        if self.orbit:
+            self.params = torch.as_tensor(w.orbit.astype(np.float32)).to(device).contiguous()
+            self.eye = torch.empty((len(w.views), 3), device=device)
+            dvr.orbit_eye(self.params, eye=self.eye)
+        else:
+            self.eye = torch.as_tensor(w.eye).to(device).contiguous()
         self.image = torch.empty((self.scene.pixels, self.scene.channels), device=device)
         self.aux = torch.empty((self.scene.pixels, 2), device=device)
         self.gimg = torch.empty_like(self.image)
         self.loss = torch.zeros(1, device=device)
-        self.g_tf = torch.zeros_like(self.tf)
-        self.g_eye = torch.zeros_like(self.eye)
-        self.g_par = torch.zeros_like(self.params)
+        self.want = tuple({"volume": "volume", "tf": "tf", "camera": "eye"}[g] for g in w.grads)
+        self.grads = {}
+        if "volume" in self.want:
+            self.grads["volume"] = [torch.zeros(v.shape, device=device) for v in self.vol]
+        if "tf" in self.want:
+            self.grads["tf"] = torch.zeros((self.tf.shape[0], 4), device=device)
+        if "eye" in self.want:
+            self.grads["eye"] = torch.zeros_like(self.eye)
+            if self.orbit:
+                self.g_par = torch.zeros_like(self.params)
         self.count = torch.zeros(1, dtype=torch.int64, device=device)
         self.tf_immediate = tf_immediate
-        # target: the same view rendered with a second transfer function
-        tft = torch.as_tensor(w.target["tf"]).to(device).contiguous()
-        dvr.orbit_eye(self.params, eye=self.eye)
-        tscene = dvr.Scene.make(self.vol, tft, w.model, w.views)
-        self.target, _ = dvr.forward(None, None, None, None, self.eye, w.step_voxels, scene=tscene)
+        # target image: the same views with the second TF or the second volume
+        if "tf" in w.target:
+            tft = torch.as_tensor(w.target["tf"]).to(device=device, dtype=tdt).contiguous()
+            tscene = dvr.Scene.make(self.vol, tft, w.model, w.views)
+        elif "volume" in w.target:
+            tv = [torch.as_tensor(w.target["volume"]).to(device=device, dtype=vdt)]
+            tscene = dvr.Scene.make(tv, self.tf, w.model, w.views)
+        else:
+            tscene = None
+        if tscene is not None:
+            self.target, _ = dvr.forward(None, None, None, None, self.eye, w.step_voxels, scene=tscene)
+        else:
+            self.target = torch.zeros_like(self.image)
         dvr.forward(None, None, None, None, self.eye, w.step_voxels, scene=self.scene, image=self.image,
                     aux=self.aux, sample_count=self.count)
         torch.cuda.synchronize()
         self.samples_per_pass = int(self.count.item())
+        self.launches_per_step = 3 + (2 if self.orbit else 0)
+
+    def zero(self):
+        self.loss.zero_()
+        for k, g in self.grads.items():
+            for t in (g if isinstance(g, list) else [g]):
+                t.zero_()
+        if self.orbit and "eye" in self.want:
+            self.g_par.zero_()
 
     def step(self, ev=None):
-        """One pass: 5 kernels of the library. `ev` = (fwd_start, fwd_end,
-        bwd_start, bwd_end) events to bracket the two march kernels."""
+        """One pass of the path. `ev` = (fwd_start, fwd_end, bwd_start,
+        bwd_end) events bracket the two march kernels."""
         dvr, w = self.dvr, self.w
-        self.loss.zero_()
-        self.g_tf.zero_()
-        self.g_eye.zero_()
-        self.g_par.zero_()
-        dvr.orbit_eye(self.params, eye=self.eye)
+        self.zero()
+        if self.orbit:
+            dvr.orbit_eye(self.params, eye=self.eye)
         if ev:
             ev[0].record()
         dvr.forward(None, None, None, None, self.eye, w.step_voxels, scene=self.scene, image=self.image,
@@ -191,27 +275,129 @@ class Workload:
         dvr.loss_l2(self.image, self.target, 1.0 / self.image.numel(), grad_image=self.gimg, loss=self.loss)
         if ev:
             ev[2].record()
-        dvr.backward(None, None, None, None, self.eye, w.step_voxels, self.aux, self.gimg,
-                     scene=self.scene, grads={"tf": self.g_tf, "eye": self.g_eye}, want=("tf", "eye"),
-                     tf_immediate=self.tf_immediate)
+        dvr.backward(None, None, None, None, self.eye, w.step_voxels, self.aux, self.gimg, scene=self.scene,
+                     grads=self.grads, want=self.want, tf_immediate=self.tf_immediate)
         if ev:
             ev[3].record()
-        dvr.orbit_eye_backward(self.params, self.g_eye, grad_params=self.g_par)
+        if self.orbit and "eye" in self.want:
+            dvr.orbit_eye_backward(self.params, self.grads["eye"], grad_params=self.g_par)
 
-    LAUNCHES_PER_STEP = 5
+    def describe(self):
+        w = self.w
+        v = self.vol[0]
+        return {
+            "workload": self.name,
+            "volume": f"{'x'.join(str(s) for s in reversed(v.shape))} {str(v.dtype).replace('torch.', '')}",
+            "model": w.model,
+            "tf_rows": int(self.tf.shape[0]) if self.tf is not None else 0,
+            "tf_dtype": str(self.tf.dtype).replace("torch.", "") if self.tf is not None else None,
+            "views": len(w.views),
+            "pixels": self.scene.pixels,
+            "step_voxels": w.step_voxels,
+            "gradients": list(w.grads),
+            "samples_per_pass": self.samples_per_pass,
+            "note": w.note,
+        }
 
 
 def algorithmic_bytes(wl, kernel):
     """Bytes the method must move per launch: 8 trilinear corners per sample
-    (element size of the volume) plus per-pixel image/aux/seed traffic."""
+    (element size of the volume) plus per-pixel image/aux/seed traffic; the
+    adjoint adds 8 FP32 read-modify-writes per sample when it scatters the
+    volume gradient."""
     e = wl.vol[0].element_size()
     px = wl.scene.pixels
-    if kernel == "forward":
-        return wl.samples_per_pass * 8 * e + px * (16 + 8)
-    return wl.samples_per_pass * 8 * e + px * (16 + 8)
+    b = wl.samples_per_pass * 8 * e + px * (4 * wl.scene.channels + 8)
+    if kernel == "backward" and "volume" in wl.want:
+        b += wl.samples_per_pass * 8 * 4 * 2
+    return b
+
+
+def accuracy(wl):
+    """Errors of one forward + adjoint against the FP64 oracle on identical
+    inputs (the workload's seeded eye positions; volume and TF as stored on
+    the device). Relative per element to (|ref| + max|ref|), as in the
+    parity tests; untimed."""
+    import torch
+
+    import oracle
+    dvr, w = wl.dvr, wl.w
+    eye = torch.as_tensor(w.eye).to(wl.device).contiguous()
+    img, aux = dvr.forward(None, None, None, None, eye, w.step_voxels, scene=wl.scene)
+    G = torch.randn(img.shape, device=wl.device, generator=torch.Generator(device=wl.device).manual_seed(1))
+    want = tuple(x for x in wl.want)
+    g = dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=wl.scene, want=want)
+    torch.cuda.synchronize()
+    vol64 = wl.vol[0].float().cpu().numpy()
+    tf64 = wl.tf.double().cpu().numpy() if wl.tf is not None else None
+    Gh = G.cpu().numpy()
+    imgh = img.cpu().numpy()
+
+    def rel(a, b):
+        a = np.asarray(a, np.float64)
+        return float((np.abs(a - b) / (np.abs(b) + np.abs(b).max())).max())
+
+    out = {"reference": "FP64 oracle, same stored inputs, fixed eye positions",
+           "definition": "max_i |gpu - ref| / (|ref| + max|ref|)"}
+    off = 0
+    errs_img, ref_tf, ref_eye = [], None, []
+    for k, view in enumerate(w.views[:4]):
+        n = view.width * view.height
+        ri, _, _ = oracle.render(vol64, tf64, w.model, view, w.eye[k], w.step_voxels)
+        errs_img.append(rel(imgh[off:off + n], ri))
+        ow = tuple(x for x in want if x != "volume")
+        rg = oracle.backward(vol64, tf64, w.model, view, w.eye[k], w.step_voxels, Gh[off:off + n], want=ow)
+        if "tf" in rg:
+            ref_tf = rg["tf"] if ref_tf is None else ref_tf + rg["tf"]
+        if "eye" in rg:
+            ref_eye.append((k, rg["eye"]))
+        off += n
+    out["image"] = max(errs_img)
+    if len(w.views) <= 4:
+        if ref_tf is not None:
+            out["grad_tf"] = rel(g["tf"].cpu().numpy(), ref_tf)
+    if ref_eye:
+        out["grad_eye"] = max(rel(g["eye"].cpu().numpy()[k], r) for k, r in ref_eye)
+    out["views_checked"] = min(4, len(w.views))
+    return out
 
 
 # -------------------------------------------------------------- our arm
+def time_steps(wl, K, W, flush, clocks=None, world=1):
+    """W untimed steps, then K steps each bracketed by CUDA events (L2 flushed
+    between steps, outside the brackets). Returns per-step, forward and
+    adjoint milliseconds and the wall time of the timed region."""
+    import torch
+    import torch.distributed as dist
+    for _ in range(W):
+        wl.step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+        clocks.mark()
+    t0 = time.perf_counter()
+    for k in range(K):
+        flush.zero_()                     # evict the volume from L2 between steps
+        st[k].record()
+        wl.step(evs[k])
+        en[k].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks is not None else None
+    step_ms = float(np.mean([s.elapsed_time(e) for s, e in zip(st, en)]))
+    fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    bwd_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))
+    return step_ms, fwd_ms, bwd_ms, wall, clk
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -226,36 +412,8 @@ def run_ours(args):
 
     wl = Workload(args.workload, dev, args.tf_immediate)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-
-    for _ in range(args.warmup):
-        wl.step()
-    torch.cuda.synchronize()
-
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
-    st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    clocks = Clocks(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    clocks.mark()
-    t0 = time.perf_counter()
-    for k in range(K):
-        flush.zero_()                     # evict the volume from L2 between steps
-        st[k].record()
-        wl.step(evs[k])
-        en[k].record()
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-
-    step_ms = float(np.mean([s.elapsed_time(e) for s, e in zip(st, en)]))
-    fwd_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
-    bwd_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))
+    step_ms, fwd_ms, bwd_ms, wall, clk = time_steps(wl, K, args.warmup, flush, Clocks(local), world)
     if world > 1:
         t = torch.tensor([step_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -267,15 +425,33 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(wl, args, world)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl.w, budget_s=12.0)
+    cpu = acc = variants = None
+    if rank == 0 and world == 1:
+        if not args.no_accuracy:
+            acc = accuracy(wl)
+        if not args.no_cpu_baseline and wl.w.volumes[0] is not None:
+            cpu = cpu_baseline(wl.w, budget_s=12.0)
+        if not args.no_variants and wl.ea:
+            variants = {}
+            for vd, td in (("bfloat16", "float16"),):
+                wv = Workload(args.workload, dev, args.tf_immediate, vol_dtype=vd, tf_dtype=td)
+                sm, fm, bm, _, _ = time_steps(wv, K, args.warmup, flush)
+                variants[f"volume_{vd}_tf_{td}"] = {
+                    "value": round(wv.samples_per_pass / (sm * 1e-3) / 1e9, 4), "unit": "Gsamples/s",
+                    "ms_per_step": round(sm, 4), "forward_ms": round(fm, 4), "adjoint_ms": round(bm, 4),
+                    "accuracy": None if args.no_accuracy else accuracy(wv),
+                    "note": "errors include the rounding of the stored volume and TF"}
+                del wv
 
     if rank == 0:
         hbm, src = peaks()
         dom = "backward" if bwd_ms >= fwd_ms else "forward"
         dur = bwd_ms if dom == "backward" else fwd_ms
         achieved = algorithmic_bytes(wl, dom) / (dur * 1e-3) / 1e9
+        cfg = wl.describe()
+        cfg.update({"l2": "flushed between timed steps (512 MiB write)",
+                    "tf_accumulation": "immediate" if args.tf_immediate else "delayed (shared memory)",
+                    "parallelism": f"replicas x{world}"})
         line = {
             "metric": METRIC,
             "value": round(value, 4),
@@ -287,20 +463,9 @@ def run_ours(args):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32",
-            "data": "synthetic (seeded 3-octave value noise, seeded TF; no dataset)",
-            "config": {
-                "workload": args.workload,
-                "volume": "256^3 f32 value noise",
-                "tf_rows": int(wl.tf.shape[0]),
-                "image": "512x512 perspective, distance 2.5, fov 45 deg",
-                "step_voxels": wl.w.step_voxels,
-                "gradients": ["tf", "camera yaw/pitch/distance"],
-                "samples_per_pass": samples,
-                "l2": "flushed between timed steps (512 MiB write)",
-                "tf_accumulation": "immediate" if args.tf_immediate else "delayed (shared memory)",
-                "parallelism": f"replicas x{world}",
-            },
+            "dtype": "f32" if wl.vol[0].dtype == torch.float32 else str(wl.vol[0].dtype).replace("torch.", ""),
+            "data": "synthetic (seeded generators; no dataset)",
+            "config": cfg,
             "forward_ms": round(fwd_ms, 4),
             "adjoint_ms": round(bwd_ms, 4),
             "forward_gsamples_s": round(samples / (fwd_ms * 1e-3) / 1e9, 3),
@@ -317,8 +482,10 @@ def run_ours(args):
                 "traffic": profiled_traffic(f"{dom}_{args.workload}"),
                 "bytes_per_sample": 8 * wl.vol[0].element_size(),
             },
+            "accuracy": acc,
+            "storage_variants": variants,
             "clocks": clk,
-            "gpu_launches": Workload.LAUNCHES_PER_STEP * K,
+            "gpu_launches": wl.launches_per_step * K,
             "e2e": e2e,
             "cpu_baseline": cpu,
         }
@@ -329,26 +496,28 @@ def run_ours(args):
 
 def run_e2e(wl, args, world):
     """Same metric through the public API with host buffers: every step
-    copies its inputs (volume, TF, orbit parameters) from pinned host memory
+    copies its inputs (volume, TF, camera parameters) from pinned host memory
     and reads back the loss and the gradients."""
     import torch
-    dvr = wl.dvr
-    h_vol = torch.as_tensor(wl.w.volumes[0]).pin_memory()
-    h_tf = torch.as_tensor(wl.w.tf).pin_memory()
-    h_par = torch.as_tensor(wl.w.orbit.astype(np.float32)).pin_memory()
-    o_loss = torch.empty(1).pin_memory()
-    o_tf = torch.empty_like(h_tf).pin_memory()
-    o_par = torch.empty_like(h_par).pin_memory()
-    d_vol = wl.vol[0]
+    h_in = [(wl.vol[0], wl.vol[0].cpu().pin_memory())]
+    if wl.tf is not None:
+        h_in.append((wl.tf, wl.tf.cpu().pin_memory()))
+    cam = wl.params if wl.orbit else wl.eye
+    h_in.append((cam, cam.cpu().pin_memory()))
+    outs = [wl.loss]
+    for k, g in wl.grads.items():
+        if k == "eye" and wl.orbit:
+            outs.append(wl.g_par)
+        else:
+            outs.extend(g if isinstance(g, list) else [g])
+    h_out = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
 
     def one():
-        d_vol.copy_(h_vol, non_blocking=True)
-        wl.tf.copy_(h_tf, non_blocking=True)
-        wl.params.copy_(h_par, non_blocking=True)
+        for d, h in h_in:
+            d.copy_(h, non_blocking=True)
         wl.step()
-        o_loss.copy_(wl.loss, non_blocking=True)
-        o_tf.copy_(wl.g_tf, non_blocking=True)
-        o_par.copy_(wl.g_par, non_blocking=True)
+        for h, o in zip(h_out, outs):
+            h.copy_(o, non_blocking=True)
         torch.cuda.synchronize()
 
     for _ in range(max(3, args.warmup)):
@@ -357,17 +526,18 @@ def run_e2e(wl, args, world):
     for _ in range(args.steps):
         one()
     dt = (time.perf_counter() - t0) / args.steps
-    h2d = h_vol.numel() * 4 + h_tf.numel() * 4 + h_par.numel() * 4
-    d2h = 4 + o_tf.numel() * 4 + o_par.numel() * 4
+    h2d = sum(h.numel() * h.element_size() for _, h in h_in)
+    d2h = sum(h.numel() * h.element_size() for h in h_out)
     return {"value": round(world * wl.samples_per_pass / dt / 1e9, 4), "unit": "Gsamples/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 4)}
 
 
 # ------------------------------------------------------ the CPU oracle arm
 class OraclePass:
-    """The oracle's forward + stored-state adjoint (with the L2 seed and the
-    orbit chain) on a strided subset of the workload's rows; the target image
-    is rendered once, untimed, as on the GPU side."""
+    """The oracle's forward + stored-state adjoint (with the L2 seed, and the
+    orbit chain when the camera is orbit-parameterised) on a strided subset
+    of the rows of the workload's first view; the target image is rendered
+    once, untimed, as on the GPU side."""
 
     def __init__(self, w, stride):
         import oracle
@@ -376,9 +546,17 @@ class OraclePass:
         self.w = w
         self.view = w.views[0]
         self.stride = stride
-        self.eye = oracle.orbit_eye(w.orbit.astype(np.float32).astype(np.float64))[0]
-        self.target, _, _ = oracle.render(w.volumes[0], w.target["tf"], w.model, self.view, self.eye,
-                                          w.step_voxels)
+        if w.orbit is not None:
+            self.eye = oracle.orbit_eye(w.orbit.astype(np.float32).astype(np.float64))[0]
+        else:
+            self.eye = w.eye[0].astype(np.float64)
+        self.vol = w.volumes[0] if w.volumes and w.volumes[0] is not None else None
+        if self.vol is None:
+            raise ValueError("the oracle baseline needs the volume on the host")
+        tf_t = w.target.get("tf", w.tf)
+        vol_t = w.target.get("volume", self.vol)
+        self.target, _, _ = oracle.render(vol_t, tf_t, w.model, self.view, self.eye, w.step_voxels)
+        self.want = tuple({"volume": "volume", "tf": "tf", "camera": "eye"}[g] for g in w.grads)
         self.phase = 0
 
     def __call__(self):
@@ -386,11 +564,11 @@ class OraclePass:
         rows = np.arange(self.phase, view.height, self.stride)
         self.phase = (self.phase + 1) % self.stride
         pix = (rows[:, None] * view.width + np.arange(view.width)[None, :]).reshape(-1).astype(np.int64)
-        img, N, _ = o.render(w.volumes[0], w.tf, w.model, view, self.eye, w.step_voxels, pix=pix)
+        img, N, _ = o.render(self.vol, w.tf, w.model, view, self.eye, w.step_voxels, pix=pix)
         G = 2.0 * (img - self.target[pix]) / self.target.size
-        g = o.backward(w.volumes[0], w.tf, w.model, view, self.eye, w.step_voxels, G, pix=pix,
-                       want=("tf", "eye"))
-        o.orbit_eye_backward(w.orbit, g["eye"][None])
+        g = o.backward(self.vol, w.tf, w.model, view, self.eye, w.step_voxels, G, pix=pix, want=self.want)
+        if w.orbit is not None and "eye" in g:
+            o.orbit_eye_backward(w.orbit, g["eye"][None])
         return int(N.sum()), pix.size
 
 
