@@ -94,9 +94,14 @@ extern "C" {
 #define DVR_F16 1
 #define DVR_BF16 2
 
-/* optical models (Sec. 3.1; Sec. 5.3 absorption-only) */
+/* optical models (Sec. 3.1; Sec. 5.3 absorption-only; Sec. 5.4 colour volume) */
 #define DVR_ABSORPTION 0
 #define DVR_EMISSION_ABSORPTION 1
+/* pre-shaded colour volume: every vertex holds (r, g, b, tau), layout
+ * [nz][ny][nx][4], interpolated trilinearly per channel, no transfer
+ * function; blended and written like DVR_EMISSION_ABSORPTION; its volume
+ * gradient has the same [nz][ny][nx][4] layout */
+#define DVR_COLOR_VOLUME 2
 
 /* dvr_backward flags */
 /* accumulate the TF gradient with one global atomic per sample and
@@ -104,8 +109,9 @@ extern "C" {
  * shared-memory accumulation ("adjoint-delayed") */
 #define DVR_FLAG_TF_IMMEDIATE 1u
 
-/* One scalar volume. `data` is a device pointer to nx*ny*nz samples of
- * `dtype`, layout [nz][ny][nx]; each of nx, ny, nz >= 2. */
+/* One volume. `data` is a device pointer to nx*ny*nz samples of `dtype`,
+ * layout [nz][ny][nx] (4 per vertex, [nz][ny][nx][4], for
+ * DVR_COLOR_VOLUME, aligned to 4 samples); each of nx, ny, nz >= 2. */
 typedef struct {
     int32_t nx, ny, nz;
     int32_t dtype;           /* DVR_F32, DVR_F16 or DVR_BF16 */
@@ -144,11 +150,11 @@ DVR_API const char* dvr_last_error(void);
  *
  * volumes[n_volumes]   host array of volume descriptors (1 <= n_volumes <= 16)
  * tf                   host pointer to the TF descriptor (EA model), else NULL
- * model                DVR_ABSORPTION or DVR_EMISSION_ABSORPTION
+ * model                DVR_ABSORPTION, DVR_EMISSION_ABSORPTION or DVR_COLOR_VOLUME
  * views[n_views]       host array, 1 <= n_views <= 4096
  * eye                  device float[n_views][3], camera positions
  * step_voxels          sample spacing in voxels, > 0
- * image                device float[P][C], C = 4 (EA) or 1 (absorption),
+ * image                device float[P][C], C = 1 (absorption) or 4,
  *                      P = max over views of pixel_offset + width*height
  * aux                  device float[P][2] or NULL: optical depth
  *                      S = sum_i dt tau_i of each ray as an unevaluated sum
@@ -169,7 +175,8 @@ DVR_API int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_
  * and accumulates:
  *
  * grad_volumes         host array [n_volumes] of device float pointers
- *                      (each [nz][ny][nx] float32, or NULL), or NULL
+ *                      (each [nz][ny][nx] float32, [nz][ny][nx][4] for the
+ *                      colour volume, or NULL), or NULL
  * grad_tf              device float[R][4] or NULL (EA model only)
  * grad_eye             device float[n_views][3] or NULL
  * grad_step            device float[1] or NULL: dL/d(step_voxels)

@@ -26,7 +26,8 @@ _lib = None
 
 ABSORPTION = 0
 EMISSION_ABSORPTION = 1
-MODELS = {"absorption": ABSORPTION, "emission_absorption": EMISSION_ABSORPTION}
+COLOR_VOLUME = 2
+MODELS = {"absorption": ABSORPTION, "emission_absorption": EMISSION_ABSORPTION, "color": COLOR_VOLUME}
 
 CFLAGS = ["-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
           "-std=c11"]
@@ -90,8 +91,9 @@ class _Common:
             vol = vol.astype(np.float64)
         self.vol = np.ascontiguousarray(vol)
         self.vf32 = int(self.vol.dtype == np.float32)
-        self.nz, self.ny, self.nx = self.vol.shape
         self.model = MODELS[model] if isinstance(model, str) else int(model)
+        # colour volumes are [nz][ny][nx][4] (r, g, b, tau per vertex)
+        self.nz, self.ny, self.nx = self.vol.shape[:3]
         if self.model == EMISSION_ABSORPTION:
             self.tf = _f64(tf)
             self.R = self.tf.shape[0]
@@ -107,7 +109,7 @@ class _Common:
         self.lens = cv(view.ortho_height if view.ortho else view.tan_half_fov_y)
         self.eye = np.array([cv(e) for e in np.asarray(eye).reshape(3)], dtype=np.float64)
         self.step = cv(step)
-        self.nc = 4 if self.model == EMISSION_ABSORPTION else 1
+        self.nc = 1 if self.model == ABSORPTION else 4
 
     def head(self):
         return (_p(self.vol), self.vf32, self.nx, self.ny, self.nz, _p(self.tf), self.R, self.model,

@@ -50,6 +50,7 @@
 
 #define ORA_ABSORPTION 0
 #define ORA_EMISSION_ABSORPTION 1
+#define ORA_COLOR_VOLUME 2      /* pre-shaded (r, g, b, tau) per vertex, Sec. 5.4 */
 
 /* Shape of the grid and the discretisation of the ray (Sec. 3.1). */
 typedef struct {
@@ -189,8 +190,19 @@ static void camera_ray(const cam_t* c, const grid_t* G, int px, int py, int fp32
  * the derivative of the density w.r.t. the grid coordinate (zero along an
  * axis where x was clamped to the box).
  */
+static double interpolate_strided(const void* V, const grid_t* G, const double x[3], int stride, int ch,
+                                  long idx[8], double wt[8], double dg[3]);
+
 static double interpolate(const void* V, const grid_t* G, const double x[3],
                           long idx[8], double wt[8], double dg[3])
+{
+    return interpolate_strided(V, G, x, 1, 0, idx, wt, dg);
+}
+
+/* The same for channel `ch` of a volume with `stride` values per vertex
+ * (vertex idx holds V[idx*stride .. idx*stride+stride-1]). */
+static double interpolate_strided(const void* V, const grid_t* G, const double x[3], int stride, int ch,
+                                  long idx[8], double wt[8], double dg[3])
 {
     int j[3];
     double fr[3];
@@ -211,7 +223,7 @@ static double interpolate(const void* V, const grid_t* G, const double x[3],
         int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
         idx[c] = ((long)(j[2] + cz) * G->n[1] + (j[1] + cy)) * (long)G->n[0] + (j[0] + cx);
         wt[c] = (cx ? fr[0] : 1.0 - fr[0]) * (cy ? fr[1] : 1.0 - fr[1]) * (cz ? fr[2] : 1.0 - fr[2]);
-        val[c] = vget(V, G, idx[c]);
+        val[c] = vget(V, G, idx[c] * stride + ch);
         d += wt[c] * val[c];
     }
     for (int a = 0; a < 3; ++a) {
@@ -262,6 +274,7 @@ typedef struct {
     double x[3], d, c[4], tau, alpha;
     long idx[8];
     double wt[8], dg[3];
+    double dg4[4][3];   /* colour volume: d(channel)/d(grid coordinate) */
     int k, slope;
     double fr;
     double ge;        /* binary32 error bound of the grid coordinates (ambiguity bounds only) */
@@ -292,6 +305,17 @@ static void eval_sample(const scene_t* s, const ray_t* ry, int i, sample_t* sm)
 {
     double ti = (double)i * s->G.dt;
     for (int a = 0; a < 3; ++a) sm->x[a] = ry->xo[a] + ti * ry->w[a];
+    if (s->model == ORA_COLOR_VOLUME) {
+        /* Sec. 5.4: the volume holds (r, g, b, tau) per vertex, no TF */
+        for (int ch = 0; ch < 4; ++ch)
+            sm->c[ch] = interpolate_strided(s->V, &s->G, sm->x, 4, ch, sm->idx, sm->wt, sm->dg4[ch]);
+        sm->d = sm->c[3];
+        sm->tau = sm->c[3];
+        sm->k = 0; sm->fr = 0.0; sm->slope = 1;
+        for (int a = 0; a < 3; ++a) sm->dg[a] = sm->dg4[3][a];
+        sm->alpha = 1.0 - exp(-s->G.dt * sm->tau);
+        return;
+    }
     sm->d = interpolate(s->V, &s->G, sm->x, sm->idx, sm->wt, sm->dg);
     if (s->model == ORA_EMISSION_ABSORPTION) {
         transfer(s->tf, s->R, sm->d, sm->c, &sm->k, &sm->fr, &sm->slope);
@@ -345,7 +369,7 @@ static void setup_scene(scene_t* s, const void* V, int vf32, int nx, int ny, int
     for (int a = 0; a < 3; ++a) s->cam.eye[a] = eye[a];
 }
 
-static int channels(int model) { return model == ORA_EMISSION_ABSORPTION ? 4 : 1; }
+static int channels(int model) { return model == ORA_ABSORPTION ? 1 : 4; }
 
 /*
  * Forward render of one view. `pix` lists the linear pixel indices to
@@ -413,7 +437,16 @@ int ora_interpolate(const double* V, int nx, int ny, int nz, const double* x, in
  * integer (a face between two cells, or a box face where the coordinate is
  * clamped), the jump of d(density)/d(g_a) across that face; 0 elsewhere.
  */
+static void face_jumps_strided(const void* V, const grid_t* G, const double x[3], double delta, int stride,
+                               int chn, double jump[3]);
+
 static void face_jumps(const void* V, const grid_t* G, const double x[3], double delta, double jump[3])
+{
+    face_jumps_strided(V, G, x, delta, 1, 0, jump);
+}
+
+static void face_jumps_strided(const void* V, const grid_t* G, const double x[3], double delta, int stride,
+                               int chn, double jump[3])
 {
     double g[3];
     for (int a = 0; a < 3; ++a) g[a] = (x[a] + G->half[a]) * G->inv_h;
@@ -447,7 +480,7 @@ static void face_jumps(const void* V, const grid_t* G, const double x[3], double
                 for (int o = 0; o < 3; ++o)
                     if (o != a) w *= bb[o] ? fr[o] : 1.0 - fr[o];
                 long idx = ((long)(j[2] + bb[2]) * G->n[1] + (j[1] + bb[1])) * (long)G->n[0] + (j[0] + bb[0]);
-                sum += w * vget(V, G, idx);
+                sum += w * vget(V, G, idx * stride + chn);
             }
             slope[sd] = sum;
         }
@@ -658,13 +691,26 @@ int ora_backward(const void* V, int vf32, int nx, int ny, int nz, const double* 
                 } else {
                     d_hat = tau_hat;
                 }
-                /* f_interpolate adjoint */
-                if (grad_vol)
-                    for (int c = 0; c < 8; ++c) atomic_add(&grad_vol[sm.idx[c]], sm.wt[c] * d_hat);
+                /* f_interpolate adjoint; gd = d(L)/d(grid coordinate) */
+                double gd[3];
+                if (model == ORA_COLOR_VOLUME) {
+                    if (grad_vol)
+                        for (int c = 0; c < 8; ++c)
+                            for (int ch = 0; ch < 4; ++ch)
+                                atomic_add(&grad_vol[sm.idx[c] * 4 + ch], sm.wt[c] * c_hat[ch]);
+                    for (int a = 0; a < 3; ++a) {
+                        gd[a] = 0.0;
+                        for (int ch = 0; ch < 4; ++ch) gd[a] += sm.dg4[ch][a] * c_hat[ch];
+                    }
+                } else {
+                    if (grad_vol)
+                        for (int c = 0; c < 8; ++c) atomic_add(&grad_vol[sm.idx[c]], sm.wt[c] * d_hat);
+                    for (int a = 0; a < 3; ++a) gd[a] = sm.dg[a] * d_hat;
+                }
                 double ti = (double)i * dt;
                 double xi_w = 0.0;
                 for (int a = 0; a < 3; ++a) {
-                    double x_hat = sm.dg[a] * d_hat * s.G.inv_h;
+                    double x_hat = gd[a] * s.G.inv_h;
                     xo_hat[a] += x_hat;
                     w_hat[a] += ti * x_hat;
                     xi_w += (double)i * ry.w[a] * x_hat;
@@ -676,10 +722,19 @@ int ora_backward(const void* V, int vf32, int nx, int ny, int nz, const double* 
                     double dx[3];
                     int any = 0;
                     double dgn[3];
-                    face_jumps(V, &s.G, sm.x, sm.ge, dgn);
-                    for (int a = 0; a < 3; ++a) {
-                        dx[a] = (fabs(sm.dg[a] * d_jump) + fabs(dgn[a] * d_hat)) * s.G.inv_h;
-                        any |= dx[a] != 0.0;
+                    if (model == ORA_COLOR_VOLUME) {
+                        for (int a = 0; a < 3; ++a) dx[a] = 0.0;
+                        for (int ch = 0; ch < 4; ++ch) {
+                            face_jumps_strided(V, &s.G, sm.x, sm.ge, 4, ch, dgn);
+                            for (int a = 0; a < 3; ++a) dx[a] += fabs(dgn[a] * c_hat[ch]) * s.G.inv_h;
+                        }
+                        for (int a = 0; a < 3; ++a) any |= dx[a] != 0.0;
+                    } else {
+                        face_jumps(V, &s.G, sm.x, sm.ge, dgn);
+                        for (int a = 0; a < 3; ++a) {
+                            dx[a] = (fabs(sm.dg[a] * d_jump) + fabs(dgn[a] * d_hat)) * s.G.inv_h;
+                            any |= dx[a] != 0.0;
+                        }
                     }
                     if (any) {
                         /* the camera adjoint is linear: bound each axis' part */
@@ -833,7 +888,18 @@ int ora_render_dual(const void* V, int vf32, int nx, int ny, int nz, const doubl
                 d = dadd(d, dmul(wt, dc(vget(V, G, idx))));
             }
             dual col[4];
-            if (model == ORA_EMISSION_ABSORPTION) {
+            if (model == ORA_COLOR_VOLUME) {
+                for (int ch = 0; ch < 4; ++ch) {
+                    col[ch] = dc(0.0);
+                    for (int c = 0; c < 8; ++c) {
+                        int b[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+                        dual wt = dc(1.0);
+                        for (int a = 0; a < 3; ++a) wt = dmul(wt, b[a] ? fr[a] : dsub(dc(1.0), fr[a]));
+                        long idx = ((long)(j[2] + b[2]) * G->n[1] + (j[1] + b[1])) * (long)G->n[0] + (j[0] + b[0]);
+                        col[ch] = dadd(col[ch], dmul(wt, dc(vget(V, G, idx * 4 + ch))));
+                    }
+                }
+            } else if (model == ORA_EMISSION_ABSORPTION) {
                 dual dcl = d;
                 if (dcl.v < 0.0) dcl = dc(0.0);
                 if (dcl.v > 1.0) dcl = dc(1.0);

@@ -17,7 +17,7 @@ LIB_PATH = os.environ.get("DVR_LIBRARY") or os.path.join(_HERE, "_lib", "libdvr.
 
 DVR_OK = 0
 DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
-DVR_ABSORPTION, DVR_EMISSION_ABSORPTION = 0, 1
+DVR_ABSORPTION, DVR_EMISSION_ABSORPTION, DVR_COLOR_VOLUME = 0, 1, 2
 DVR_FLAG_TF_IMMEDIATE = 1
 
 # every symbol include/dvr.h declares

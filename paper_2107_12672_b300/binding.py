@@ -22,7 +22,8 @@ from .synthetic import View
 __all__ = ["View", "Scene", "forward", "backward", "loss_l2", "orbit_eye", "orbit_eye_backward",
            "render", "orbit_camera", "split_views", "MODELS"]
 
-MODELS = {"absorption": _abi.DVR_ABSORPTION, "emission_absorption": _abi.DVR_EMISSION_ABSORPTION}
+MODELS = {"absorption": _abi.DVR_ABSORPTION, "emission_absorption": _abi.DVR_EMISSION_ABSORPTION,
+          "color": _abi.DVR_COLOR_VOLUME}
 _DTYPES = {torch.float32: _abi.DVR_F32, torch.float16: _abi.DVR_F16, torch.bfloat16: _abi.DVR_BF16}
 
 
@@ -70,11 +71,14 @@ class Scene:
         vd = (_abi.DvrVolume * len(volumes))()
         for i, v in enumerate(volumes):
             _require_cuda(v, f"volume {i}")
-            if v.dim() != 3:
+            if model == _abi.DVR_COLOR_VOLUME:
+                if v.dim() != 4 or v.shape[3] != 4:
+                    raise ValueError("a colour volume is a [nz][ny][nx][4] tensor")
+            elif v.dim() != 3:
                 raise ValueError("a volume is a 3-D tensor [nz][ny][nx]")
             if v.dtype not in _DTYPES:
                 raise ValueError(f"volume dtype {v.dtype} unsupported")
-            nz, ny, nx = v.shape
+            nz, ny, nx = v.shape[:3]
             vd[i] = _abi.DvrVolume(nx, ny, nz, _DTYPES[v.dtype], v.data_ptr())
         td = None
         if model == _abi.DVR_EMISSION_ABSORPTION:
@@ -93,7 +97,7 @@ class Scene:
                                  int(getattr(w, "volume_index", 0)), float(lens), 0, off)
             offsets.append(off)
             off += int(w.width) * int(w.height)
-        ch = 4 if model == _abi.DVR_EMISSION_ABSORPTION else 1
+        ch = 1 if model == _abi.DVR_ABSORPTION else 4
         return Scene(list(volumes), tf, model, list(views), vd, td, wd, off, ch, offsets)
 
     def tf_ref(self):

@@ -39,8 +39,9 @@ struct Common {
 int check_common(const dvr_volume* vols, int nvol, const dvr_tf* tf, int model, const dvr_view* views,
                  int nviews, const float* eye, float step, Common& c)
 {
-    if (model != DVR_ABSORPTION && model != DVR_EMISSION_ABSORPTION)
-        return fail(DVR_ERR_ARG, "model %d is not DVR_ABSORPTION or DVR_EMISSION_ABSORPTION", model);
+    if (model != DVR_ABSORPTION && model != DVR_EMISSION_ABSORPTION && model != DVR_COLOR_VOLUME)
+        return fail(DVR_ERR_ARG, "model %d is not DVR_ABSORPTION, DVR_EMISSION_ABSORPTION or DVR_COLOR_VOLUME",
+                    model);
     if (!vols || nvol < 1 || nvol > dvr::kMaxVolumes)
         return fail(DVR_ERR_ARG, "n_volumes %d outside [1, %d] or volumes is NULL", nvol, dvr::kMaxVolumes);
     if (!views || nviews < 1 || nviews > 4096)
@@ -60,8 +61,10 @@ int check_common(const dvr_volume* vols, int nvol, const dvr_tf* tf, int model, 
             return fail(DVR_ERR_DTYPE, "volume %d: dtype %d unsupported", i, v.dtype);
         if (v.dtype != c.dtype)
             return fail(DVR_ERR_DTYPE, "volume %d: all volumes of one call must share a dtype", i);
-        if (!aligned(v.data, v.dtype == DVR_F32 ? 4 : 2))
-            return fail(DVR_ERR_ARG, "volume %d: data is not aligned to its element size", i);
+        const size_t esz = v.dtype == DVR_F32 ? 4 : 2;
+        if (!aligned(v.data, model == DVR_COLOR_VOLUME ? 4 * esz : esz))
+            return fail(DVR_ERR_ARG, "volume %d: data is not aligned to its %s", i,
+                        model == DVR_COLOR_VOLUME ? "4-sample vertex" : "element size");
     }
     if (model == DVR_EMISSION_ABSORPTION) {
         if (!tf || !tf->rgba) return fail(DVR_ERR_ARG, "emission-absorption needs a transfer function");
@@ -73,6 +76,7 @@ int check_common(const dvr_volume* vols, int nvol, const dvr_tf* tf, int model, 
             return fail(DVR_ERR_ARG, "TF rows are not aligned (16 bytes for DVR_F32)");
         c.channels = 4;
     }
+    if (model == DVR_COLOR_VOLUME) c.channels = 4;
     c.pixels = 0;
     for (int i = 0; i < nviews; ++i) {
         const dvr_view& w = views[i];
@@ -158,7 +162,8 @@ int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, 
         p.image = image;
         p.aux = aux;
         p.sample_count = sample_count;
-        cudaError_t e = dvr::launch_forward(p, model, c.dtype, (cudaStream_t)stream);
+        cudaError_t e = model == DVR_COLOR_VOLUME ? dvr::launch_forward_color(p, c.dtype, (cudaStream_t)stream)
+                                                  : dvr::launch_forward(p, model, c.dtype, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "dvr_forward launch");
     }
     return DVR_OK;
@@ -182,7 +187,11 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
         return fail(DVR_ERR_ARG, "grad_tf needs the emission-absorption model");
     bool gvol = false;
     if (grad_volumes)
-        for (int i = 0; i < n_volumes; ++i) gvol |= grad_volumes[i] != nullptr;
+        for (int i = 0; i < n_volumes; ++i) {
+            gvol |= grad_volumes[i] != nullptr;
+            if (grad_volumes[i] && !aligned(grad_volumes[i], model == DVR_COLOR_VOLUME ? 16 : 4))
+                return fail(DVR_ERR_ARG, "grad volume %d is not aligned to its vertex", i);
+        }
     const int tfm = grad_tf ? ((flags & DVR_FLAG_TF_IMMEDIATE) ? dvr::kTFImmediate : dvr::kTFDelayed)
                             : dvr::kTFNone;
     const bool pos = grad_eye != nullptr || grad_step != nullptr;
@@ -206,7 +215,9 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
         p.grad_tf = grad_tf;
         p.grad_eye = grad_eye;
         p.grad_step = grad_step;
-        cudaError_t e = dvr::launch_backward(p, model, c.dtype, gvol, tfm, pos, (cudaStream_t)stream);
+        cudaError_t e = model == DVR_COLOR_VOLUME
+            ? dvr::launch_backward_color(p, c.dtype, gvol, pos, (cudaStream_t)stream)
+            : dvr::launch_backward(p, model, c.dtype, gvol, tfm, pos, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "dvr_backward launch");
     }
     return DVR_OK;

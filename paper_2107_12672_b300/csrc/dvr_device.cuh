@@ -429,6 +429,70 @@ __device__ __forceinline__ int find_view(const Params& p, int tile)
     return lo;
 }
 
+__device__ __forceinline__ float dot3(const float a[3], const float b[3])
+{
+    return fmaf(a[2], b[2], fmaf(a[1], b[1], a[0] * b[0]));
+}
+
+// Adjoint of f_camera for one ray: from (x^_o, w^) to e^.
+__device__ __forceinline__ void camera_adjoint(const Ray& R, int ortho, const float xo_hat[3],
+                                               const float w_in[3], float e_hat[3])
+{
+    const float xw = dot3(xo_hat, R.w);
+    float o_hat[3], w_hat[3];
+    // tn = (face - o_a) / w_a along the axis whose face set it
+    const float wa = R.axis == 0 ? R.w[0] : (R.axis == 1 ? R.w[1] : R.w[2]);
+    const float k = R.axis >= 0 ? xw / wa : 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const bool sel = a == R.axis;
+        o_hat[a] = xo_hat[a] - (sel ? k : 0.f);
+        w_hat[a] = fmaf(R.tn, xo_hat[a], w_in[a]) - (sel ? R.tn * k : 0.f);
+    }
+    float f_hat[3], r_hat[3], u_hat[3];
+    if (!ortho) {
+        const float ww = dot3(R.w, w_hat);
+        const float inv = 1.f / R.dl;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float dh = (w_hat[a] - R.w[a] * ww) * inv;
+            f_hat[a] = dh;
+            r_hat[a] = R.su * dh;
+            u_hat[a] = R.sv * dh;
+            e_hat[a] = o_hat[a];
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r_hat[a] = R.su * o_hat[a];
+            u_hat[a] = R.sv * o_hat[a];
+            f_hat[a] = w_hat[a];
+            e_hat[a] = o_hat[a];
+        }
+    }
+    // u = r x f
+    r_hat[0] += R.f[1] * u_hat[2] - R.f[2] * u_hat[1];
+    r_hat[1] += R.f[2] * u_hat[0] - R.f[0] * u_hat[2];
+    r_hat[2] += R.f[0] * u_hat[1] - R.f[1] * u_hat[0];
+    f_hat[0] += u_hat[1] * R.r[2] - u_hat[2] * R.r[1];
+    f_hat[1] += u_hat[2] * R.r[0] - u_hat[0] * R.r[2];
+    f_hat[2] += u_hat[0] * R.r[1] - u_hat[1] * R.r[0];
+    // r = q/|q|, q = (-f_z, 0, f_x)
+    if (!R.degenerate) {
+        const float rr = dot3(R.r, r_hat);
+        const float inv = 1.f / R.ql;
+        const float q0 = (r_hat[0] - R.r[0] * rr) * inv;
+        const float q2 = (r_hat[2] - R.r[2] * rr) * inv;
+        f_hat[2] -= q0;
+        f_hat[0] += q2;
+    }
+    // f = -e/|e|
+    const float ff = dot3(R.f, f_hat);
+    const float inv = 1.f / R.el;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) e_hat[a] -= (f_hat[a] - R.f[a] * ff) * inv;
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll

@@ -31,6 +31,7 @@ __all__ = [
     "gaussian_blobs",
     "value_noise",
     "random_tf",
+    "color_volume",
     "fibonacci_sphere",
     "View",
     "Workload",
@@ -123,6 +124,14 @@ def value_noise(n: int, seed: int, cells=(4, 8, 16), amps=(1.0, 0.5, 0.25),
     lo, hi = out.min(), out.max()
     out.sub_(lo).div_(hi - lo)
     return out
+
+
+def color_volume(n: int, seed: int, tau_max: float = 20.0, dtype=np.float32) -> np.ndarray:
+    """[n][n][n][4] pre-shaded colour volume: value noise per channel
+    (seeds seed..seed+3), colours in [0, 1], absorption in [0, tau_max]."""
+    chans = [value_noise(n, seed=seed + k, dtype=np.float64) for k in range(4)]
+    chans[3] = chans[3] * tau_max
+    return np.stack(chans, axis=-1).astype(dtype)
 
 
 def random_tf(R: int, seed: int, tau_max: float = 50.0, dtype=np.float32) -> np.ndarray:

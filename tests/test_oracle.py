@@ -375,3 +375,64 @@ def test_kink_ambiguity_bounds_one_sided_derivatives():
     g2 = oracle.backward(v2, tf, "emission_absorption", view, eye, 0.5, G, fp32=False,
                          want=("volume",), margin=1.0)
     assert g2["volume_ambiguity"].max() == 0
+
+
+# ------------------------------------------------------- pre-shaded colour volume
+def test_color_volume_equals_ea_for_affine_tf():
+    """Sec. 5.4 colour volume: per-vertex (r, g, b, tau), interpolated. An
+    affine TF (R = 2) commutes with trilinear interpolation for densities in
+    [0, 1], so the colour volume TF(v) renders exactly as the EA model."""
+    rng = np.random.default_rng(4)
+    n = 9
+    v = rng.uniform(0.0, 1.0, (n, n, n))
+    tf = np.array([[0.1, 0.7, 0.3, 1.5], [0.9, 0.2, 0.6, 6.0]])
+    cv = tf[0][None, None, None, :] * (1 - v[..., None]) + tf[1][None, None, None, :] * v[..., None]
+    view = syn.View(13, 10)
+    eye = [0.8, -0.6, 1.7]
+    a, Na, _ = oracle.render(v, tf, "emission_absorption", view, eye, 0.5)
+    b, Nb, _ = oracle.render(cv, None, "color", view, eye, 0.5)
+    assert (Na == Nb).all()
+    np.testing.assert_allclose(b, a, rtol=1e-12, atol=1e-14)
+
+
+def test_color_volume_constant_closed_form():
+    n = 7
+    row = np.array([0.3, 0.6, 0.1, 4.0])
+    cv = np.broadcast_to(row, (n, n, n, 4)).copy()
+    view = syn.View(5, 6)
+    img, N, _ = oracle.render(cv, None, "color", view, [0.9, 0.4, 1.8], 0.5)
+    dt = float(np.float32(np.float32(0.5) / np.float32(6)))
+    A = 1 - np.exp(-row[3] * N * dt)
+    np.testing.assert_allclose(img[:, 3], A, rtol=1e-13, atol=1e-15)
+    for ch in range(3):
+        np.testing.assert_allclose(img[:, ch], row[ch] * A, rtol=1e-13, atol=1e-15)
+
+
+def test_color_volume_fd_every_entry_and_eye():
+    """Central differences w.r.t. every channel of every vertex of a 6^3
+    colour volume and w.r.t. the eye equal the adjoint."""
+    rng = np.random.default_rng(5)
+    n = 6
+    cv = rng.uniform(0.1, 1.0, (n, n, n, 4))
+    cv[..., 3] *= 5.0
+    view = syn.View(5, 4)
+    eye = np.array([0.9, 0.6, 1.7])
+    G = rng.normal(size=(20, 4))
+    g = oracle.backward(cv, None, "color", view, eye, 0.5, G, fp32=False, want=("volume", "eye"))
+    h = 1e-6
+    fd = np.zeros_like(cv)
+    for idx in np.ndindex(cv.shape):
+        vp = cv.copy(); vp[idx] += h
+        vm = cv.copy(); vm[idx] -= h
+        fd[idx] = (_loss(oracle.render(vp, None, "color", view, eye, 0.5, fp32=False)[0], G)
+                   - _loss(oracle.render(vm, None, "color", view, eye, 0.5, fp32=False)[0], G)) / (2 * h)
+    scale = np.abs(g["volume"]).max()
+    assert np.abs(fd - g["volume"]).max() <= 1e-6 * scale
+    for k in range(3):
+        ep = eye.copy(); ep[k] += h
+        em = eye.copy(); em[k] -= h
+        fd_e = (_loss(oracle.render(cv, None, "color", view, ep, 0.5, fp32=False)[0], G)
+                - _loss(oracle.render(cv, None, "color", view, em, 0.5, fp32=False)[0], G)) / (2 * h)
+        assert abs(fd_e - g["eye"][k]) <= 1e-6 * max(1.0, np.abs(g["eye"]).max())
+    img, dimg = oracle.render_dual(cv, None, "color", view, eye, 0.5)
+    np.testing.assert_allclose(g["eye"], np.einsum("pc,pck->k", G, dimg), rtol=1e-9)

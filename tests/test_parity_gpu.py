@@ -40,7 +40,7 @@ def _oracle(w, vols, tf, G, want=("volume", "tf", "eye")):
     vols64 = [as_oracle_volume(v) for v in vols]
     tf64 = as_oracle_volume(tf) if tf is not None else None
     offs, P = pixel_offsets(w.views)
-    nc = 4 if w.model == "emission_absorption" else 1
+    nc = 1 if w.model == "absorption" else 4
     img = np.zeros((P, nc))
     Ntot = 0
     gv = [np.zeros(v.shape) for v in vols64]
@@ -281,3 +281,32 @@ def test_memory_constant_in_step_count():
         peaks.append(torch.cuda.max_memory_allocated())
         del img, aux, G
     assert peaks[0] == peaks[1] == peaks[2]
+
+
+# ------------------------------------------------------- pre-shaded colour volume
+@pytest.mark.parametrize("vdt", [torch.float32, torch.float16, torch.bfloat16])
+def test_color_volume_parity(vdt):
+    """Colour volume (Sec. 5.4; r, g, b, tau per vertex): image, 4-channel
+    volume gradient and eye gradient against the oracle."""
+    n = 24
+    cv = syn.color_volume(n, seed=31)
+    w = syn.Workload("color", "color", [cv], None, [syn.View(45, 37)],
+                     np.array([[0.9, -0.7, 1.9]], dtype=np.float32), None, 0.5, ("volume", "camera"))
+    want = ("volume", "eye")
+    gpu = _run_gpu(w, vol_dtype=vdt, want=want)
+    ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
+    _compare(w, gpu, ref, want)
+
+
+def test_color_volume_equals_ea_for_affine_tf_gpu():
+    """On the GPU too: a colour volume holding an affine TF of the densities
+    renders as the EA model with that TF, and the TF-space gradients agree."""
+    n = 20
+    v = syn.value_noise(n, seed=8)
+    tf = np.array([[0.1, 0.7, 0.3, 1.5], [0.9, 0.2, 0.6, 6.0]], dtype=np.float32)
+    cv = (tf[0][None, None, None, :] * (1 - v[..., None]) + tf[1][None, None, None, :] * v[..., None]).astype(np.float32)
+    views = [syn.View(33, 29)]
+    eye = to_dev(np.array([[0.7, 0.8, 1.6]], dtype=np.float32))
+    a, _ = dvr.forward([to_dev(v)], to_dev(tf), "emission_absorption", views, eye, 0.5)
+    b, _ = dvr.forward([to_dev(cv)], None, "color", views, eye, 0.5)
+    assert_close(b.cpu().numpy(), a.cpu().numpy(), 2e-6, "colour vs EA")
