@@ -194,6 +194,27 @@ DVR_API int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr
                  float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags, void* stream);
 
 /*
+ * Forward-mode differentiation w.r.t. the eye (Sec. 4.2; "forward-immediate"
+ * of Sec. 5.1): one pass that evaluates Alg. 1 with forward variables
+ * carrying d/d(eye_x, eye_y, eye_z), for every pixel of every view.
+ * Inputs as dvr_forward (DVR_ABSORPTION or DVR_EMISSION_ABSORPTION;
+ * DVR_ERR_UNSUPPORTED for DVR_COLOR_VOLUME).
+ * image                device float[P][C] or NULL: the same image as dvr_forward
+ * tangent              device float[P][C][3]: d(image[p][c]) / d(eye_k)
+ */
+DVR_API int dvr_forward_tangent(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
+                                int32_t model, const dvr_view* views, int32_t n_views, const float* eye,
+                                float step_voxels, float* image, float* tangent, void* stream);
+
+/*
+ * Camera gradient from forward-mode tangents: grad_eye[v][k] +=
+ * sum over the pixels p of view v and channels c of
+ * grad_image[p][c] * tangent[p][c][k]. `model` fixes C as in dvr_forward.
+ */
+DVR_API int dvr_tangent_contract(const dvr_view* views, int32_t n_views, int32_t model, const float* tangent,
+                                 const float* grad_image, float* grad_eye, void* stream);
+
+/*
  * L2 image loss and its gradient, the seed of Alg. 2 (first line):
  * loss += scale * sum_j (image_j - target_j)^2 and
  * grad_image_j = 2 * scale * (image_j - target_j), over n floats.

@@ -57,7 +57,7 @@ def _load():
         lib.ora_rays.argtypes = [I, I, I, I, I, I, D, P, D, I, P, P, P]
         lib.ora_interpolate.argtypes = [P, I, I, I, P, L, P]
         lib.ora_backward.argtypes = [P, I, I, I, I, P, I, I, I, I, I, D, P, D, I, P, L, P, I, P, P, P, P, D, P, P]
-        lib.ora_render_dual.argtypes = [P, I, I, I, I, P, I, I, I, I, I, D, P, D, P, L, P, P]
+        lib.ora_render_dual.argtypes = [P, I, I, I, I, P, I, I, I, I, I, D, P, D, I, P, L, P, P]
         lib.ora_orbit_eye.argtypes = [P, L, P]
         lib.ora_orbit_eye_backward.argtypes = [P, L, P, P]
         lib.ora_threads.restype = I
@@ -180,15 +180,20 @@ def backward(volume, tf, model, view, eye, step, grad_image, fp32=True, pix=None
     return out
 
 
-def render_dual(volume, tf, model, view, eye, step, pix=None):
+def render_dual(volume, tf, model, view, eye, step, pix=None, n_fp32=False):
     """Forward-mode (Sec. 4.2) render seeded on the eye position; binary64
-    ray setup. Returns (image [npix][C], dimage [npix][C][3])."""
+    ray setup (with n_fp32, the sample count N of each ray is the binary32
+    decision the kernels take). Returns (image [npix][C], dimage [npix][C][3])."""
     c = _Common(volume, tf, model, view, eye, step, False)
+    if n_fp32:
+        c.eye = np.array([_f32val(e) for e in c.eye])
+        c.step = _f32val(c.step)
+        c.lens = _f32val(c.lens)
     p, n = _pix(pix)
     total = n if p is not None else c.W * c.H
     img = np.zeros((total, c.nc))
     dimg = np.zeros((total, c.nc, 3))
-    _load().ora_render_dual(*c.head(), _p(p), n, _p(img), _p(dimg))
+    _load().ora_render_dual(*c.head(), int(bool(n_fp32)), _p(p), n, _p(img), _p(dimg))
     return img, dimg
 
 

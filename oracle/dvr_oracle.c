@@ -795,7 +795,7 @@ static inline dual dneg(dual a) { dual r; r.v = -a.v; for (int k = 0; k < 3; ++k
  * values). Outputs image [npix][nc] and dimage [npix][nc][3].
  */
 int ora_render_dual(const void* V, int vf32, int nx, int ny, int nz, const double* tf, int R, int model,
-                    int W, int H, int ortho, double lens, const double* eye, double step,
+                    int W, int H, int ortho, double lens, const double* eye, double step, int n_fp32,
                     const int64_t* pix, int64_t npix, double* image, double* dimage)
 {
     scene_t s;
@@ -858,6 +858,15 @@ int ora_render_dual(const void* V, int vf32, int nx, int ny, int nz, const doubl
         if (hit && tfar > tn.v) {
             double nq = ceil((tfar - tn.v) / G->dt - 0x1p-10);
             N = nq > 0.0 ? (int)nq : 0;
+        }
+        if (n_fp32) {
+            /* take the integer N from the binary32 setup of the kernel (the
+             * derivatives stay binary64) */
+            scene_t s32;
+            setup_scene(&s32, V, vf32, nx, ny, nz, tf, R, model, W, H, ortho, lens, eye, step, 1);
+            ray_t r32;
+            camera_ray(&s32.cam, &s32.G, px, py, 1, &r32);
+            N = r32.N;
         }
         dual xo[3];
         for (int a = 0; a < 3; ++a) xo[a] = dadd(o[a], dmul(tn, w[a]));

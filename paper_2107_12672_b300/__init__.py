@@ -9,15 +9,15 @@ The CUDA library is loaded on first use; nothing falls back to the CPU.
 from . import synthetic
 from .synthetic import View
 
-__all__ = ["synthetic", "View", "forward", "backward", "render", "loss_l2", "orbit_eye",
+__all__ = ["synthetic", "View", "forward", "backward", "forward_tangent", "tangent_contract", "render", "loss_l2", "orbit_eye",
            "orbit_eye_backward", "orbit_camera", "Scene", "split_views", "lib"]
 
 
 def __getattr__(name):
     # the torch binding (and with it the CUDA library) loads lazily, so that
     # the input generators can be imported without CUDA
-    if name in ("forward", "backward", "render", "loss_l2", "orbit_eye", "orbit_eye_backward",
-                "orbit_camera", "Scene", "split_views", "MODELS"):
+    if name in ("forward", "backward", "forward_tangent", "tangent_contract", "render", "loss_l2",
+                "orbit_eye", "orbit_eye_backward", "orbit_camera", "Scene", "split_views", "MODELS"):
         from . import binding as _r
         return getattr(_r, name)
     if name == "lib":

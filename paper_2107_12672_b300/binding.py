@@ -19,7 +19,7 @@ import torch
 from . import _abi
 from .synthetic import View
 
-__all__ = ["View", "Scene", "forward", "backward", "loss_l2", "orbit_eye", "orbit_eye_backward",
+__all__ = ["View", "Scene", "forward", "backward", "forward_tangent", "tangent_contract", "loss_l2", "orbit_eye", "orbit_eye_backward",
            "render", "orbit_camera", "split_views", "MODELS"]
 
 MODELS = {"absorption": _abi.DVR_ABSORPTION, "emission_absorption": _abi.DVR_EMISSION_ABSORPTION,
@@ -149,6 +149,33 @@ def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, wa
                                   _ptr(g.get("step")), flags, _stream_ptr(stream))
     _abi.check(rc, "dvr_backward")
     return g
+
+
+def forward_tangent(volumes, tf, model, views, eye, step_voxels, *, scene: Scene | None = None, image=None,
+                    tangent=None, stream=None):
+    """Forward-mode pass (Sec. 4.2): image [P][C] and d(image)/d(eye)
+    [P][C][3] in one launch."""
+    sc = scene or Scene.make(volumes, tf, model, views)
+    dev = sc.volumes[0].device
+    if image is None:
+        image = torch.empty((sc.pixels, sc.channels), device=dev, dtype=torch.float32)
+    if tangent is None:
+        tangent = torch.empty((sc.pixels, sc.channels, 3), device=dev, dtype=torch.float32)
+    rc = _abi.load().dvr_forward_tangent(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
+                                         len(sc.views), _ptr(eye), float(step_voxels), _ptr(image),
+                                         _ptr(tangent), _stream_ptr(stream))
+    _abi.check(rc, "dvr_forward_tangent")
+    return image, tangent
+
+
+def tangent_contract(scene: Scene, tangent, grad_image, *, grad_eye=None, stream=None):
+    """Camera gradient from tangents: grad_eye[v] += sum G * d(image)/d(eye)."""
+    if grad_eye is None:
+        grad_eye = torch.zeros((len(scene.views), 3), device=tangent.device, dtype=torch.float32)
+    rc = _abi.load().dvr_tangent_contract(scene.view_desc, len(scene.views), scene.model, _ptr(tangent),
+                                          _ptr(grad_image), _ptr(grad_eye), _stream_ptr(stream))
+    _abi.check(rc, "dvr_tangent_contract")
+    return grad_eye
 
 
 def loss_l2(image, target, scale=1.0, *, grad_image=None, loss=None, stream=None):

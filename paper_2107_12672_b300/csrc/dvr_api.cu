@@ -223,6 +223,60 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
     return DVR_OK;
 }
 
+int dvr_forward_tangent(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
+                        const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
+                        float* image, float* tangent, void* stream)
+{
+    g_err[0] = 0;
+    Common c;
+    int rc = check_common(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, c);
+    if (rc) return rc;
+    if (model == DVR_COLOR_VOLUME)
+        return fail(DVR_ERR_UNSUPPORTED, "forward-mode tangents are implemented for the scalar models");
+    if (!tangent) return fail(DVR_ERR_ARG, "tangent is NULL");
+    if (!aligned(tangent, 4)) return fail(DVR_ERR_ARG, "tangent is not 4-byte aligned");
+    if (image && !aligned(image, c.channels == 4 ? 16 : 4)) return fail(DVR_ERR_ARG, "image is not aligned");
+    dvr::Params p;
+    for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
+        const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
+        pack(p, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
+             step_voxels);
+        p.image = image;
+        cudaError_t e = dvr::launch_tangent(p, model, c.dtype, tangent, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dvr_forward_tangent launch");
+    }
+    return DVR_OK;
+}
+
+int dvr_tangent_contract(const dvr_view* views, int32_t n_views, int32_t model, const float* tangent,
+                         const float* grad_image, float* grad_eye, void* stream)
+{
+    g_err[0] = 0;
+    if (model != DVR_ABSORPTION && model != DVR_EMISSION_ABSORPTION && model != DVR_COLOR_VOLUME)
+        return fail(DVR_ERR_ARG, "unknown model %d", model);
+    if (!views || n_views < 1 || n_views > 4096) return fail(DVR_ERR_ARG, "n_views outside [1, 4096]");
+    if (!tangent || !grad_image || !grad_eye) return fail(DVR_ERR_ARG, "tangent, grad_image, grad_eye required");
+    for (int i = 0; i < n_views; ++i)
+        if (views[i].width < 1 || views[i].height < 1 || views[i].pixel_offset < 0)
+            return fail(DVR_ERR_ARG, "view %d: invalid size or offset", i);
+    const int channels = model == DVR_ABSORPTION ? 1 : 4;
+    dvr::Params p;
+    for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
+        const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
+        memset(&p, 0, sizeof(p));
+        for (int i = v0; i < v1; ++i) {
+            p.view[i - v0].width = views[i].width;
+            p.view[i - v0].height = views[i].height;
+            p.view[i - v0].pixel_offset = views[i].pixel_offset;
+        }
+        p.n_views = v1 - v0;
+        p.view_base = v0;
+        cudaError_t e = dvr::launch_contract(p, channels, tangent, grad_image, grad_eye, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dvr_tangent_contract launch");
+    }
+    return DVR_OK;
+}
+
 int dvr_loss_l2(const float* image, const float* target, int64_t n, float scale, float* grad_image,
                 float* loss, void* stream)
 {

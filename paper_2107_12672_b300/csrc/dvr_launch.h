@@ -20,6 +20,9 @@ cudaError_t launch_backward(const Params& p, int model, int vol_dtype, bool grad
 cudaError_t launch_forward_color(const Params& p, int vol_dtype, cudaStream_t stream);
 cudaError_t launch_backward_color(const Params& p, int vol_dtype, bool grad_volume, bool grad_position,
                                   cudaStream_t stream);
+cudaError_t launch_tangent(const Params& p, int model, int vol_dtype, float* tangent, cudaStream_t stream);
+cudaError_t launch_contract(const Params& p, int channels, const float* tangent, const float* grad_image,
+                            float* grad_eye, cudaStream_t stream);
 cudaError_t launch_loss_l2(const float* image, const float* target, long long n, float scale,
                            float* grad_image, float* loss, cudaStream_t stream);
 cudaError_t launch_orbit_eye(const float* params, int n, float* eye, cudaStream_t stream);
