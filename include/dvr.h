@@ -224,6 +224,38 @@ DVR_API int dvr_loss_l2(const float* image, const float* target, int64_t n, floa
                 float* grad_image, float* loss, void* stream);
 
 /*
+ * L1 image loss of Eq. tf-loss and its subgradient:
+ * loss += scale * sum_j |image_j - target_j|,
+ * grad_image_j = scale * sign(image_j - target_j) (0 where equal).
+ */
+DVR_API int dvr_loss_l1(const float* image, const float* target, int64_t n, float scale,
+                        float* grad_image, float* loss, void* stream);
+
+/*
+ * Smoothing priors (Eq. tf-loss; its 3D form on the densities, Sec. 5.3).
+ * dvr_tf_prior: tf device float[R][4]; loss += scale * sum_c sum_r
+ *   (tf[r+1][c] - tf[r][c])^2 (the paper's normalisation is
+ *   scale = lambda / (4 (R - 1))); grad (device float[R][4] or NULL) += the
+ *   gradient of that term.
+ * dvr_volume_prior: volume device float[nz][ny][nx]; loss += scale * the sum
+ *   of squared differences of all pairs of neighbouring vertices along x, y
+ *   and z; grad (same layout, or NULL) += its gradient. loss: device float[1]
+ *   or NULL.
+ */
+DVR_API int dvr_tf_prior(const float* tf, int32_t R, float scale, float* grad, float* loss, void* stream);
+DVR_API int dvr_volume_prior(const float* volume, int32_t nx, int32_t ny, int32_t nz, float scale,
+                             float* grad, float* loss, void* stream);
+
+/*
+ * Resample a float32 vertex grid [sz][sy][sx] to [dz][dy][dx] over the same
+ * box (trilinear), the resolution step of the multi-resolution schedule of
+ * Sec. 5.3. Both grids must span the same box:
+ * (s_a - 1) (d_max - 1) == (d_a - 1) (s_max - 1) for every axis.
+ */
+DVR_API int dvr_resample(const float* src, int32_t sx, int32_t sy, int32_t sz, float* dst, int32_t dx,
+                         int32_t dy, int32_t dz, void* stream);
+
+/*
  * Orbit camera (Sec. 5.1: camera on a sphere around the volume, given by
  * longitude and latitude): eye = dist * (cos p sin y, sin p, cos p cos y)
  * from params[v] = (yaw y, pitch p, distance dist), device float[n][3].

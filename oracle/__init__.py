@@ -265,3 +265,48 @@ def backward_views(volumes, tf, model, views, eye, step, grad_images, fp32=True,
         if "eye" in g:
             ge[v] = g["eye"]
     return {"volume": gv, "tf": gt, "eye": ge}
+
+
+# ---------------------------------------------------------------------------
+# Optimisation-side terms (Sec. 5.2, Sec. 5.3), by their definitions.
+# ---------------------------------------------------------------------------
+def volume_prior(volume):
+    """sum over all pairs of neighbouring vertices (along x, y, z) of the
+    squared difference, and its gradient (binary64)."""
+    v = _f64(volume)
+    loss = 0.0
+    grad = np.zeros_like(v)
+    for axis in range(3):
+        d = np.diff(v, axis=axis)
+        loss += float((d * d).sum())
+        pad_lo = [(0, 0)] * 3
+        pad_hi = [(0, 0)] * 3
+        pad_lo[axis] = (1, 0)
+        pad_hi[axis] = (0, 1)
+        # d/dv_i of (v_{i+1} - v_i)^2 = -2 d_i ; of (v_i - v_{i-1})^2 = +2 d_{i-1}
+        grad += 2.0 * np.pad(d, pad_lo) - 2.0 * np.pad(d, pad_hi)
+    return loss, grad
+
+
+def tf_prior(tf):
+    """Eq. tf-loss prior without its normalisation: sum_c sum_r
+    (T[r+1][c] - T[r][c])^2, and its gradient."""
+    t = _f64(tf)
+    d = np.diff(t, axis=0)
+    grad = 2.0 * np.pad(d, [(1, 0), (0, 0)]) - 2.0 * np.pad(d, [(0, 1), (0, 0)])
+    return float((d * d).sum()), grad
+
+
+def resample(volume, shape):
+    """Trilinear resampling to `shape` (nz, ny, nx) over the same box:
+    f_interpolate of the source at the world positions of the new vertices."""
+    v = _f64(volume)
+    dz, dy, dx = shape
+    dmax = max(shape)
+    coords = []
+    for n in (dx, dy, dz):
+        ext = (n - 1) / (dmax - 1)
+        coords.append(-0.5 * ext + np.arange(n) / (dmax - 1))
+    Z, Y, X = np.meshgrid(coords[2], coords[1], coords[0], indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    return interpolate(v, pts).reshape(shape)

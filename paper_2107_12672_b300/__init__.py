@@ -16,8 +16,9 @@ __all__ = ["synthetic", "View", "forward", "backward", "forward_tangent", "tange
 def __getattr__(name):
     # the torch binding (and with it the CUDA library) loads lazily, so that
     # the input generators can be imported without CUDA
-    if name in ("forward", "backward", "forward_tangent", "tangent_contract", "render", "loss_l2",
-                "orbit_eye", "orbit_eye_backward", "orbit_camera", "Scene", "split_views", "MODELS"):
+    if name in ("forward", "backward", "forward_tangent", "tangent_contract", "render", "loss_l2", "loss_l1",
+                "tf_prior", "volume_prior", "resample", "volume_smoothness", "orbit_eye",
+                "orbit_eye_backward", "orbit_camera", "Scene", "split_views", "MODELS"):
         from . import binding as _r
         return getattr(_r, name)
     if name == "lib":

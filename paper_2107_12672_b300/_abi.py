@@ -22,7 +22,8 @@ DVR_FLAG_TF_IMMEDIATE = 1
 
 # every symbol include/dvr.h declares
 SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_forward", "dvr_backward", "dvr_forward_tangent",
-           "dvr_tangent_contract", "dvr_loss_l2", "dvr_orbit_eye", "dvr_orbit_eye_backward")
+           "dvr_tangent_contract", "dvr_loss_l2", "dvr_loss_l1", "dvr_tf_prior", "dvr_volume_prior",
+           "dvr_resample", "dvr_orbit_eye", "dvr_orbit_eye_backward")
 
 
 class DvrVolume(ctypes.Structure):
@@ -65,10 +66,15 @@ def load() -> ctypes.CDLL:
         lib.dvr_forward_tangent.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P]
         lib.dvr_tangent_contract.argtypes = [P, I32, I32, P, P, P, P]
         lib.dvr_loss_l2.argtypes = [P, P, I64, F, P, P, P]
+        lib.dvr_loss_l1.argtypes = [P, P, I64, F, P, P, P]
+        lib.dvr_tf_prior.argtypes = [P, I32, F, P, P, P]
+        lib.dvr_volume_prior.argtypes = [P, I32, I32, I32, F, P, P, P]
+        lib.dvr_resample.argtypes = [P, I32, I32, I32, P, I32, I32, I32, P]
         lib.dvr_orbit_eye.argtypes = [P, I32, P, P]
         lib.dvr_orbit_eye_backward.argtypes = [P, P, I32, P, P]
         for name in ("dvr_forward", "dvr_backward", "dvr_forward_tangent", "dvr_tangent_contract",
-                     "dvr_loss_l2", "dvr_orbit_eye", "dvr_orbit_eye_backward"):
+                     "dvr_loss_l2", "dvr_loss_l1", "dvr_tf_prior", "dvr_volume_prior", "dvr_resample",
+                     "dvr_orbit_eye", "dvr_orbit_eye_backward"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib

@@ -19,7 +19,8 @@ import torch
 from . import _abi
 from .synthetic import View
 
-__all__ = ["View", "Scene", "forward", "backward", "forward_tangent", "tangent_contract", "loss_l2", "orbit_eye", "orbit_eye_backward",
+__all__ = ["View", "Scene", "forward", "backward", "forward_tangent", "tangent_contract", "loss_l2",
+           "loss_l1", "tf_prior", "volume_prior", "resample", "volume_smoothness", "orbit_eye", "orbit_eye_backward",
            "render", "orbit_camera", "split_views", "MODELS"]
 
 MODELS = {"absorption": _abi.DVR_ABSORPTION, "emission_absorption": _abi.DVR_EMISSION_ABSORPTION,
@@ -186,6 +187,71 @@ def loss_l2(image, target, scale=1.0, *, grad_image=None, loss=None, stream=None
                                  _ptr(grad_image), _ptr(loss), _stream_ptr(stream))
     _abi.check(rc, "dvr_loss_l2")
     return grad_image
+
+
+def loss_l1(image, target, scale=1.0, *, grad_image=None, loss=None, stream=None):
+    """L1 loss of Eq. tf-loss: loss += scale*sum|x-y|, grad = scale*sign(x-y)."""
+    if grad_image is None:
+        grad_image = torch.empty_like(image)
+    rc = _abi.load().dvr_loss_l1(_ptr(image), _ptr(target), image.numel(), float(scale), _ptr(grad_image),
+                                 _ptr(loss), _stream_ptr(stream))
+    _abi.check(rc, "dvr_loss_l1")
+    return grad_image
+
+
+def tf_prior(tf, weight, *, grad=None, loss=None, stream=None):
+    """Smoothing prior of Eq. tf-loss with the paper's normalisation
+    weight / (4 (R - 1)); returns (loss[1], grad) accumulated into the given
+    buffers (fresh zeros otherwise)."""
+    R = tf.shape[0]
+    loss = torch.zeros(1, device=tf.device) if loss is None else loss
+    grad = torch.zeros_like(tf) if grad is None else grad
+    rc = _abi.load().dvr_tf_prior(_ptr(tf), R, float(weight) / (4 * (R - 1)), _ptr(grad), _ptr(loss),
+                                  _stream_ptr(stream))
+    _abi.check(rc, "dvr_tf_prior")
+    return loss, grad
+
+
+def volume_prior(volume, weight, *, grad=None, loss=None, stream=None):
+    """3D smoothing prior (Sec. 5.3): weight times the mean over all pairs of
+    neighbouring vertices of their squared difference."""
+    nz, ny, nx = volume.shape
+    pairs = (nx - 1) * ny * nz + nx * (ny - 1) * nz + nx * ny * (nz - 1)
+    loss = torch.zeros(1, device=volume.device) if loss is None else loss
+    grad = torch.zeros_like(volume) if grad is None else grad
+    rc = _abi.load().dvr_volume_prior(_ptr(volume), nx, ny, nz, float(weight) / pairs, _ptr(grad), _ptr(loss),
+                                      _stream_ptr(stream))
+    _abi.check(rc, "dvr_volume_prior")
+    return loss, grad
+
+
+def resample(volume, shape, *, out=None, stream=None):
+    """Trilinear resampling of a float32 vertex grid to `shape` (nz, ny, nx)
+    over the same box (multi-resolution schedule, Sec. 5.3)."""
+    sz, sy, sx = volume.shape
+    dz, dy, dx = shape
+    out = torch.empty(shape, device=volume.device, dtype=torch.float32) if out is None else out
+    rc = _abi.load().dvr_resample(_ptr(volume), sx, sy, sz, _ptr(out), dx, dy, dz, _stream_ptr(stream))
+    _abi.check(rc, "dvr_resample")
+    return out
+
+
+class _VolumePriorFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, volume, weight):
+        loss, grad = volume_prior(volume.detach().contiguous(), weight)
+        ctx.save_for_backward(grad)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return grad * g, None
+
+
+def volume_smoothness(volume, weight):
+    """Differentiable 3D smoothing prior (autograd)."""
+    return _VolumePriorFn.apply(volume, float(weight))
 
 
 def orbit_eye(params, *, eye=None, stream=None):

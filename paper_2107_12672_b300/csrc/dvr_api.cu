@@ -288,6 +288,53 @@ int dvr_loss_l2(const float* image, const float* target, int64_t n, float scale,
     return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_loss_l2 launch");
 }
 
+int dvr_loss_l1(const float* image, const float* target, int64_t n, float scale, float* grad_image,
+                float* loss, void* stream)
+{
+    g_err[0] = 0;
+    if (n < 0) return fail(DVR_ERR_ARG, "n < 0");
+    if (n == 0) return DVR_OK;
+    if (!image || !target || !grad_image) return fail(DVR_ERR_ARG, "image, target and grad_image are required");
+    cudaError_t e = dvr::launch_loss_l1(image, target, n, scale, grad_image, loss, (cudaStream_t)stream);
+    return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_loss_l1 launch");
+}
+
+int dvr_tf_prior(const float* tf, int32_t R, float scale, float* grad, float* loss, void* stream)
+{
+    g_err[0] = 0;
+    if (!tf || R < 2 || R > dvr::kMaxTF) return fail(DVR_ERR_ARG, "need a TF with 2..%d rows", dvr::kMaxTF);
+    if (!grad && !loss) return DVR_OK;
+    cudaError_t e = dvr::launch_tf_prior(tf, R, scale, grad, loss, (cudaStream_t)stream);
+    return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_tf_prior launch");
+}
+
+int dvr_volume_prior(const float* volume, int32_t nx, int32_t ny, int32_t nz, float scale, float* grad,
+                     float* loss, void* stream)
+{
+    g_err[0] = 0;
+    if (!volume || nx < 1 || ny < 1 || nz < 1) return fail(DVR_ERR_ARG, "need a non-empty volume");
+    if (!grad && !loss) return DVR_OK;
+    cudaError_t e = dvr::launch_volume_prior(volume, nx, ny, nz, scale, grad, loss, (cudaStream_t)stream);
+    return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_volume_prior launch");
+}
+
+int dvr_resample(const float* src, int32_t sx, int32_t sy, int32_t sz, float* dst, int32_t dx, int32_t dy,
+                 int32_t dz, void* stream)
+{
+    g_err[0] = 0;
+    if (!src || !dst) return fail(DVR_ERR_ARG, "src and dst are required");
+    if (sx < 2 || sy < 2 || sz < 2 || dx < 2 || dy < 2 || dz < 2)
+        return fail(DVR_ERR_ARG, "every dimension must be >= 2");
+    const long long smax = sx > sy ? (sx > sz ? sx : sz) : (sy > sz ? sy : sz);
+    const long long dmax = dx > dy ? (dx > dz ? dx : dz) : (dy > dz ? dy : dz);
+    const int s3[3] = {sx, sy, sz}, d3[3] = {dx, dy, dz};
+    for (int a = 0; a < 3; ++a)
+        if ((long long)(s3[a] - 1) * (dmax - 1) != (long long)(d3[a] - 1) * (smax - 1))
+            return fail(DVR_ERR_ARG, "source and destination grids do not span the same box (axis %d)", a);
+    cudaError_t e = dvr::launch_resample(src, sx, sy, sz, dst, dx, dy, dz, (cudaStream_t)stream);
+    return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_resample launch");
+}
+
 int dvr_orbit_eye(const float* params, int32_t n, float* eye, void* stream)
 {
     g_err[0] = 0;

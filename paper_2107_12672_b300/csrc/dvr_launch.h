@@ -23,6 +23,13 @@ cudaError_t launch_backward_color(const Params& p, int vol_dtype, bool grad_volu
 cudaError_t launch_tangent(const Params& p, int model, int vol_dtype, float* tangent, cudaStream_t stream);
 cudaError_t launch_contract(const Params& p, int channels, const float* tangent, const float* grad_image,
                             float* grad_eye, cudaStream_t stream);
+cudaError_t launch_volume_prior(const float* v, int nx, int ny, int nz, float scale, float* grad, float* loss,
+                                cudaStream_t s);
+cudaError_t launch_tf_prior(const float* tf, int R, float scale, float* grad, float* loss, cudaStream_t s);
+cudaError_t launch_loss_l1(const float* x, const float* y, long long n, float scale, float* g, float* loss,
+                           cudaStream_t s);
+cudaError_t launch_resample(const float* src, int sx, int sy, int sz, float* dst, int dx, int dy, int dz,
+                            cudaStream_t s);
 cudaError_t launch_loss_l2(const float* image, const float* target, long long n, float scale,
                            float* grad_image, float* loss, cudaStream_t stream);
 cudaError_t launch_orbit_eye(const float* params, int n, float* eye, cudaStream_t stream);

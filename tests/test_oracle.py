@@ -436,3 +436,47 @@ def test_color_volume_fd_every_entry_and_eye():
         assert abs(fd_e - g["eye"][k]) <= 1e-6 * max(1.0, np.abs(g["eye"]).max())
     img, dimg = oracle.render_dual(cv, None, "color", view, eye, 0.5)
     np.testing.assert_allclose(g["eye"], np.einsum("pc,pck->k", G, dimg), rtol=1e-9)
+
+
+# ------------------------------------------------------ optimisation-side terms
+def test_volume_prior_closed_form_and_fd():
+    """3D smoothing prior (Sec. 5.3): a ramp a*z has every z-difference a and
+    no x/y differences, so the sum is a^2 nx ny (nz - 1); the gradient of the
+    quadratic matches central differences exactly."""
+    nz, ny, nx = 5, 4, 6
+    a = 0.7
+    ramp = np.broadcast_to((a * np.arange(nz))[:, None, None], (nz, ny, nx))
+    loss, grad = oracle.volume_prior(ramp)
+    assert abs(loss - a * a * nx * ny * (nz - 1)) < 1e-12
+    rng = np.random.default_rng(0)
+    v = rng.normal(size=(3, 4, 5))
+    loss, grad = oracle.volume_prior(v)
+    for idx in [(0, 0, 0), (1, 2, 3), (2, 3, 4), (1, 0, 2)]:
+        vp = v.copy(); vp[idx] += 1e-4
+        vm = v.copy(); vm[idx] -= 1e-4
+        fd = (oracle.volume_prior(vp)[0] - oracle.volume_prior(vm)[0]) / 2e-4
+        assert abs(fd - grad[idx]) < 1e-8
+
+
+def test_tf_prior_closed_form():
+    """Eq. tf-loss prior: rows differing by a constant c in every channel sum
+    to 4 (R - 1) c^2."""
+    R, c = 9, 0.3
+    tf = np.arange(R)[:, None] * c + np.zeros((1, 4))
+    loss, grad = oracle.tf_prior(tf)
+    assert abs(loss - 4 * (R - 1) * c * c) < 1e-12
+    assert np.abs(grad[1:-1]).max() < 1e-12          # interior rows: equal differences cancel
+
+
+def test_resample_reproduces_linear_fields():
+    """Resampling onto a finer grid over the same box keeps a linear field
+    exactly (trilinear reproduction), and the identity shape is the identity."""
+    n = 5
+    xs = np.linspace(-0.5, 0.5, n)
+    Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
+    v = 0.3 + 1.1 * X - 0.7 * Y + 0.4 * Z
+    up = oracle.resample(v, (9, 9, 9))
+    xs9 = np.linspace(-0.5, 0.5, 9)
+    Z9, Y9, X9 = np.meshgrid(xs9, xs9, xs9, indexing="ij")
+    np.testing.assert_allclose(up, 0.3 + 1.1 * X9 - 0.7 * Y9 + 0.4 * Z9, atol=1e-13)
+    np.testing.assert_allclose(oracle.resample(v, v.shape), v, atol=1e-14)

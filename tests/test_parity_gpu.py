@@ -352,3 +352,64 @@ def test_forward_tangent(model, ortho):
     # other one-sided derivative in binary32: most pixels agree tightly
     assert np.quantile(err, 0.99) < 1e-4, np.quantile(err, 0.99)
     assert err.max() < 5e-2, err.max()
+
+
+# ------------------------------------------------------ optimisation-side kernels
+def test_priors_losses_and_resampling():
+    """Smoothing priors (Eq. tf-loss, 3D form of Sec. 5.3), L1 loss and
+    resampling kernels against their oracle definitions."""
+    rng = np.random.default_rng(3)
+    v = rng.normal(size=(37, 29, 41)).astype(np.float32)
+    loss = torch.zeros(1, device="cuda")
+    g = torch.zeros(v.shape, device="cuda")
+    from paper_2107_12672_b300 import binding as b
+    lib = b._abi.load()
+    b._abi.check(lib.dvr_volume_prior(to_dev(v).data_ptr(), 41, 29, 37, 0.5, g.data_ptr(), loss.data_ptr(), None),
+                 "prior")
+    torch.cuda.synchronize()
+    rl, rg = oracle.volume_prior(v)
+    assert abs(loss.item() - 0.5 * rl) <= 1e-5 * abs(0.5 * rl)
+    assert_close(g.cpu().numpy(), 0.5 * rg, 1e-5, "volume prior gradient")
+    tf = rng.uniform(0, 1, (16, 4)).astype(np.float32)
+    l2, g2 = dvr.tf_prior(to_dev(tf), 0.4)
+    rl, rg = oracle.tf_prior(tf)
+    assert abs(l2.item() - 0.4 / 60 * rl) <= 1e-5 * abs(0.4 / 60 * rl)
+    assert_close(g2.cpu().numpy(), 0.4 / 60 * rg, 1e-5, "tf prior gradient")
+    x = rng.normal(size=10001).astype(np.float32)
+    y = rng.normal(size=10001).astype(np.float32)
+    l1 = torch.zeros(1, device="cuda")
+    g1 = dvr.loss_l1(to_dev(x), to_dev(y), 0.25, loss=l1).cpu().numpy()
+    np.testing.assert_array_equal(g1, 0.25 * np.sign(x - y))
+    assert abs(l1.item() - 0.25 * np.abs(x.astype(np.float64) - y).sum()) <= 1e-5 * l1.item()
+    src = rng.uniform(0, 1, (17, 17, 17)).astype(np.float32)
+    up = dvr.resample(to_dev(src), (33, 33, 33)).cpu().numpy()
+    assert_close(up, oracle.resample(src, (33, 33, 33)), 1e-6, "resample")
+
+
+def test_multiresolution_reconstruction():
+    """The schedule of Sec. 5.3 on the synthetic tomography workload: start at
+    17^3, refine by resampling to 33^3 and 65^3, Adam on the densities with
+    the L2 image loss plus the 3D smoothing prior; the loss at the finest
+    level ends well below its start."""
+    w = syn.workload("tomo_256x64", scale=0.25)       # 64^3 target, 64 views
+    eye = to_dev(w.eye)
+    target_vol = to_dev(syn.gaussian_blobs(65, 32, seed=4))
+    with torch.no_grad():
+        target = dvr.render(target_vol, None, eye, w.views, w.step_voxels, "absorption")
+    x = torch.zeros((17, 17, 17), device="cuda")
+    first = last = None
+    for level, n in enumerate((17, 33, 65)):
+        if n != x.shape[0]:
+            x = dvr.resample(x.contiguous(), (n, n, n))
+        x = x.detach().requires_grad_(True)
+        opt = torch.optim.Adam([x], lr=0.05)
+        for it in range(30):
+            opt.zero_grad()
+            img = dvr.render(x, None, eye, w.views, w.step_voxels * (n - 1) / 64, "absorption")
+            loss = ((img - target) ** 2).mean() + dvr.volume_smoothness(x, 0.01)
+            loss.backward()
+            opt.step()
+            if first is None:
+                first = float(loss.detach())
+        last = float(loss.detach())
+    assert last < first / 5, (first, last)
