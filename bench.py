@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default 8x4 ray tiles")
+    ap.add_argument("--tile-width", type=int, default=0, help="fix the warp tile width (1..32)")
     ap.add_argument("--no-variants", action="store_true", help="skip the BF16/FP16 storage comparison")
     return ap.parse_args()
 
@@ -459,6 +461,14 @@ def run_ours(args):
     wl = Workload(args.workload, dev, args.tf_immediate)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     K = args.steps
+    tuning = None
+    if args.tile_width:
+        from paper_2107_12672_b300 import autotune
+        autotune.set_tile_width(args.tile_width)
+        tuning = {"width": args.tile_width, "fixed": True}
+    elif not args.no_autotune:
+        from paper_2107_12672_b300 import autotune
+        tuning = autotune.autotune(wl.scene, wl.eye, wl.w.step_voxels, want=wl.want)
     step_ms, fwd_ms, bwd_ms, wall, clk = time_steps(wl, K, args.warmup, flush, Clocks(local), world)
     if world > 1:
         t = torch.tensor([step_ms], device=dev)
@@ -498,6 +508,7 @@ def run_ours(args):
         achieved = algorithmic_bytes(wl, dom) / (dur * 1e-3) / 1e9
         cfg = wl.describe()
         cfg.update({"l2": "flushed between timed steps (512 MiB write)",
+                    "tile": tuning,
                     "tf_accumulation": "immediate" if args.tf_immediate else "delayed (shared memory)",
                     "parallelism": f"replicas x{world}"})
         line = {

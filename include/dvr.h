@@ -142,6 +142,15 @@ typedef struct {
 /* ABI version (DVR_ABI_VERSION). */
 DVR_API int dvr_abi_version(void);
 
+/*
+ * Ray tiling: each warp marches a tile of width x (32 / width) pixels,
+ * width in {1, 2, 4, 8, 16, 32} (default 8). The shape changes only which
+ * rays share a warp (and so the memory access pattern), never the result.
+ * The setting is process-wide and read when a launch is issued.
+ */
+DVR_API int dvr_set_tile_width(int32_t width);
+DVR_API int dvr_get_tile_width(void);
+
 /* Message for the last failing call on this host thread ("" if none). */
 DVR_API const char* dvr_last_error(void);
 

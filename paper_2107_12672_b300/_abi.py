@@ -21,7 +21,7 @@ DVR_ABSORPTION, DVR_EMISSION_ABSORPTION, DVR_COLOR_VOLUME = 0, 1, 2
 DVR_FLAG_TF_IMMEDIATE = 1
 
 # every symbol include/dvr.h declares
-SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_forward", "dvr_backward", "dvr_forward_tangent",
+SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_set_tile_width", "dvr_get_tile_width", "dvr_forward", "dvr_backward", "dvr_forward_tangent",
            "dvr_tangent_contract", "dvr_loss_l2", "dvr_loss_l1", "dvr_tf_prior", "dvr_volume_prior",
            "dvr_resample", "dvr_orbit_eye", "dvr_orbit_eye_backward")
 
@@ -60,6 +60,9 @@ def load() -> ctypes.CDLL:
         P, I32, I64, F, U32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
                                ctypes.c_uint32)
         lib.dvr_abi_version.restype = ctypes.c_int
+        lib.dvr_set_tile_width.argtypes = [I32]
+        lib.dvr_set_tile_width.restype = ctypes.c_int
+        lib.dvr_get_tile_width.restype = ctypes.c_int
         lib.dvr_last_error.restype = ctypes.c_char_p
         lib.dvr_forward.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P]
         lib.dvr_backward.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, P, P, U32, P]

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <cmath>
 
 #include "dvr.h"
@@ -13,6 +14,9 @@
 namespace {
 
 thread_local char g_err[512] = "";
+
+// warp tile width in pixels (height 32 / width) used by every launch
+std::atomic<int> g_tile_w{dvr::kTileW};
 
 int fail(int code, const char* fmt, ...)
 {
@@ -108,6 +112,9 @@ void pack(dvr::Params& p, const dvr_volume* vols, int nvol, const dvr_tf* tf, co
         int m = vols[i].nx > vols[i].ny ? vols[i].nx : vols[i].ny;
         p.vol[i].nmax = vols[i].nz > m ? vols[i].nz : m;
     }
+    const int tw = g_tile_w.load(std::memory_order_relaxed), th = 32 / tw;
+    p.tile_w = tw;
+    p.tile_h = th;
     int tiles = 0;
     for (int i = v0; i < v1; ++i) {
         const dvr_view& w = views[i];
@@ -117,10 +124,10 @@ void pack(dvr::Params& p, const dvr_volume* vols, int nvol, const dvr_tf* tf, co
         d.ortho = w.ortho;
         d.volume = w.volume;
         d.lens = w.lens;
-        d.tiles_x = (w.width + dvr::kTileW - 1) / dvr::kTileW;
+        d.tiles_x = (w.width + tw - 1) / tw;
         d.pixel_offset = w.pixel_offset;
         p.tile_start[i - v0] = tiles;
-        tiles += d.tiles_x * ((w.height + dvr::kTileH - 1) / dvr::kTileH);
+        tiles += d.tiles_x * ((w.height + th - 1) / th);
     }
     p.tile_start[v1 - v0] = tiles;
     p.total_tiles = tiles;
@@ -140,6 +147,17 @@ void pack(dvr::Params& p, const dvr_volume* vols, int nvol, const dvr_tf* tf, co
 extern "C" {
 
 int dvr_abi_version(void) { return DVR_ABI_VERSION; }
+
+int dvr_set_tile_width(int32_t width)
+{
+    g_err[0] = 0;
+    if (width != 1 && width != 2 && width != 4 && width != 8 && width != 16 && width != 32)
+        return fail(DVR_ERR_ARG, "tile width %d is not one of 1, 2, 4, 8, 16, 32", width);
+    g_tile_w.store(width, std::memory_order_relaxed);
+    return DVR_OK;
+}
+
+int dvr_get_tile_width(void) { return g_tile_w.load(std::memory_order_relaxed); }
 
 const char* dvr_last_error(void) { return g_err; }
 

@@ -17,8 +17,8 @@ namespace dvr {
 constexpr int kMaxVolumes = 16;
 constexpr int kMaxViewsPerLaunch = 512;
 constexpr int kWarps = 4;            // warps per block
-constexpr int kTileW = 8;            // a warp renders an 8 x 4 pixel tile
-constexpr int kTileH = 4;
+constexpr int kTileW = 8;            // default warp tile: 8 x 4 pixels (tile_w x tile_h = 32,
+constexpr int kTileH = 4;            // set per launch)
 constexpr int kMaxTF = 1024;         // transfer-function rows staged in shared memory
 
 // Minimum resident blocks per SM the compiler must allow (register budget
@@ -50,6 +50,7 @@ struct Params {
     int tile_start[kMaxViewsPerLaunch + 1];  // prefix sum of warp tiles per view
     int n_views;
     int total_tiles;
+    int tile_w, tile_h;              // warp tile in pixels, tile_w * tile_h = 32
     int view_base;                   // index of view[0] in the caller's arrays
     int R;
     int tf_dtype;
@@ -408,14 +409,17 @@ __device__ __forceinline__ int center_out(int r, int n)
     return (r & 1) ? c + k : c - k;
 }
 
-// Pixel of this lane in warp tile `local` of a view.
-__device__ __forceinline__ void tile_pixel(const ViewDesc& vw, int local, int lane, int& px, int& py)
+// Pixel of this lane in warp tile `local` of a view (tiles of
+// p.tile_w x p.tile_h pixels).
+__device__ __forceinline__ void tile_pixel(const Params& p, const ViewDesc& vw, int local, int lane, int& px,
+                                           int& py)
 {
-    const int tiles_y = (vw.height + kTileH - 1) / kTileH;
+    const int tw = p.tile_w, th = p.tile_h;
+    const int tiles_y = (vw.height + th - 1) / th;
     const int tx = center_out(local % vw.tiles_x, vw.tiles_x);
     const int ty = center_out(local / vw.tiles_x, tiles_y);
-    px = tx * kTileW + (lane & (kTileW - 1));
-    py = ty * kTileH + (lane / kTileW);
+    px = tx * tw + (lane & (tw - 1));
+    py = ty * th + (lane / tw);
 }
 
 // Warp tile -> (view, pixel) mapping.

@@ -27,7 +27,7 @@ forward_kernel(const __grid_constant__ Params p)
         const int v = find_view(p, tile);
         const ViewDesc& vw = p.view[v];
         int px, py;
-        tile_pixel(vw, tile - p.tile_start[v], lane, px, py);
+        tile_pixel(p, vw, tile - p.tile_start[v], lane, px, py);
         const bool valid = px < vw.width && py < vw.height;
         const VolumeDesc& vd = p.vol[vw.volume];
         const VT* __restrict__ vol = reinterpret_cast<const VT*>(vd.data);

@@ -120,7 +120,7 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
     const int v = find_view(p, tile);
     const ViewDesc& vw = p.view[v];
     int px, py;
-    tile_pixel(vw, tile - p.tile_start[v], lane, px, py);
+    tile_pixel(p, vw, tile - p.tile_start[v], lane, px, py);
     const bool valid = px < vw.width && py < vw.height;
     if (!valid) return;                          // no warp-wide operations follow
     const VolumeDesc& vd = p.vol[vw.volume];

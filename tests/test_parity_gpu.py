@@ -413,3 +413,38 @@ def test_multiresolution_reconstruction():
                 first = float(loss.detach())
         last = float(loss.detach())
     assert last < first / 5, (first, last)
+
+
+# ------------------------------------------------------------ ray tiling
+def test_tile_width_changes_nothing_and_autotuner_picks_one():
+    """Every warp tile shape gives bit-identical images (each ray is computed
+    the same way) and gradients equal up to the order of atomic additions;
+    the autotuner selects one of the candidates and leaves it set."""
+    from paper_2107_12672_b300 import autotune
+    w = syn.workload("ea_256", scale=0.25)
+    w.views = [syn.View(100, 77)]
+    vols = [to_dev(w.volumes[0])]
+    tf = to_dev(w.tf)
+    eye = to_dev(w.eye)
+    sc = dvr.Scene.make(vols, tf, w.model, w.views)
+    G = to_dev(seeded_grad_image(100 * 77, 4, 4))
+    ref = None
+    old = autotune.get_tile_width()
+    try:
+        for width in (1, 2, 4, 8, 16, 32):
+            autotune.set_tile_width(width)
+            img, aux = dvr.forward(None, None, None, None, eye, w.step_voxels, scene=sc)
+            g = dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=sc,
+                             want=("volume", "tf", "eye"))
+            torch.cuda.synchronize()
+            cur = (img.cpu(), g["volume"][0].cpu().numpy(), g["tf"].cpu().numpy(), g["eye"].cpu().numpy())
+            if ref is None:
+                ref = cur
+                continue
+            assert torch.equal(cur[0], ref[0]), width
+            for a, b in zip(cur[1:], ref[1:]):
+                assert_close(a, b, 1e-5, f"width {width}")
+        res = autotune.autotune(sc, eye, w.step_voxels, want=("tf", "eye"), reps=2)
+        assert res["width"] in autotune.CANDIDATES and autotune.get_tile_width() == res["width"]
+    finally:
+        autotune.set_tile_width(old)
