@@ -89,8 +89,10 @@ backward_kernel(const __grid_constant__ Params p)
         }
         __syncthreads();
     }
-    // kTFPrivate: this lane's copy, element (row, ch) at [(row*4 + ch)*32]
-    float* my_tfp = tfg + warp * p.R * 128 + lane;
+    // kTFPrivate: this lane's copy, row r at float4 [r*32 + lane] (a warp's
+    // 128-bit accesses are served per quarter-warp, whose 8 lanes cover all
+    // 32 banks: conflict-free for any rows)
+    float4* my_tfp = reinterpret_cast<float4*>(tfg) + warp * p.R * 32 + lane;
     // kTFWarp: this warp's copy, [row][ch]
     float* my_tfg = tfg + warp * p.R * 4;
     const float Rm1 = (float)(p.R - 1);
@@ -186,15 +188,14 @@ backward_kernel(const __grid_constant__ Params p)
                     // the lane's own copy: plain adds, no two lanes share a
                     // bank (measured faster than shared-memory reductions)
                     const float w0 = 1.f - s.fr, w1 = s.fr;
-                    float* q = my_tfp + s.k * 128;
-                    q[0] += w0 * h0;
-                    q[32] += w0 * h1;
-                    q[64] += w0 * h2;
-                    q[96] += w0 * tau_hat;
-                    q[128] += w1 * h0;
-                    q[160] += w1 * h1;
-                    q[192] += w1 * h2;
-                    q[224] += w1 * tau_hat;
+                    float4* q = my_tfp + s.k * 32;
+                    float4 a = q[0], b = q[32];
+                    a.x = fmaf(w0, h0, a.x); a.y = fmaf(w0, h1, a.y);
+                    a.z = fmaf(w0, h2, a.z); a.w = fmaf(w0, tau_hat, a.w);
+                    b.x = fmaf(w1, h0, b.x); b.y = fmaf(w1, h1, b.y);
+                    b.z = fmaf(w1, h2, b.z); b.w = fmaf(w1, tau_hat, b.w);
+                    q[0] = a;
+                    q[32] = b;
                 } else if (TFM == kTFWarp) {
                     if (s.k != tr.k) {
                         tf_run_flush(my_tfg, tr);
@@ -284,14 +285,23 @@ backward_kernel(const __grid_constant__ Params p)
 
     if (EA && TFM == kTFPrivate) {
         __syncthreads();
-        // warp w sums entries j = w, w + kWarps, ...: each lane reads its own
-        // column (conflict-free), then a warp reduction
-        for (int j = warp; j < p.R * 4; j += kWarps) {
-            float s = 0.f;
+        // warp w sums rows r = w, w + kWarps, ...: each lane reads its own
+        // float4 of every warp's copy, then warp reductions
+        const float4* tfp = reinterpret_cast<const float4*>(tfg);
+        for (int r = warp; r < p.R; r += kWarps) {
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) s += tfg[w * p.R * 128 + j * 32 + lane];
-            s = warp_sum(s);
-            if (lane == 0 && s != 0.f) atomicAdd(p.grad_tf + j, s);
+            for (int w = 0; w < kWarps; ++w) {
+                const float4 t = tfp[(w * p.R + r) * 32 + lane];
+                s.x += t.x; s.y += t.y; s.z += t.z; s.w += t.w;
+            }
+            s.x = warp_sum(s.x); s.y = warp_sum(s.y); s.z = warp_sum(s.z); s.w = warp_sum(s.w);
+            if (lane == 0) {
+                if (s.x != 0.f) atomicAdd(p.grad_tf + 4 * r + 0, s.x);
+                if (s.y != 0.f) atomicAdd(p.grad_tf + 4 * r + 1, s.y);
+                if (s.z != 0.f) atomicAdd(p.grad_tf + 4 * r + 2, s.z);
+                if (s.w != 0.f) atomicAdd(p.grad_tf + 4 * r + 3, s.w);
+            }
         }
     } else if (EA && TFM == kTFWarp) {
         __syncthreads();
