@@ -358,6 +358,15 @@ def accuracy(wl):
     if len(w.views) <= 4:
         if ref_tf is not None:
             out["grad_tf"] = rel(g["tf"].cpu().numpy(), ref_tf)
+            if wl.vol[0].dtype == torch.float32 and len(w.views) == 1:
+                # how the opacity before each sample is recovered (Sec. 4.4)
+                inv = {"optical_depth (default)": out["grad_tf"]}
+                for mode in ("alpha64", "alpha32"):
+                    gm = dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=wl.scene,
+                                      want=("tf",), inversion=mode)
+                    inv[{"alpha64": "alpha_form_fp64_above_0.99", "alpha32": "alpha_form_fp32"}[mode]] = \
+                        rel(gm["tf"].cpu().numpy(), ref_tf)
+                out["grad_tf_by_inversion"] = inv
     if ref_eye:
         out["grad_eye"] = max(rel(g["eye"].cpu().numpy()[k], r) for k, r in ref_eye)
     out["views_checked"] = min(4, len(w.views))

@@ -108,6 +108,15 @@ extern "C" {
  * channel ("adjoint-immediate", Sec. 5.2) instead of the default per-block
  * shared-memory accumulation ("adjoint-delayed") */
 #define DVR_FLAG_TF_IMMEDIATE 1u
+/* ablations of the opacity recovery (emission-absorption, FP32 volume, TF
+ * gradient delayed); by default the adjoint recovers 1 - A_i = exp(-S_i)
+ * from the exactly carried optical depth S. INVERT_ALPHA32 applies
+ * Eq. inv-blend-forward as printed, A_i = (alpha - A_{i+1}) / (alpha - 1),
+ * in binary32 starting from the binary32 image opacity; INVERT_ALPHA64
+ * starts from the optical depth and does that division in binary64 once
+ * A > 0.99. Other configurations return DVR_ERR_UNSUPPORTED. */
+#define DVR_FLAG_INVERT_ALPHA32 2u
+#define DVR_FLAG_INVERT_ALPHA64 4u
 
 /* One volume. `data` is a device pointer to nx*ny*nz samples of `dtype`,
  * layout [nz][ny][nx] (4 per vertex, [nz][ny][nx][4], for

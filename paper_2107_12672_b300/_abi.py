@@ -19,6 +19,8 @@ DVR_OK = 0
 DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
 DVR_ABSORPTION, DVR_EMISSION_ABSORPTION, DVR_COLOR_VOLUME = 0, 1, 2
 DVR_FLAG_TF_IMMEDIATE = 1
+DVR_FLAG_INVERT_ALPHA32 = 2
+DVR_FLAG_INVERT_ALPHA64 = 4
 
 # every symbol include/dvr.h declares
 SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_set_tile_width", "dvr_get_tile_width", "dvr_forward", "dvr_backward", "dvr_forward_tangent",

@@ -125,10 +125,13 @@ def forward(volumes, tf, model, views, eye, step_voxels, *, scene: Scene | None 
 
 
 def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, want=("volume", "tf", "eye"),
-             scene: Scene | None = None, grads: dict | None = None, tf_immediate=False, stream=None):
+             scene: Scene | None = None, grads: dict | None = None, tf_immediate=False, inversion="depth",
+             stream=None):
     """Alg. 2 for all views in one launch. Returns a dict with float32
     gradients for the requested parameters ("volume" -> list, "tf", "eye",
-    "step"); buffers passed in `grads` are accumulated into."""
+    "step"); buffers passed in `grads` are accumulated into. `inversion`
+    selects how the opacity before each sample is recovered: "depth"
+    (default), or the ablations "alpha32" / "alpha64" (the paper's form)."""
     sc = scene or Scene.make(volumes, tf, model, views)
     dev = sc.volumes[0].device
     g = dict(grads or {})
@@ -144,6 +147,7 @@ def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, wa
     if "volume" in g:
         gv = (ctypes.c_void_p * len(sc.volumes))(*[_ptr(t) for t in g["volume"]])
     flags = _abi.DVR_FLAG_TF_IMMEDIATE if tf_immediate else 0
+    flags |= {"depth": 0, "alpha32": _abi.DVR_FLAG_INVERT_ALPHA32, "alpha64": _abi.DVR_FLAG_INVERT_ALPHA64}[inversion]
     rc = _abi.load().dvr_backward(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
                                   len(sc.views), _ptr(eye), float(step_voxels), _ptr(aux),
                                   _ptr(grad_image), gv, _ptr(g.get("tf")), _ptr(g.get("eye")),

@@ -193,10 +193,19 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
                  float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags, void* stream)
 {
     g_err[0] = 0;
-    if (flags & ~DVR_FLAG_TF_IMMEDIATE) return fail(DVR_ERR_ARG, "unknown flag bits 0x%x", flags);
+    if (flags & ~(DVR_FLAG_TF_IMMEDIATE | DVR_FLAG_INVERT_ALPHA32 | DVR_FLAG_INVERT_ALPHA64))
+        return fail(DVR_ERR_ARG, "unknown flag bits 0x%x", flags);
+    if ((flags & DVR_FLAG_INVERT_ALPHA32) && (flags & DVR_FLAG_INVERT_ALPHA64))
+        return fail(DVR_ERR_ARG, "choose one inversion ablation");
+    const int inv = (flags & DVR_FLAG_INVERT_ALPHA32) ? dvr::kInvAlpha32
+                  : (flags & DVR_FLAG_INVERT_ALPHA64) ? dvr::kInvAlpha64 : dvr::kInvDepth;
     Common c;
     int rc = check_common(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, c);
     if (rc) return rc;
+    if (inv != dvr::kInvDepth && (model != DVR_EMISSION_ABSORPTION || c.dtype != DVR_F32 || !grad_tf ||
+                                  (flags & DVR_FLAG_TF_IMMEDIATE)))
+        return fail(DVR_ERR_UNSUPPORTED, "inversion ablations: emission-absorption, FP32 volume, delayed TF "
+                    "gradient only");
     if (!aux || !grad_image) return fail(DVR_ERR_ARG, "aux and grad_image are required");
     if (!aligned(aux, 8)) return fail(DVR_ERR_ARG, "aux is not 8-byte aligned");
     if (!aligned(grad_image, c.channels == 4 ? 16 : 4))
@@ -235,7 +244,7 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
         p.grad_step = grad_step;
         cudaError_t e = model == DVR_COLOR_VOLUME
             ? dvr::launch_backward_color(p, c.dtype, gvol, pos, (cudaStream_t)stream)
-            : dvr::launch_backward(p, model, c.dtype, gvol, tfm, pos, (cudaStream_t)stream);
+            : dvr::launch_backward(p, model, c.dtype, gvol, tfm, pos, inv, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "dvr_backward launch");
     }
     return DVR_OK;

@@ -25,6 +25,8 @@
 //  - eye / step: x^_o, w^ summed in registers along the ray (Alg. 2 last
 //    loop line), chained through f_camera per ray, warp-reduced, one atomic
 //    per warp.
+#include <type_traits>
+
 #include "dvr_device.cuh"
 #include "dvr_launch.h"
 
@@ -71,7 +73,7 @@ __device__ __forceinline__ void cell_run_flush(float* g, uint32_t sy, uint32_t s
     for (int j = 0; j < 8; ++j) r.a[j] = 0.f;
 }
 
-template <int MODEL, typename VT, bool GVOL, int TFM, bool POS>
+template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV = kInvDepth>
 __global__ void __launch_bounds__(kWarps * 32, DVR_BWD_MIN_BLOCKS)
 backward_kernel(const __grid_constant__ Params p)
 {
@@ -132,6 +134,11 @@ backward_kernel(const __grid_constant__ Params p)
             sh = s2.x; sl = s2.y;
         }
         float Th = -Ah;                         // adjoint of the transmittance 1 - A
+        // ablations: accumulated opacity A_{i+1} carried as in the paper,
+        // starting from the binary32 image opacity (the value dvr_forward
+        // wrote) or, with the binary64 guard, from the optical depth
+        float Af = INV == kInvAlpha32 ? -expm1f(-(sh + sl)) : 0.f;
+        double Ad = INV == kInvAlpha64 ? -expm1(-((double)sh + (double)sl)) : 0.0;
         const float dconst = EA ? 0.f : Ah * expf(-(sh + sl)) * G.dt;   // absorption: d^_i
         float gs[3] = {0.f, 0.f, 0.f}, gi[3] = {0.f, 0.f, 0.f};
         float dt_hat = 0.f;
@@ -172,11 +179,24 @@ backward_kernel(const __grid_constant__ Params p)
                 const float em = expm1f(-x);
                 const float alpha = -em;
                 const float ea = 1.f + em;            // 1 - alpha
-                float s2, err;
-                two_sum(sh, -x, s2, err);             // S_i = S_{i+1} - dt tau_i
-                sh = s2;
-                sl += err;
-                const float T = expf(-(sh + sl));     // 1 - A_i
+                float T;                              // 1 - A_i
+                if (INV == kInvDepth) {
+                    float s2, err;
+                    two_sum(sh, -x, s2, err);         // S_i = S_{i+1} - dt tau_i
+                    sh = s2;
+                    sl += err;
+                    T = expf(-(sh + sl));
+                } else if (INV == kInvAlpha32) {
+                    Af = (alpha - Af) / (alpha - 1.f);  // Eq. inv-blend-forward, binary32
+                    T = 1.f - Af;
+                } else {
+                    if (Ad > 0.99) {
+                        Ad = ((double)alpha - Ad) / ((double)alpha - 1.0);
+                    } else {
+                        Ad = (double)((alpha - (float)Ad) / (alpha - 1.f));
+                    }
+                    T = (float)(1.0 - Ad);
+                }
                 const float cC = fmaf(s.c.z, Ch2, fmaf(s.c.y, Ch1, s.c.x * Ch0));
                 const float Ta = T * alpha;
                 const float a_hat = T * (cC - Th);     // adjoint of alpha_i
@@ -314,10 +334,10 @@ backward_kernel(const __grid_constant__ Params p)
     }
 }
 
-template <int MODEL, typename VT, bool GVOL, int TFM, bool POS>
+template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV = kInvDepth>
 static cudaError_t launch_one(const Params& p, cudaStream_t stream)
 {
-    auto k = backward_kernel<MODEL, VT, GVOL, TFM, POS>;
+    auto k = backward_kernel<MODEL, VT, GVOL, TFM, POS, INV>;
     size_t smem = 0;
     if (MODEL == DVR_EMISSION_ABSORPTION) {
         smem = sizeof(float4) * (size_t)p.R;
@@ -341,48 +361,59 @@ static cudaError_t launch_one(const Params& p, cudaStream_t stream)
 }
 
 template <int MODEL, typename VT, bool GVOL, int TFM>
-static cudaError_t pick_pos(const Params& p, bool pos, cudaStream_t s)
+static cudaError_t pick_pos(const Params& p, bool pos, int inv, cudaStream_t s)
 {
+    if constexpr (MODEL == DVR_EMISSION_ABSORPTION && std::is_same<VT, float>::value &&
+                  (TFM == kTFPrivate || TFM == kTFWarp)) {
+        if (inv == kInvAlpha32)
+            return pos ? launch_one<MODEL, VT, GVOL, TFM, true, kInvAlpha32>(p, s)
+                       : launch_one<MODEL, VT, GVOL, TFM, false, kInvAlpha32>(p, s);
+        if (inv == kInvAlpha64)
+            return pos ? launch_one<MODEL, VT, GVOL, TFM, true, kInvAlpha64>(p, s)
+                       : launch_one<MODEL, VT, GVOL, TFM, false, kInvAlpha64>(p, s);
+    }
+    if (inv != kInvDepth) return cudaErrorNotSupported;
     return pos ? launch_one<MODEL, VT, GVOL, TFM, true>(p, s)
                : launch_one<MODEL, VT, GVOL, TFM, false>(p, s);
 }
 
 template <int MODEL, typename VT, bool GVOL>
-static cudaError_t pick_tf(const Params& p, int tfm, bool pos, cudaStream_t s)
+static cudaError_t pick_tf(const Params& p, int tfm, bool pos, int inv, cudaStream_t s)
 {
     if constexpr (MODEL != DVR_EMISSION_ABSORPTION) {
-        return pick_pos<MODEL, VT, GVOL, kTFNone>(p, pos, s);
+        return pick_pos<MODEL, VT, GVOL, kTFNone>(p, pos, inv, s);
     } else {
-        if (tfm == kTFNone) return pick_pos<MODEL, VT, GVOL, kTFNone>(p, pos, s);
-        if (tfm == kTFImmediate) return pick_pos<MODEL, VT, GVOL, kTFImmediate>(p, pos, s);
-        if (p.R <= kPrivateMaxR) return pick_pos<MODEL, VT, GVOL, kTFPrivate>(p, pos, s);
-        return pick_pos<MODEL, VT, GVOL, kTFWarp>(p, pos, s);
+        if (tfm == kTFNone) return pick_pos<MODEL, VT, GVOL, kTFNone>(p, pos, inv, s);
+        if (tfm == kTFImmediate) return pick_pos<MODEL, VT, GVOL, kTFImmediate>(p, pos, inv, s);
+        if (p.R <= kPrivateMaxR) return pick_pos<MODEL, VT, GVOL, kTFPrivate>(p, pos, inv, s);
+        return pick_pos<MODEL, VT, GVOL, kTFWarp>(p, pos, inv, s);
     }
 }
 
 template <int MODEL, typename VT>
-static cudaError_t pick_vol(const Params& p, bool gvol, int tfm, bool pos, cudaStream_t s)
+static cudaError_t pick_vol(const Params& p, bool gvol, int tfm, bool pos, int inv, cudaStream_t s)
 {
-    return gvol ? pick_tf<MODEL, VT, true>(p, tfm, pos, s) : pick_tf<MODEL, VT, false>(p, tfm, pos, s);
+    return gvol ? pick_tf<MODEL, VT, true>(p, tfm, pos, inv, s) : pick_tf<MODEL, VT, false>(p, tfm, pos, inv, s);
 }
 
 template <int MODEL>
-static cudaError_t pick_dtype(const Params& p, int dtype, bool gvol, int tfm, bool pos, cudaStream_t s)
+static cudaError_t pick_dtype(const Params& p, int dtype, bool gvol, int tfm, bool pos, int inv, cudaStream_t s)
 {
     switch (dtype) {
-    case DVR_F32: return pick_vol<MODEL, float>(p, gvol, tfm, pos, s);
-    case DVR_F16: return pick_vol<MODEL, __half>(p, gvol, tfm, pos, s);
-    case DVR_BF16: return pick_vol<MODEL, __nv_bfloat16>(p, gvol, tfm, pos, s);
+    case DVR_F32: return pick_vol<MODEL, float>(p, gvol, tfm, pos, inv, s);
+    case DVR_F16: return pick_vol<MODEL, __half>(p, gvol, tfm, pos, inv, s);
+    case DVR_BF16: return pick_vol<MODEL, __nv_bfloat16>(p, gvol, tfm, pos, inv, s);
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_backward(const Params& p, int model, int vol_dtype, bool grad_volume,
-                            int tf_mode, bool grad_position, cudaStream_t stream)
+                            int tf_mode, bool grad_position, int inv_mode, cudaStream_t stream)
 {
     if (model == DVR_EMISSION_ABSORPTION)
-        return pick_dtype<DVR_EMISSION_ABSORPTION>(p, vol_dtype, grad_volume, tf_mode, grad_position, stream);
-    return pick_dtype<DVR_ABSORPTION>(p, vol_dtype, grad_volume, kTFNone, grad_position, stream);
+        return pick_dtype<DVR_EMISSION_ABSORPTION>(p, vol_dtype, grad_volume, tf_mode, grad_position, inv_mode,
+                                                   stream);
+    return pick_dtype<DVR_ABSORPTION>(p, vol_dtype, grad_volume, kTFNone, grad_position, inv_mode, stream);
 }
 
 }  // namespace dvr

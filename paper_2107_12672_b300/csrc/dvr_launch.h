@@ -14,9 +14,17 @@ namespace dvr {
 enum TFMode { kTFNone = 0, kTFDelayed = 1, kTFImmediate = 2, kTFPrivate = 3, kTFWarp = 4 };
 constexpr int kPrivateMaxR = 32;
 
+// How the adjoint recovers the accumulated opacity before each sample.
+// kInvDepth: from the exactly carried optical depth (default).
+// kInvAlpha32: Eq. inv-blend-forward as printed, A_i = (alpha - A_{i+1}) /
+//   (alpha - 1), in binary32 from the binary32 image opacity (ablation).
+// kInvAlpha64: the same, starting from the optical depth and dividing in
+//   binary64 once A > 0.99 (ablation).
+enum InvMode { kInvDepth = 0, kInvAlpha32 = 1, kInvAlpha64 = 2 };
+
 cudaError_t launch_forward(const Params& p, int model, int vol_dtype, cudaStream_t stream);
 cudaError_t launch_backward(const Params& p, int model, int vol_dtype, bool grad_volume,
-                            int tf_mode, bool grad_position, cudaStream_t stream);
+                            int tf_mode, bool grad_position, int inv_mode, cudaStream_t stream);
 cudaError_t launch_forward_color(const Params& p, int vol_dtype, cudaStream_t stream);
 cudaError_t launch_backward_color(const Params& p, int vol_dtype, bool grad_volume, bool grad_position,
                                   cudaStream_t stream);
