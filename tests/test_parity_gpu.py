@@ -476,3 +476,22 @@ def test_inversion_ablation_at_high_opacity():
     assert errs["depth"] <= GRAD_RTOL, errs
     assert errs["alpha64"] <= GRAD_RTOL, errs
     assert errs["alpha32"] > 10 * errs["depth"], errs
+
+
+# ------------------------------------------------------------- volume shapes
+@pytest.mark.parametrize("shape,model", [((24, 40, 33), "emission_absorption"),   # nz, ny, nx: non-cubic box
+                                         ((7, 2, 5), "emission_absorption"),      # two vertices along y
+                                         ((17, 9, 30), "absorption")])
+def test_non_cubic_volumes(shape, model):
+    """Boxes whose axes differ (the longest has length 1, the others shorter,
+    as for the paper's 256 x 256 x 161 tooth) and a 2-vertex axis."""
+    rng = np.random.default_rng(sum(shape))
+    vol = rng.uniform(0.05, 0.95, shape).astype(np.float32)
+    tf = syn.random_tf(9, seed=7, tau_max=12.0) if model == "emission_absorption" else None
+    w = syn.Workload("shape", model, [vol], tf, [syn.View(37, 31), syn.View(20, 23, ortho=True, ortho_height=1.1)],
+                     np.array([[0.7, 0.9, 1.6], [-1.2, 0.3, 0.8]], dtype=np.float32), None, 0.45,
+                     ("volume", "tf", "camera"))
+    want = ("volume", "tf", "eye") if tf is not None else ("volume", "eye")
+    gpu = _run_gpu(w, want=want)
+    ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
+    _compare(w, gpu, ref, want)
