@@ -153,6 +153,8 @@ class Clocks:
                 if self.t0 is not None:
                     self.samples.append((sm, r))
                 time.sleep(0.005)
+            if self.t0 is not None:   # one more at the end of the region (regions shorter than 5 ms)
+                self.samples.append((nv.clock(), nv.reasons()))
         except Exception as e:      # reported in the JSON line instead of the clocks
             self.error = f"{type(e).__name__}: {e}"[:200]
 

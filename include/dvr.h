@@ -73,7 +73,7 @@
 extern "C" {
 #endif
 
-#define DVR_ABI_VERSION 1
+#define DVR_ABI_VERSION 2
 
 /* exported from the shared library (which hides everything else) */
 #if defined(__GNUC__)
@@ -204,12 +204,28 @@ DVR_API int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_
  * aux                  device float[P][2] written by dvr_forward
  * grad_image           device float[P][C]: dL/d(image)
  * flags                bitwise OR of DVR_FLAG_*
- * Errors as dvr_forward.
+ * workspace            device scratch of at least
+ *                      dvr_backward_workspace_bytes(n_views) bytes, 16-byte
+ *                      aligned, owned by the caller. The call zeroes it on
+ *                      `stream` and uses it for the tile queues of the
+ *                      adjoint launches (warps fetch ray tiles from a
+ *                      counter, which balances rays of very different
+ *                      lengths); its contents afterwards are unspecified.
+ *                      Two calls in flight at once on different streams
+ *                      need separate workspaces.
+ * workspace_bytes      its size
+ * Errors as dvr_forward; DVR_ERR_ARG also when the workspace is NULL,
+ * misaligned or too small.
  */
 DVR_API int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                  const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
                  const float* aux, const float* grad_image, float* const* grad_volumes,
-                 float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags, void* stream);
+                 float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
+/* Bytes of device workspace a dvr_backward call over n_views views needs
+ * (a multiple of 256; 0 if n_views < 1). */
+DVR_API size_t dvr_backward_workspace_bytes(int32_t n_views);
 
 /*
  * Forward-mode differentiation w.r.t. the eye (Sec. 4.2; "forward-immediate"

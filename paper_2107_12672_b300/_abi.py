@@ -15,6 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # kernel variants); by default the in-tree build is loaded.
 LIB_PATH = os.environ.get("DVR_LIBRARY") or os.path.join(_HERE, "_lib", "libdvr.so")
 
+ABI_VERSION = 2          # DVR_ABI_VERSION of the header these argtypes follow
 DVR_OK = 0
 DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
 DVR_ABSORPTION, DVR_EMISSION_ABSORPTION, DVR_COLOR_VOLUME = 0, 1, 2
@@ -23,7 +24,8 @@ DVR_FLAG_INVERT_ALPHA32 = 2
 DVR_FLAG_INVERT_ALPHA64 = 4
 
 # every symbol include/dvr.h declares
-SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_set_tile_width", "dvr_get_tile_width", "dvr_forward", "dvr_backward", "dvr_forward_tangent",
+SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_set_tile_width", "dvr_get_tile_width", "dvr_forward", "dvr_backward",
+           "dvr_backward_workspace_bytes", "dvr_forward_tangent",
            "dvr_tangent_contract", "dvr_loss_l2", "dvr_loss_l1", "dvr_tf_prior", "dvr_volume_prior",
            "dvr_resample", "dvr_orbit_eye", "dvr_orbit_eye_backward")
 
@@ -62,12 +64,17 @@ def load() -> ctypes.CDLL:
         P, I32, I64, F, U32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
                                ctypes.c_uint32)
         lib.dvr_abi_version.restype = ctypes.c_int
+        if lib.dvr_abi_version() != ABI_VERSION:
+            raise DVRError(f"{LIB_PATH} has ABI version {lib.dvr_abi_version()}, the binding expects "
+                           f"{ABI_VERSION}: rebuild it")
         lib.dvr_set_tile_width.argtypes = [I32]
         lib.dvr_set_tile_width.restype = ctypes.c_int
         lib.dvr_get_tile_width.restype = ctypes.c_int
         lib.dvr_last_error.restype = ctypes.c_char_p
         lib.dvr_forward.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P]
-        lib.dvr_backward.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, P, P, U32, P]
+        lib.dvr_backward.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, P, P, U32, P, ctypes.c_size_t, P]
+        lib.dvr_backward_workspace_bytes.argtypes = [I32]
+        lib.dvr_backward_workspace_bytes.restype = ctypes.c_size_t
         lib.dvr_forward_tangent.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P]
         lib.dvr_tangent_contract.argtypes = [P, I32, I32, P, P, P, P]
         lib.dvr_loss_l2.argtypes = [P, P, I64, F, P, P, P]

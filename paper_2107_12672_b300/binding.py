@@ -104,6 +104,15 @@ class Scene:
     def tf_ref(self):
         return ctypes.byref(self.tf_desc) if self.tf_desc is not None else None
 
+    def workspace(self, lib, stream=None) -> torch.Tensor:
+        """Fresh adjoint workspace (tile-queue counters) from the caching
+        allocator, tied to the stream the call runs on."""
+        n = int(lib.dvr_backward_workspace_bytes(len(self.views)))
+        ws = torch.empty(n, dtype=torch.uint8, device=self.volumes[0].device)
+        if stream is not None:
+            ws.record_stream(stream)
+        return ws
+
 
 def forward(volumes, tf, model, views, eye, step_voxels, *, scene: Scene | None = None, image=None,
             aux=None, sample_count=None, stream=None):
@@ -148,10 +157,12 @@ def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, wa
         gv = (ctypes.c_void_p * len(sc.volumes))(*[_ptr(t) for t in g["volume"]])
     flags = _abi.DVR_FLAG_TF_IMMEDIATE if tf_immediate else 0
     flags |= {"depth": 0, "alpha32": _abi.DVR_FLAG_INVERT_ALPHA32, "alpha64": _abi.DVR_FLAG_INVERT_ALPHA64}[inversion]
-    rc = _abi.load().dvr_backward(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
-                                  len(sc.views), _ptr(eye), float(step_voxels), _ptr(aux),
-                                  _ptr(grad_image), gv, _ptr(g.get("tf")), _ptr(g.get("eye")),
-                                  _ptr(g.get("step")), flags, _stream_ptr(stream))
+    lib = _abi.load()
+    ws = sc.workspace(lib, stream)
+    rc = lib.dvr_backward(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
+                          len(sc.views), _ptr(eye), float(step_voxels), _ptr(aux),
+                          _ptr(grad_image), gv, _ptr(g.get("tf")), _ptr(g.get("eye")),
+                          _ptr(g.get("step")), flags, _ptr(ws), ws.numel(), _stream_ptr(stream))
     _abi.check(rc, "dvr_backward")
     return g
 

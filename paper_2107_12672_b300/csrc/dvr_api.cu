@@ -34,6 +34,17 @@ int cuda_fail(cudaError_t e, const char* what)
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 
+// Adjoint workspace: one tile-queue counter per launch (views are launched
+// in groups of kMaxViewsPerLaunch), each on its own 128-byte line.
+constexpr size_t kQueueStride = 128;
+
+size_t workspace_bytes(int n_views)
+{
+    if (n_views < 1) return 0;
+    const size_t launches = (size_t)(n_views + dvr::kMaxViewsPerLaunch - 1) / dvr::kMaxViewsPerLaunch;
+    return (launches * kQueueStride + 255) / 256 * 256;
+}
+
 struct Common {
     int dtype = 0;
     int channels = 1;
@@ -161,6 +172,8 @@ int dvr_get_tile_width(void) { return g_tile_w.load(std::memory_order_relaxed); 
 
 const char* dvr_last_error(void) { return g_err; }
 
+size_t dvr_backward_workspace_bytes(int32_t n_views) { return workspace_bytes(n_views); }
+
 int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                 const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
                 float* image, float* aux, unsigned long long* sample_count, void* stream)
@@ -190,7 +203,8 @@ int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, 
 int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                  const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
                  const float* aux, const float* grad_image, float* const* grad_volumes,
-                 float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags, void* stream)
+                 float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags,
+                 void* workspace, size_t workspace_bytes_, void* stream)
 {
     g_err[0] = 0;
     if (flags & ~(DVR_FLAG_TF_IMMEDIATE | DVR_FLAG_INVERT_ALPHA32 | DVR_FLAG_INVERT_ALPHA64))
@@ -222,6 +236,10 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
     const int tfm = grad_tf ? ((flags & DVR_FLAG_TF_IMMEDIATE) ? dvr::kTFImmediate : dvr::kTFDelayed)
                             : dvr::kTFNone;
     const bool pos = grad_eye != nullptr || grad_step != nullptr;
+    const size_t ws = workspace_bytes(n_views);
+    if (!workspace || workspace_bytes_ < ws)
+        return fail(DVR_ERR_ARG, "workspace %p of %zu bytes: %zu bytes needed", workspace, workspace_bytes_, ws);
+    if (!aligned(workspace, 16)) return fail(DVR_ERR_ARG, "workspace is not 16-byte aligned");
     if (!gvol && tfm == dvr::kTFNone && !pos) return DVR_OK;   // nothing requested
     // the scattering kernel variant is chosen per launch: when any volume
     // takes a gradient, every rendered volume needs a buffer
@@ -230,11 +248,15 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
             if (!grad_volumes[views[i].volume])
                 return fail(DVR_ERR_ARG, "view %d renders volume %d, which has no gradient buffer "
                             "while another volume has one", i, views[i].volume);
+    cudaError_t e0 = cudaMemsetAsync(workspace, 0, ws, (cudaStream_t)stream);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "dvr_backward workspace");
     dvr::Params p;
     for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
         const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
         pack(p, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
              step_voxels);
+        p.queue = reinterpret_cast<unsigned*>(static_cast<char*>(workspace)
+                                              + (size_t)(v0 / dvr::kMaxViewsPerLaunch) * kQueueStride);
         if (grad_volumes)
             for (int i = 0; i < n_volumes; ++i) p.vol[i].grad = grad_volumes[i];
         p.aux = const_cast<float*>(aux);

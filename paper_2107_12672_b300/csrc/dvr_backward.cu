@@ -25,6 +25,7 @@
 //  - eye / step: x^_o, w^ summed in registers along the ray (Alg. 2 last
 //    loop line), chained through f_camera per ray, warp-reduced, one atomic
 //    per warp.
+#include <atomic>
 #include <type_traits>
 
 #include "dvr_device.cuh"
@@ -99,8 +100,12 @@ backward_kernel(const __grid_constant__ Params p)
     float* my_tfg = tfg + warp * p.R * 4;
     const float Rm1 = (float)(p.R - 1);
 
-    const int tile = blockIdx.x * kWarps + warp;
-    if (tile < p.total_tiles) {
+    // warps take tiles from the queue until it runs dry; the scatter variants
+    // (GVOL) keep one tile per warp (measured faster there: with the queue a
+    // block's warps no longer march neighbouring tiles together)
+    constexpr bool QUEUE = !GVOL;
+    for (int tile = QUEUE ? next_tile(p.queue, lane) : blockIdx.x * kWarps + warp; tile < p.total_tiles;
+         tile = QUEUE ? next_tile(p.queue, lane) : p.total_tiles) {
         const int v = find_view(p, tile);
         const ViewDesc& vw = p.view[v];
         int px, py;
@@ -160,6 +165,7 @@ backward_kernel(const __grid_constant__ Params p)
             fetch_sample_reuse<VT>(vol, G, m, N - 1, 0xffffffffu, n1);
             fetch_sample_reuse<VT>(vol, G, m, N - 2, n1.c.base, n2);
         }
+#pragma unroll (GVOL ? 1 : 2)
         for (int i = N - 1; i >= 0; --i) {
             const float fi = (float)i;
             MCell cur = n1;
@@ -355,7 +361,24 @@ static cudaError_t launch_one(const Params& p, cudaStream_t stream)
         if (err != cudaSuccess) return err;
         configured |= 1ull << dev;
     }
-    const int blocks = (p.total_tiles + kWarps - 1) / kWarps;   // one tile per warp
+    // one tile per warp; with the tile queue, as many blocks as fit on the
+    // device at once
+    int blocks = (p.total_tiles + kWarps - 1) / kWarps;
+    if (!GVOL) {
+        // resident blocks per SM for this shared-memory size, cached per
+        // instantiation (smem << 8 | blocks; the last query wins)
+        static std::atomic<unsigned long long> occ{0};
+        unsigned long long o = occ.load(std::memory_order_relaxed);
+        if ((o >> 8) != smem || o == 0) {
+            int per_sm = 0;
+            cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWarps * 32, smem);
+            if (err != cudaSuccess) return err;
+            o = (unsigned long long)smem << 8 | (unsigned long long)(per_sm & 0xff);
+            occ.store(o, std::memory_order_relaxed);
+        }
+        const int cap = (int)(o & 0xff) * sm_count();
+        if (cap > 0 && blocks > cap) blocks = cap;
+    }
     k<<<blocks, kWarps * 32, smem, stream>>>(p);
     return cudaGetLastError();
 }

@@ -64,6 +64,7 @@ struct Params {
     float* grad_eye;
     float* grad_step;
     unsigned long long* sample_count;
+    unsigned* queue;                 // adjoint tile queue: a counter zeroed before the launch
 };
 
 // ---------------------------------------------------------------- storage
@@ -420,6 +421,17 @@ __device__ __forceinline__ void tile_pixel(const Params& p, const ViewDesc& vw, 
     const int ty = center_out(local / vw.tiles_x, tiles_y);
     px = tx * tw + (lane & (tw - 1));
     py = ty * th + (lane / tw);
+}
+
+// Dynamic tile queue: a warp takes the next unprocessed tile from a counter
+// in global memory (zeroed before the launch), so warps whose rays are short
+// go on to further tiles instead of idling until their block ends. Together
+// with the centre-out order this hands out the long tiles first.
+__device__ __forceinline__ int next_tile(unsigned* queue, int lane)
+{
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(queue, 1u);
+    return (int)__shfl_sync(0xffffffffu, t, 0);
 }
 
 // Warp tile -> (view, pixel) mapping.

@@ -55,6 +55,7 @@ forward_kernel(const __grid_constant__ Params p)
             fetch_sample_reuse<VT>(vol, G, m, 0, 0xffffffffu, n1);
             fetch_sample_reuse<VT>(vol, G, m, 1, n1.c.base, n2);
         }
+#pragma unroll 3
         for (int i = 0; i < N; ++i) {
             MCell cur = n1;
             cell_resolve(cur, last_v);

@@ -27,7 +27,9 @@ def test_library_loads_and_exports_every_symbol():
     lib = _abi.load()
     for name in _declared():
         assert hasattr(lib, name), name
-    assert lib.dvr_abi_version() == 1
+    header = open(os.path.join(ROOT, "include", "dvr.h")).read()
+    version = int(re.search(r"#define DVR_ABI_VERSION (\d+)", header).group(1))
+    assert lib.dvr_abi_version() == version == _abi.ABI_VERSION
     out = subprocess.run(["nm", "-D", "--defined-only", _abi.LIB_PATH], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\bT (dvr_\w+)", out))
     assert set(_declared()) <= exported
@@ -113,11 +115,28 @@ def test_argument_errors_need_no_gpu(case, code):
     assert lib.dvr_last_error().decode()
 
 
-def test_backward_rejects_unknown_flags():
+def _call_backward(workspace=4096, nbytes=256, flags=0):
     lib = _abi.load()
-    rc = lib.dvr_backward(_one_volume(), 1, None, 0, _one_view(), 1, 16, 0.5, 64, 64, None, None,
-                          None, None, 0x80, None)
-    assert rc == -1 and b"flag" in lib.dvr_last_error()
+    return lib.dvr_backward(_one_volume(), 1, None, 0, _one_view(), 1, 16, 0.5, 64, 64, None, None,
+                            128, None, flags, workspace, nbytes, None)
+
+
+def test_backward_rejects_unknown_flags():
+    assert _call_backward(flags=0x80) == -1
+    assert b"flag" in _abi.load().dvr_last_error()
+
+
+def test_backward_workspace_size():
+    lib = _abi.load()
+    # one 128-byte tile-queue counter per launch of up to 512 views, rounded to 256 bytes
+    assert [lib.dvr_backward_workspace_bytes(n) for n in (0, 1, 512, 513, 1024, 1025, 4096)] == \
+        [0, 256, 256, 256, 256, 512, 1024]
+
+
+@pytest.mark.parametrize("workspace,nbytes", [(None, 256), (4096, 255), (4104, 256)])
+def test_backward_rejects_bad_workspace(workspace, nbytes):
+    assert _call_backward(workspace, nbytes) == -1
+    assert b"workspace" in _abi.load().dvr_last_error()
 
 
 def test_no_oracle_in_the_product_path():
