@@ -300,6 +300,34 @@ DVR_API int dvr_orbit_eye(const float* params, int32_t n, float* eye, void* stre
 DVR_API int dvr_orbit_eye_backward(const float* params, const float* grad_eye, int32_t n,
                            float* grad_params, void* stream);
 
+/*
+ * dvr_backward for callers that cannot allocate device memory. The paper
+ * has no counterpart: this is an interface convenience. Some hosts hand the
+ * renderer a stream but keep every byte of device memory to themselves (a
+ * plugin inside another application with its own memory budget), and some
+ * loops must not call cudaMalloc because it can synchronise the whole
+ * device. Such callers cannot provide the workspace dvr_backward asks for.
+ *
+ * Arguments, results and errors are those of dvr_backward without
+ * `workspace` and `workspace_bytes`. The tile-queue counters live instead in
+ * a fixed 256-byte array in the library's device memory (each GPU that
+ * loads the library holds it until the process exits), so one call covers
+ * at most 1024 views; larger calls return DVR_ERR_ARG and launch nothing.
+ * - The first call on a device looks up that array's device address with
+ *   the device current; make that first call before any stream capture.
+ * - Every call shares the array: each call zeroes the counters on `stream`
+ *   before its launches, and two calls whose work overlaps on the GPU
+ *   (different streams, or different host threads) race on them and give
+ *   wrong gradients. Order such calls, or use dvr_backward with separate
+ *   workspaces.
+ * - Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ */
+DVR_API int dvr_backward_noalloc(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
+                                 int32_t model, const dvr_view* views, int32_t n_views, const float* eye,
+                                 float step_voxels, const float* aux, const float* grad_image,
+                                 float* const* grad_volumes, float* grad_tf, float* grad_eye,
+                                 float* grad_step, uint32_t flags, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

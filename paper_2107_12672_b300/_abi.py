@@ -27,7 +27,7 @@ DVR_FLAG_INVERT_ALPHA64 = 4
 SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_set_tile_width", "dvr_get_tile_width", "dvr_forward", "dvr_backward",
            "dvr_backward_workspace_bytes", "dvr_forward_tangent",
            "dvr_tangent_contract", "dvr_loss_l2", "dvr_loss_l1", "dvr_tf_prior", "dvr_volume_prior",
-           "dvr_resample", "dvr_orbit_eye", "dvr_orbit_eye_backward")
+           "dvr_resample", "dvr_orbit_eye", "dvr_orbit_eye_backward", "dvr_backward_noalloc")
 
 
 class DvrVolume(ctypes.Structure):
@@ -75,6 +75,8 @@ def load() -> ctypes.CDLL:
         lib.dvr_backward.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, P, P, U32, P, ctypes.c_size_t, P]
         lib.dvr_backward_workspace_bytes.argtypes = [I32]
         lib.dvr_backward_workspace_bytes.restype = ctypes.c_size_t
+        lib.dvr_backward_noalloc.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, P, P, U32, P]
+        lib.dvr_backward_noalloc.restype = ctypes.c_int
         lib.dvr_forward_tangent.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P]
         lib.dvr_tangent_contract.argtypes = [P, I32, I32, P, P, P, P]
         lib.dvr_loss_l2.argtypes = [P, P, I64, F, P, P, P]

@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <mutex>
 
 #include "dvr.h"
 #include "dvr_launch.h"
@@ -403,3 +404,61 @@ int dvr_orbit_eye_backward(const float* params, const float* grad_eye, int32_t n
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// dvr_backward_noalloc: the adjoint with its tile-queue counters in a fixed
+// array of the library's own device memory instead of a caller workspace,
+// for callers that have no way to allocate one.
+
+// 256 bytes: two counter lines, enough for two launches of up to
+// kMaxViewsPerLaunch views each (1024 views per call).
+constexpr size_t kNoallocScratchBytes = 256;
+constexpr int kNoallocMaxViews = (int)(kNoallocScratchBytes / kQueueStride) * dvr::kMaxViewsPerLaunch;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64];   // device address of g_noalloc_scratch, per device
+
+// In host code g_noalloc_scratch names a host-side shadow, not device memory,
+// so the kernels get the address the runtime reports for the current device.
+int noalloc_scratch(void** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "dvr_backward_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(DVR_ERR_ARG, "dvr_backward_noalloc: device %d beyond 63", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "dvr_backward_noalloc: cudaGetSymbolAddress");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return DVR_OK;
+}
+
+}  // namespace
+
+extern "C" int dvr_backward_noalloc(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
+                                    int32_t model, const dvr_view* views, int32_t n_views, const float* eye,
+                                    float step_voxels, const float* aux, const float* grad_image,
+                                    float* const* grad_volumes, float* grad_tf, float* grad_eye,
+                                    float* grad_step, uint32_t flags, void* stream)
+{
+    g_err[0] = 0;
+    const size_t need = workspace_bytes(n_views);
+    if (need > kNoallocScratchBytes)
+        return fail(DVR_ERR_ARG, "dvr_backward_noalloc: %d views need %zu bytes of tile-queue scratch, the "
+                    "static array holds %zu (at most %d views per call; use dvr_backward with a workspace)",
+                    n_views, need, kNoallocScratchBytes, kNoallocMaxViews);
+    void* scratch = nullptr;
+    const int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    // dvr_backward zeroes the counters on `stream` before it launches
+    return dvr_backward(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, aux, grad_image,
+                        grad_volumes, grad_tf, grad_eye, grad_step, flags, scratch, kNoallocScratchBytes,
+                        stream);
+}
