@@ -81,7 +81,7 @@ backward_kernel(const __grid_constant__ Params p)
     constexpr bool EA = MODEL == DVR_EMISSION_ABSORPTION;
     extern __shared__ float4 smem[];
     float4* tf_s = smem;                                   // [R]
-    float* tfg = reinterpret_cast<float*>(smem + p.R);     // TF gradient copies
+    float* tfg = reinterpret_cast<float*>(smem + 2 * p.R); // TF gradient copies
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     if (EA) {
@@ -159,19 +159,21 @@ backward_kernel(const __grid_constant__ Params p)
 
         // software pipeline with same-cell reuse as in the forward march,
         // in reverse order
+        TFCache tfc;
+        tf_cache_init(tfc);
         MCell n1, n2;
-        float last_v[8];
+        float2 last_v[4];
         if (N > 0) {
             fetch_sample_reuse<VT>(vol, G, m, N - 1, 0xffffffffu, n1);
             fetch_sample_reuse<VT>(vol, G, m, N - 2, n1.c.base, n2);
         }
-#pragma unroll (GVOL ? 1 : 2)
+#pragma unroll (GVOL ? 1 : 3)
         for (int i = N - 1; i >= 0; --i) {
             const float fi = (float)i;
             MCell cur = n1;
             cell_resolve(cur, last_v);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) last_v[k] = cur.c.v[k];
+            for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
             n1 = n2;
             fetch_sample_reuse<VT>(vol, G, m, i - 2, n1.c.base, n2);
             const Cell& c = cur.c;
@@ -180,9 +182,9 @@ backward_kernel(const __grid_constant__ Params p)
             float d_hat;
             if (EA) {
                 TFSample s;
-                tf_lookup(tf_s, p.R, d, s);
+                tf_lookup(tf_s, p.R, d, tfc, s);
                 const float x = G.dt * s.c.w;
-                const float em = expm1f(-x);
+                const float em = neg_expm1_br(x);
                 const float alpha = -em;
                 const float ea = 1.f + em;            // 1 - alpha
                 float T;                              // 1 - A_i
@@ -346,7 +348,7 @@ static cudaError_t launch_one(const Params& p, cudaStream_t stream)
     auto k = backward_kernel<MODEL, VT, GVOL, TFM, POS, INV>;
     size_t smem = 0;
     if (MODEL == DVR_EMISSION_ABSORPTION) {
-        smem = sizeof(float4) * (size_t)p.R;
+        smem = sizeof(float4) * 2 * (size_t)p.R;
         if (TFM == kTFPrivate) smem += sizeof(float) * 4 * 32 * kWarps * (size_t)p.R;
         if (TFM == kTFWarp) smem += sizeof(float) * 4 * kWarps * (size_t)p.R;
     }
@@ -356,7 +358,7 @@ static cudaError_t launch_one(const Params& p, cudaStream_t stream)
     cudaGetDevice(&dev);
     if (dev < 64 && !(configured >> dev & 1ull)) {
         cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(sizeof(float4) * kMaxTF * (1 + kWarps)
+                                               (int)(sizeof(float4) * kMaxTF * (2 + kWarps)
                                                      + sizeof(float) * 4 * 32 * kWarps * kPrivateMaxR));
         if (err != cudaSuccess) return err;
         configured |= 1ull << dev;

@@ -138,7 +138,7 @@ forward_color_kernel(const __grid_constant__ Params p)
             fetch4<VT>(vol, G, m, i + 1, nxt);
             const float4 s = cell4_value(c);
             const float x = G.dt * s.w;
-            const float em = expm1f(-x);
+            const float em = neg_expm1_sel(x);
             const float wgt = -T * em;
             C0 = fmaf(wgt, s.x, C0);
             C1 = fmaf(wgt, s.y, C1);
@@ -213,7 +213,7 @@ backward_color_kernel(const __grid_constant__ Params p)
         fetch4<VT>(vol, G, m, i - 1, nxt);
         const float4 s = cell4_value(c);
         const float x = G.dt * s.w;
-        const float em = expm1f(-x);
+        const float em = neg_expm1_br(x);
         const float alpha = -em;
         const float ea = 1.f + em;
         float s2, err;

@@ -81,6 +81,59 @@ template <> struct Load<__nv_bfloat16> {
     }
 };
 
+// ------------------------------------------------- packed binary32 pairs
+// sm_100 and later issue two binary32 additions, multiplications or fused
+// multiply-adds per instruction on a register pair (FADD2 / FMUL2 / FFMA2).
+// Each half is rounded exactly as the scalar operation, so a packed
+// evaluation gives the same bits as the scalar one in the same order.
+__device__ __forceinline__ float2 p2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long*>(&a)),
+          "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+    return *reinterpret_cast<const float2*>(&d);
+}
+__device__ __forceinline__ float2 p2dup(float a) { return make_float2(a, a); }
+
+// expm1(-x), the negated opacity -alpha of a segment with optical depth x
+// (Sec. 3.1, alpha = 1 - exp(-dt tau)). For |x| <= 1/8 the Taylor series of
+// e^y - 1 at y = -x to degree 7 in Horner form (truncation below 2^-33
+// relative, far under one binary32 ulp); beyond, exp(-x) - 1 with CUDA's
+// expf (exact subtraction there, within ~1e-6 relative). Two forms with the
+// same value: a select for the forward marches, whose loop bodies schedule
+// best without a branch, and a branch for the adjoints, which then skip the
+// unused expf. Every kernel takes alpha from one of them, so forward,
+// adjoint, forward-mode and colour-volume passes see the same opacities.
+__device__ __forceinline__ float expm1_taylor(float y)
+{
+    float q = fmaf(y, 1.f / 5040.f, 1.f / 720.f);
+    q = fmaf(y, q, 1.f / 120.f);
+    q = fmaf(y, q, 1.f / 24.f);
+    q = fmaf(y, q, 1.f / 6.f);
+    q = fmaf(y, q, 0.5f);
+    q = fmaf(y, q, 1.f);
+    return y * q;
+}
+
+static __device__ __noinline__ float neg_expm1_wide(float x) { return expf(-x) - 1.f; }
+
+__device__ __forceinline__ float neg_expm1_sel(float x)
+{
+    const float t = expm1_taylor(-x);
+    const float w = expf(-x) - 1.f;
+    return fabsf(x) <= 0.125f ? t : w;
+}
+
+__device__ __forceinline__ float neg_expm1_br(float x)
+{
+    if (fabsf(x) <= 0.125f) return expm1_taylor(-x);
+    return neg_expm1_wide(x);
+}
+
 // --------------------------------------------------------------- the ray
 struct Ray {
     float o[3], w[3], xo[3];
@@ -230,17 +283,18 @@ __device__ __forceinline__ float march_coord(const March& m, int a, float fi)
 // Trilinear interpolation at grid coordinate g (clamped to the box), split
 // into locating the cell and loading its 8 corners (cell_fetch) and the
 // interpolation itself (cell_value), so that a march can issue the loads of
-// the next sample before it interpolates the current one.
+// the next sample before it interpolates the current one. The corners are
+// held as z pairs, vz[x + 2y] = (corner (x, y, 0), corner (x, y, 1)), so that
+// the x and y lerps of both z planes run as packed pairs.
 struct Cell {
     uint32_t base;                   // index of corner (0,0,0)
     float fx, fy, fz;
     bool in[3];                      // false where g was clamped
-    float v[8];                      // corner values, bit i: x, y, z
+    float2 vz[4];
 };
 
-template <typename VT>
-__device__ __forceinline__ void cell_fetch(const VT* __restrict__ vol, const Grid& G, const float gc[3],
-                                           Cell& c)
+// Cell of grid coordinate gc: corner index, fractions, clamp flags.
+__device__ __forceinline__ void cell_locate(const Grid& G, const float gc[3], Cell& c)
 {
     int j[3];
     float fr[3];
@@ -253,49 +307,64 @@ __device__ __forceinline__ void cell_fetch(const VT* __restrict__ vol, const Gri
         fr[a] = gg - (float)j[a];
     }
     c.fx = fr[0]; c.fy = fr[1]; c.fz = fr[2];
-    const uint32_t sx = 1u, sy = (uint32_t)G.n[0], sz = (uint32_t)G.n[0] * (uint32_t)G.n[1];
-    c.base = (uint32_t)j[0] + sy * (uint32_t)j[1] + sz * (uint32_t)j[2];
+    c.base = (uint32_t)j[0] + (uint32_t)G.n[0] * ((uint32_t)j[1] + (uint32_t)G.n[1] * (uint32_t)j[2]);
+}
+
+template <typename VT>
+__device__ __forceinline__ void cell_load(const VT* __restrict__ vol, const Grid& G, Cell& c)
+{
+    const uint32_t sy = (uint32_t)G.n[0], sz = (uint32_t)G.n[0] * (uint32_t)G.n[1];
     const VT* p = vol + c.base;
-    c.v[0] = Load<VT>::get(p);
-    c.v[1] = Load<VT>::get(p + sx);
-    c.v[2] = Load<VT>::get(p + sy);
-    c.v[3] = Load<VT>::get(p + sy + sx);
-    c.v[4] = Load<VT>::get(p + sz);
-    c.v[5] = Load<VT>::get(p + sz + sx);
-    c.v[6] = Load<VT>::get(p + sz + sy);
-    c.v[7] = Load<VT>::get(p + sz + sy + sx);
+    c.vz[0].x = Load<VT>::get(p);
+    c.vz[1].x = Load<VT>::get(p + 1);
+    c.vz[2].x = Load<VT>::get(p + sy);
+    c.vz[3].x = Load<VT>::get(p + sy + 1);
+    c.vz[0].y = Load<VT>::get(p + sz);
+    c.vz[1].y = Load<VT>::get(p + sz + 1);
+    c.vz[2].y = Load<VT>::get(p + sz + sy);
+    c.vz[3].y = Load<VT>::get(p + sz + sy + 1);
+}
+
+template <typename VT>
+__device__ __forceinline__ void cell_fetch(const VT* __restrict__ vol, const Grid& G, const float gc[3],
+                                           Cell& c)
+{
+    cell_locate(G, gc, c);
+    cell_load<VT>(vol, G, c);
+}
+
+// x lerps of both z planes for rows y = 0 and y = 1, then the y lerp of
+// both planes: returns (c0, c1), the values on the z = 0 and z = 1 faces.
+__device__ __forceinline__ float2 cell_faces(const Cell& c, float2& e0, float2& e1, float2& y01)
+{
+    const float2 fx = p2dup(c.fx);
+    e0 = p2sub(c.vz[1], c.vz[0]);                  // x differences, row y = 0 (z0, z1)
+    e1 = p2sub(c.vz[3], c.vz[2]);                  // row y = 1
+    const float2 r0 = p2fma(fx, e0, c.vz[0]);      // (c00, c01)
+    const float2 r1 = p2fma(fx, e1, c.vz[2]);      // (c10, c11)
+    y01 = p2sub(r1, r0);
+    return p2fma(p2dup(c.fy), y01, r0);
 }
 
 __device__ __forceinline__ float cell_value(const Cell& c)
 {
-    const float c00 = fmaf(c.fx, c.v[1] - c.v[0], c.v[0]);
-    const float c10 = fmaf(c.fx, c.v[3] - c.v[2], c.v[2]);
-    const float c01 = fmaf(c.fx, c.v[5] - c.v[4], c.v[4]);
-    const float c11 = fmaf(c.fx, c.v[7] - c.v[6], c.v[6]);
-    const float c0 = fmaf(c.fy, c10 - c00, c00);
-    const float c1 = fmaf(c.fy, c11 - c01, c01);
-    return fmaf(c.fz, c1 - c0, c0);
+    float2 e0, e1, y01;
+    const float2 f = cell_faces(c, e0, e1, y01);
+    return fmaf(c.fz, f.y - f.x, f.x);
 }
 
 // Density and its derivative w.r.t. the grid coordinate (zero along clamped
 // axes), sharing the lerps of cell_value.
 __device__ __forceinline__ float cell_value_grad(const Cell& c, float dg[3])
 {
-    const float e00 = c.v[1] - c.v[0], e10 = c.v[3] - c.v[2];
-    const float e01 = c.v[5] - c.v[4], e11 = c.v[7] - c.v[6];
-    const float c00 = fmaf(c.fx, e00, c.v[0]);
-    const float c10 = fmaf(c.fx, e10, c.v[2]);
-    const float c01 = fmaf(c.fx, e01, c.v[4]);
-    const float c11 = fmaf(c.fx, e11, c.v[6]);
-    const float y0 = c10 - c00, y1 = c11 - c01;
-    const float c0 = fmaf(c.fy, y0, c00);
-    const float c1 = fmaf(c.fy, y1, c01);
-    const float ex0 = fmaf(c.fy, e10 - e00, e00);
-    const float ex1 = fmaf(c.fy, e11 - e01, e01);
-    dg[0] = c.in[0] ? fmaf(c.fz, ex1 - ex0, ex0) : 0.f;
-    dg[1] = c.in[1] ? fmaf(c.fz, y1 - y0, y0) : 0.f;
-    dg[2] = c.in[2] ? c1 - c0 : 0.f;
-    return fmaf(c.fz, c1 - c0, c0);
+    float2 e0, e1, y01;
+    const float2 f = cell_faces(c, e0, e1, y01);
+    const float2 ex = p2fma(p2dup(c.fy), p2sub(e1, e0), e0);   // d/dx on both z faces
+    dg[0] = c.in[0] ? fmaf(c.fz, ex.y - ex.x, ex.x) : 0.f;
+    dg[1] = c.in[1] ? fmaf(c.fz, y01.y - y01.x, y01.x) : 0.f;
+    const float dz = f.y - f.x;
+    dg[2] = c.in[2] ? dz : 0.f;
+    return fmaf(c.fz, dz, f.x);
 }
 
 template <typename VT>
@@ -323,43 +392,24 @@ __device__ __forceinline__ void fetch_sample_reuse(const VT* __restrict__ vol, c
 {
     const float fi = (float)i;
     const float gc[3] = {march_coord(m, 0, fi), march_coord(m, 1, fi), march_coord(m, 2, fi)};
-    Cell& c = mc.c;
-    int j[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float hi = (float)(G.n[a] - 1);
-        c.in[a] = (gc[a] >= 0.f) && (gc[a] <= hi);
-        const float gg = fminf(fmaxf(gc[a], 0.f), hi);
-        j[a] = min((int)gg, G.n[a] - 2);
-        (a == 0 ? c.fx : (a == 1 ? c.fy : c.fz)) = gg - (float)j[a];
-    }
-    const uint32_t sy = (uint32_t)G.n[0], sz = (uint32_t)G.n[0] * (uint32_t)G.n[1];
-    c.base = (uint32_t)j[0] + sy * (uint32_t)j[1] + sz * (uint32_t)j[2];
-    mc.reuse = c.base == prev_base;
-    if (!mc.reuse) {
-        const VT* p = vol + c.base;
-        c.v[0] = Load<VT>::get(p);
-        c.v[1] = Load<VT>::get(p + 1);
-        c.v[2] = Load<VT>::get(p + sy);
-        c.v[3] = Load<VT>::get(p + sy + 1);
-        c.v[4] = Load<VT>::get(p + sz);
-        c.v[5] = Load<VT>::get(p + sz + 1);
-        c.v[6] = Load<VT>::get(p + sz + sy);
-        c.v[7] = Load<VT>::get(p + sz + sy + 1);
-    }
+    cell_locate(G, gc, mc.c);
+    mc.reuse = mc.c.base == prev_base;
+    if (!mc.reuse) cell_load<VT>(vol, G, mc.c);
 }
 
 // Corners of a fetched sample: its own loads, or those of the previous one.
-__device__ __forceinline__ void cell_resolve(MCell& mc, const float last_v[8])
+__device__ __forceinline__ void cell_resolve(MCell& mc, const float2 last[4])
 {
     if (mc.reuse) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) mc.c.v[k] = last_v[k];
+        for (int k = 0; k < 4; ++k) mc.c.vz[k] = last[k];
     }
 }
 
-// f_TF from the shared-memory copy: R rows at densities r/(R-1), linear in
-// between, density clamped to [0, 1].
+// f_TF from the shared-memory copy. R rows at densities r/(R-1), linear in
+// between, density clamped to [0, 1]. The copy holds, per row k, the row
+// itself at [2k] and its difference to row k + 1 at [2k + 1], so a lookup is
+// two 16-byte reads and one packed FMA per channel pair.
 struct TFSample {
     float4 c;                        // r, g, b, tau
     float4 dc;                       // row k+1 - row k
@@ -368,35 +418,53 @@ struct TFSample {
     bool slope;
 };
 
-__device__ __forceinline__ void tf_lookup(const float4* __restrict__ tf, int R, float d, TFSample& s)
+// Rows k and k + 1 of the last lookup, kept in registers: a march's
+// densities change slowly, so consecutive samples mostly stay in one TF
+// segment and read no shared memory (a lane whose segment is unchanged sits
+// out the reload, which then touches fewer banks).
+struct TFCache {
+    int k;
+    float4 a, dc;
+};
+
+__device__ __forceinline__ void tf_cache_init(TFCache& t) { t.k = -1; }
+
+__device__ __forceinline__ void tf_lookup(const float4* __restrict__ tf, int R, float d, TFCache& t,
+                                          TFSample& s)
 {
     s.slope = (d >= 0.f) && (d <= 1.f);
     const float dc = fminf(fmaxf(d, 0.f), 1.f);
     const float u = dc * (float)(R - 1);
     s.k = min((int)u, R - 2);
     s.fr = u - (float)s.k;
-    const float4 a = tf[s.k];
-    const float4 b = tf[s.k + 1];
-    s.dc = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
-    s.c.x = fmaf(s.fr, s.dc.x, a.x);
-    s.c.y = fmaf(s.fr, s.dc.y, a.y);
-    s.c.z = fmaf(s.fr, s.dc.z, a.z);
-    s.c.w = fmaf(s.fr, s.dc.w, a.w);
+    if (s.k != t.k) {
+        t.a = tf[2 * s.k];
+        t.dc = tf[2 * s.k + 1];
+        t.k = s.k;
+    }
+    s.dc = t.dc;
+    const float2 fr = p2dup(s.fr);
+    const float2 lo = p2fma(fr, make_float2(t.dc.x, t.dc.y), make_float2(t.a.x, t.a.y));
+    const float2 hi = p2fma(fr, make_float2(t.dc.z, t.dc.w), make_float2(t.a.z, t.a.w));
+    s.c = make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
-// Stage the TF (float or half rows) into shared memory as float4.
+// Stage the TF (float or half rows) into shared memory as float4 pairs
+// (row, difference to the next row); 2R float4.
+__device__ __forceinline__ float4 tf_row(const Params& p, int r)
+{
+    if (p.tf_dtype == DVR_F32) return __ldg(reinterpret_cast<const float4*>(p.tf) + r);
+    const __half* h = reinterpret_cast<const __half*>(p.tf) + 4 * r;
+    return make_float4(__half2float(h[0]), __half2float(h[1]), __half2float(h[2]), __half2float(h[3]));
+}
+
 __device__ __forceinline__ void stage_tf(const Params& p, float4* tf_s)
 {
     for (int r = threadIdx.x; r < p.R; r += blockDim.x) {
-        float4 v;
-        if (p.tf_dtype == DVR_F32) {
-            v = __ldg(reinterpret_cast<const float4*>(p.tf) + r);
-        } else {
-            const __half* h = reinterpret_cast<const __half*>(p.tf) + 4 * r;
-            v = make_float4(__half2float(h[0]), __half2float(h[1]), __half2float(h[2]),
-                            __half2float(h[3]));
-        }
-        tf_s[r] = v;
+        const float4 a = tf_row(p, r);
+        const float4 b = r + 1 < p.R ? tf_row(p, r + 1) : a;
+        tf_s[2 * r] = a;
+        tf_s[2 * r + 1] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
     }
 }
 

@@ -14,7 +14,7 @@ template <int MODEL, typename VT>
 __global__ void __launch_bounds__(kWarps * 32, DVR_FWD_MIN_BLOCKS)
 forward_kernel(const __grid_constant__ Params p)
 {
-    __shared__ float4 tf_s[MODEL == DVR_EMISSION_ABSORPTION ? kMaxTF : 1];
+    __shared__ float4 tf_s[MODEL == DVR_EMISSION_ABSORPTION ? 2 * kMaxTF : 1];
     if (MODEL == DVR_EMISSION_ABSORPTION) {
         stage_tf(p, tf_s);
         __syncthreads();
@@ -49,8 +49,10 @@ forward_kernel(const __grid_constant__ Params p)
         // flight while sample i is composited (positions past the ray end are
         // clamped to the box, so the extra fetches stay in bounds); a sample
         // in the same cell as its predecessor loads nothing
+        TFCache tfc;
+        tf_cache_init(tfc);
         MCell n1, n2;
-        float last_v[8];
+        float2 last_v[4];
         if (N > 0) {
             fetch_sample_reuse<VT>(vol, G, m, 0, 0xffffffffu, n1);
             fetch_sample_reuse<VT>(vol, G, m, 1, n1.c.base, n2);
@@ -60,7 +62,7 @@ forward_kernel(const __grid_constant__ Params p)
             MCell cur = n1;
             cell_resolve(cur, last_v);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) last_v[k] = cur.c.v[k];
+            for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
             n1 = n2;
             fetch_sample_reuse<VT>(vol, G, m, i + 2, n1.c.base, n2);
             const Cell& c = cur.c;
@@ -68,9 +70,9 @@ forward_kernel(const __grid_constant__ Params p)
             float x;
             if (MODEL == DVR_EMISSION_ABSORPTION) {
                 TFSample s;
-                tf_lookup(tf_s, p.R, d, s);
+                tf_lookup(tf_s, p.R, d, tfc, s);
                 x = G.dt * s.c.w;
-                const float em = expm1f(-x);          // -alpha_i
+                const float em = neg_expm1_sel(x);        // -alpha_i
                 const float wgt = -T * em;            // (1 - A_i) alpha_i
                 C0 = fmaf(wgt, s.c.x, C0);
                 C1 = fmaf(wgt, s.c.y, C1);

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
 {
     constexpr bool EA = MODEL == DVR_EMISSION_ABSORPTION;
-    __shared__ float4 tf_s[EA ? kMaxTF : 1];
+    __shared__ float4 tf_s[EA ? 2 * kMaxTF : 1];
     if (EA) {
         stage_tf(p, tf_s);
         __syncthreads();
@@ -140,6 +140,8 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
 
     float sh = 0.f, sl = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
     float dC[3][3] = {}, dT[3] = {0.f, 0.f, 0.f}, dS[3] = {0.f, 0.f, 0.f};
+    TFCache tfc;
+    tf_cache_init(tfc);
     Cell nxt;
     if (N > 0) fetch_sample<VT>(vol, G, m, 0, nxt);
     for (int i = 0; i < N; ++i) {
@@ -159,9 +161,9 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
         float x;
         if (EA) {
             TFSample s;
-            tf_lookup(tf_s, p.R, d, s);
+            tf_lookup(tf_s, p.R, d, tfc, s);
             x = G.dt * s.c.w;
-            const float em = expm1f(-x);
+            const float em = neg_expm1_sel(x);
             const float alpha = -em, ea = 1.f + em;
             const float sl_ = s.slope ? Rm1 : 0.f;
             const float wgt = -T * em;               // the forward kernel's roundings
