@@ -476,7 +476,7 @@ def run_ours(args):
     if args.tile_width:
         from paper_2107_12672_b300 import autotune
         autotune.set_tile_width(args.tile_width)
-        tuning = {"width": args.tile_width, "fixed": True}
+        tuning = {"width": args.tile_width, "adjoint_width": args.tile_width, "fixed": True}
     elif not args.no_autotune:
         from paper_2107_12672_b300 import autotune
         tuning = autotune.autotune(wl.scene, wl.eye, wl.w.step_voxels, want=wl.want)

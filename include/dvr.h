@@ -73,7 +73,7 @@
 extern "C" {
 #endif
 
-#define DVR_ABI_VERSION 2
+#define DVR_ABI_VERSION 3
 
 /* exported from the shared library (which hides everything else) */
 #if defined(__GNUC__)
@@ -156,9 +156,20 @@ DVR_API int dvr_abi_version(void);
  * width in {1, 2, 4, 8, 16, 32} (default 8). The shape changes only which
  * rays share a warp (and so the memory access pattern), never the result.
  * The setting is process-wide and read when a launch is issued.
+ *
+ * The forward marches (DVR_PASS_FORWARD: dvr_forward, dvr_forward_tangent)
+ * and the adjoint marches (DVR_PASS_ADJOINT: dvr_backward,
+ * dvr_backward_noalloc) keep separate widths, since their best shapes can
+ * differ. dvr_set_tile_width sets both; dvr_get_tile_width returns the
+ * forward width. An unknown pass or width returns DVR_ERR_ARG (the getter
+ * returns -1 for an unknown pass) and changes nothing.
  */
+#define DVR_PASS_FORWARD 0
+#define DVR_PASS_ADJOINT 1
 DVR_API int dvr_set_tile_width(int32_t width);
 DVR_API int dvr_get_tile_width(void);
+DVR_API int dvr_set_pass_tile_width(int32_t pass, int32_t width);
+DVR_API int dvr_get_pass_tile_width(int32_t pass);
 
 /* Message for the last failing call on this host thread ("" if none). */
 DVR_API const char* dvr_last_error(void);

@@ -1,12 +1,12 @@
 """Autotuner for the ray tiling of the march kernels.
 
 A warp marches a tile of `width x (32 / width)` pixels; which shape touches
-the fewest cache sectors per gather depends on the view direction and the
-volume layout, so the tuner times forward + adjoint passes of the caller's
-own workload for each candidate width and keeps the fastest (the choice
-never changes results: every ray is computed the same way). Choices are
-cached per device and workload signature for the life of the process, and
-optionally in a JSON file.
+the fewest cache sectors per gather depends on the view direction, the
+volume layout and the pass, so the tuner times the forward and the adjoint
+passes of the caller's own workload for each candidate width and keeps the
+fastest width for each pass (the choice never changes results: every ray is
+computed the same way). Choices are cached per device and workload
+signature for the life of the process, and optionally in a JSON file.
 """
 from __future__ import annotations
 
@@ -30,18 +30,25 @@ def signature(scene: Scene, want) -> str:
     return f"{dev}|m{scene.model}|{vols}|{tf}|{views}|{','.join(sorted(want))}"
 
 
-def set_tile_width(width: int) -> None:
-    _abi.check(_abi.load().dvr_set_tile_width(int(width)), "dvr_set_tile_width")
+def set_tile_width(width: int, adjoint: int | None = None) -> None:
+    """Set the forward tile width, and the adjoint's (the same if None)."""
+    lib = _abi.load()
+    _abi.check(lib.dvr_set_pass_tile_width(_abi.DVR_PASS_FORWARD, int(width)), "dvr_set_pass_tile_width")
+    _abi.check(lib.dvr_set_pass_tile_width(_abi.DVR_PASS_ADJOINT, int(width if adjoint is None else adjoint)),
+               "dvr_set_pass_tile_width")
 
 
-def get_tile_width() -> int:
-    return int(_abi.load().dvr_get_tile_width())
+def get_tile_width(adjoint: bool = False) -> int:
+    return int(_abi.load().dvr_get_pass_tile_width(_abi.DVR_PASS_ADJOINT if adjoint else _abi.DVR_PASS_FORWARD))
 
 
 def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 5,
              candidates=CANDIDATES, cache_file: str | None = None) -> dict:
-    """Time forward + adjoint for each tile width, set the fastest, and
-    return {"width": best, "ms": {width: ms}}. Cached per signature."""
+    """Time the forward and the adjoint pass for each tile width (two
+    interleaved rounds, the faster of the two kept), set the fastest width
+    of each pass, and return {"width": forward width, "adjoint_width": ...,
+    "ms": {"forward": {width: ms}, "adjoint": {width: ms}}}. Cached per
+    signature."""
     key = signature(scene, want)
     if key not in _cache and cache_file and os.path.exists(cache_file):
         try:
@@ -49,7 +56,7 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
         except (OSError, ValueError):
             pass
     if key in _cache:
-        set_tile_width(_cache[key]["width"])
+        set_tile_width(_cache[key]["width"], _cache[key]["adjoint_width"])
         return _cache[key]
     dev = scene.volumes[0].device
     image = torch.empty((scene.pixels, scene.channels), device=dev)
@@ -63,27 +70,38 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
     if "eye" in want:
         grads["eye"] = torch.zeros((len(scene.views), 3), device=dev)
     w_want = tuple(grads.keys())
-    times = {}
-    for width in candidates:
-        set_tile_width(width)
 
-        def once():
-            forward(None, None, None, None, eye, step_voxels, scene=scene, image=image, aux=aux)
-            backward(None, None, None, None, eye, step_voxels, aux, seed, scene=scene, grads=grads, want=w_want)
+    def fwd():
+        forward(None, None, None, None, eye, step_voxels, scene=scene, image=image, aux=aux)
 
-        once()
-        torch.cuda.synchronize()
+    def bwd():
+        backward(None, None, None, None, eye, step_voxels, aux, seed, scene=scene, grads=grads, want=w_want)
+
+    def timed(fn):
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
         start.record()
         for _ in range(reps):
-            once()
+            fn()
         end.record()
         torch.cuda.synchronize()
-        times[width] = start.elapsed_time(end) / reps
-    best = min(times, key=times.get)
-    set_tile_width(best)
-    result = {"width": best, "ms": {str(k): round(v, 4) for k, v in times.items()}}
+        return start.elapsed_time(end) / reps
+
+    times = {"forward": {}, "adjoint": {}}
+    for _ in range(2):
+        for width in candidates:
+            set_tile_width(width)
+            fwd()
+            bwd()
+            torch.cuda.synchronize()
+            for name, fn in (("forward", fwd), ("adjoint", bwd)):
+                t = timed(fn)
+                times[name][width] = min(t, times[name].get(width, t))
+    best_f = min(times["forward"], key=times["forward"].get)
+    best_b = min(times["adjoint"], key=times["adjoint"].get)
+    set_tile_width(best_f, best_b)
+    result = {"width": best_f, "adjoint_width": best_b,
+              "ms": {n: {str(k): round(v, 4) for k, v in t.items()} for n, t in times.items()}}
     _cache[key] = result
     if cache_file:
         try:

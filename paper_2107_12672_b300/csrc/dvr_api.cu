@@ -16,8 +16,8 @@ namespace {
 
 thread_local char g_err[512] = "";
 
-// warp tile width in pixels (height 32 / width) used by every launch
-std::atomic<int> g_tile_w{dvr::kTileW};
+// warp tile width in pixels (height 32 / width), per pass (DVR_PASS_*)
+std::atomic<int> g_tile_w[2] = {dvr::kTileW, dvr::kTileW};
 
 int fail(int code, const char* fmt, ...)
 {
@@ -112,7 +112,7 @@ int check_common(const dvr_volume* vols, int nvol, const dvr_tf* tf, int model, 
 }
 
 // Fill the launch parameters for views [v0, v1).
-void pack(dvr::Params& p, const dvr_volume* vols, int nvol, const dvr_tf* tf, const dvr_view* views,
+void pack(dvr::Params& p, int pass, const dvr_volume* vols, int nvol, const dvr_tf* tf, const dvr_view* views,
           int v0, int v1, const float* eye, float step)
 {
     memset(&p, 0, sizeof(p));
@@ -124,7 +124,7 @@ void pack(dvr::Params& p, const dvr_volume* vols, int nvol, const dvr_tf* tf, co
         int m = vols[i].nx > vols[i].ny ? vols[i].nx : vols[i].ny;
         p.vol[i].nmax = vols[i].nz > m ? vols[i].nz : m;
     }
-    const int tw = g_tile_w.load(std::memory_order_relaxed), th = 32 / tw;
+    const int tw = g_tile_w[pass].load(std::memory_order_relaxed), th = 32 / tw;
     p.tile_w = tw;
     p.tile_h = th;
     int tiles = 0;
@@ -160,16 +160,30 @@ extern "C" {
 
 int dvr_abi_version(void) { return DVR_ABI_VERSION; }
 
-int dvr_set_tile_width(int32_t width)
+int dvr_set_pass_tile_width(int32_t pass, int32_t width)
 {
     g_err[0] = 0;
+    if (pass != DVR_PASS_FORWARD && pass != DVR_PASS_ADJOINT)
+        return fail(DVR_ERR_ARG, "pass %d is not DVR_PASS_FORWARD or DVR_PASS_ADJOINT", pass);
     if (width != 1 && width != 2 && width != 4 && width != 8 && width != 16 && width != 32)
         return fail(DVR_ERR_ARG, "tile width %d is not one of 1, 2, 4, 8, 16, 32", width);
-    g_tile_w.store(width, std::memory_order_relaxed);
+    g_tile_w[pass].store(width, std::memory_order_relaxed);
     return DVR_OK;
 }
 
-int dvr_get_tile_width(void) { return g_tile_w.load(std::memory_order_relaxed); }
+int dvr_get_pass_tile_width(int32_t pass)
+{
+    if (pass != DVR_PASS_FORWARD && pass != DVR_PASS_ADJOINT) return -1;
+    return g_tile_w[pass].load(std::memory_order_relaxed);
+}
+
+int dvr_set_tile_width(int32_t width)
+{
+    const int rc = dvr_set_pass_tile_width(DVR_PASS_FORWARD, width);
+    return rc ? rc : dvr_set_pass_tile_width(DVR_PASS_ADJOINT, width);
+}
+
+int dvr_get_tile_width(void) { return dvr_get_pass_tile_width(DVR_PASS_FORWARD); }
 
 const char* dvr_last_error(void) { return g_err; }
 
@@ -189,7 +203,7 @@ int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, 
     dvr::Params p;
     for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
         const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
-        pack(p, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
+        pack(p, DVR_PASS_FORWARD, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
              step_voxels);
         p.image = image;
         p.aux = aux;
@@ -254,12 +268,16 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
     dvr::Params p;
     for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
         const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
-        pack(p, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
+        pack(p, DVR_PASS_ADJOINT, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
              step_voxels);
         p.queue = reinterpret_cast<unsigned*>(static_cast<char*>(workspace)
                                               + (size_t)(v0 / dvr::kMaxViewsPerLaunch) * kQueueStride);
         if (grad_volumes)
-            for (int i = 0; i < n_volumes; ++i) p.vol[i].grad = grad_volumes[i];
+            for (int i = 0; i < n_volumes; ++i) {
+                p.vol[i].grad = grad_volumes[i];
+                const long long bytes = 4ll * volumes[i].nx * volumes[i].ny * volumes[i].nz;
+                p.vol[i].grad_vec = bytes <= dvr::l2_bytes();
+            }
         p.aux = const_cast<float*>(aux);
         p.grad_image = grad_image;
         p.grad_tf = grad_tf;
@@ -289,7 +307,7 @@ int dvr_forward_tangent(const dvr_volume* volumes, int32_t n_volumes, const dvr_
     dvr::Params p;
     for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
         const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
-        pack(p, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
+        pack(p, DVR_PASS_FORWARD, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
              step_voxels);
         p.image = image;
         cudaError_t e = dvr::launch_tangent(p, model, c.dtype, tangent, (cudaStream_t)stream);

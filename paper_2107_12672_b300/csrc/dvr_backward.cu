@@ -57,18 +57,38 @@ struct CellRun {
     float a[8];
 };
 
-__device__ __forceinline__ void cell_run_flush(float* g, uint32_t sy, uint32_t sz, CellRun& r)
+// Adds a to g[i] and b to g[i + 1]. With v16 (g 16-byte aligned and the
+// gradient array no larger than L2), one 16-byte vector reduction on the
+// aligned float4 holding g[i] (zeros in its other words; adding zero changes
+// nothing) carries both, plus a scalar one for b when g[i] is the last word
+// of its float4: about 1.25 L2 atomic operations per pair instead of 2.
+// Measured on B300: 64-view tomography of a 256^3 volume (64 MiB gradient)
+// adjoint 52.3 -> 41.4 ms; but with gradients of 512 MiB and 4 GiB, which
+// live in HBM, 160.7 -> 230.1 ms and 2036 -> 2762 ms, hence the size rule.
+// Near the end of the array (where the float4 would reach past element
+// nvox - 1) both are scalar.
+__device__ __forceinline__ void red_pair(float* g, bool v16, uint32_t i, uint32_t nvox, float a, float b)
+{
+    const uint32_t o = i & 3u;
+    if (v16 && i - o + 4u <= nvox) {
+        const float4 v = make_float4(o == 0u ? a : 0.f, o == 0u ? b : (o == 1u ? a : 0.f),
+                                     o == 1u ? b : (o == 2u ? a : 0.f), o == 2u ? b : (o == 3u ? a : 0.f));
+        atomicAdd(reinterpret_cast<float4*>(g + (i - o)), v);
+        if (o == 3u) atomicAdd(g + i + 1, b);
+    } else {
+        atomicAdd(g + i, a);
+        atomicAdd(g + i + 1, b);
+    }
+}
+
+__device__ __forceinline__ void cell_run_flush(float* g, bool v16, uint32_t nvox, uint32_t sy, uint32_t sz,
+                                               CellRun& r)
 {
     if (r.base != 0xffffffffu) {
-        float* q = g + r.base;
-        atomicAdd(q, r.a[0]);
-        atomicAdd(q + 1, r.a[1]);
-        atomicAdd(q + sy, r.a[2]);
-        atomicAdd(q + sy + 1, r.a[3]);
-        atomicAdd(q + sz, r.a[4]);
-        atomicAdd(q + sz + 1, r.a[5]);
-        atomicAdd(q + sz + sy, r.a[6]);
-        atomicAdd(q + sz + sy + 1, r.a[7]);
+        red_pair(g, v16, r.base, nvox, r.a[0], r.a[1]);
+        red_pair(g, v16, r.base + sy, nvox, r.a[2], r.a[3]);
+        red_pair(g, v16, r.base + sz, nvox, r.a[4], r.a[5]);
+        red_pair(g, v16, r.base + sz + sy, nvox, r.a[6], r.a[7]);
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) r.a[j] = 0.f;
@@ -156,6 +176,8 @@ backward_kernel(const __grid_constant__ Params p)
 #pragma unroll
         for (int j = 0; j < 8; ++j) cr.a[j] = 0.f;
         const uint32_t vsy = (uint32_t)G.n[0], vsz = vsy * (uint32_t)G.n[1];
+        const uint32_t vnvox = vsz * (uint32_t)G.n[2];
+        const bool gv16 = vd.grad_vec && ((uintptr_t)gvol & 15u) == 0;
 
         // software pipeline with same-cell reuse as in the forward march,
         // in reverse order
@@ -258,7 +280,7 @@ backward_kernel(const __grid_constant__ Params p)
             }
             if (GVOL) {
                 if (c.base != cr.base) {
-                    cell_run_flush(gvol, vsy, vsz, cr);
+                    cell_run_flush(gvol, gv16, vnvox, vsy, vsz, cr);
                     cr.base = c.base;
                 }
                 const float a0 = d_hat * (1.f - c.fz), a1 = d_hat * c.fz;
@@ -285,7 +307,7 @@ backward_kernel(const __grid_constant__ Params p)
         }
 
         if (TFM == kTFWarp) tf_run_flush(my_tfg, tr);
-        if (GVOL) cell_run_flush(gvol, vsy, vsz, cr);
+        if (GVOL) cell_run_flush(gvol, gv16, vnvox, vsy, vsz, cr);
 
         if (POS) {
             if (!EA) dt_hat *= expf(-(sh + sl));          // absorption: T_N sum_i A^ d_i

@@ -35,6 +35,7 @@ struct VolumeDesc {
     float* grad;                     // adjoint only, may be null
     int n[3];
     int nmax;
+    int grad_vec;                    // scatter the gradient with 16-byte vector reductions
 };
 
 struct ViewDesc {

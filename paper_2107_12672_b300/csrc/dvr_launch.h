@@ -44,7 +44,9 @@ cudaError_t launch_orbit_eye(const float* params, int n, float* eye, cudaStream_
 cudaError_t launch_orbit_eye_backward(const float* params, const float* grad_eye, int n,
                                       float* grad_params, cudaStream_t stream);
 
-// Number of SMs of the current device (cached per device).
+// Number of SMs and L2 size in bytes of the current device (cached per
+// device; 0 bytes if unknown).
 int sm_count();
+long long l2_bytes();
 
 }  // namespace dvr

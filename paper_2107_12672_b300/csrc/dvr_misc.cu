@@ -17,6 +17,19 @@ int sm_count()
     return cached[dev];
 }
 
+long long l2_bytes()
+{
+    static long long cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (cached[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrL2CacheSize, dev);
+        cached[dev] = n > 0 ? n : -1;
+    }
+    return cached[dev] > 0 ? cached[dev] : 0;
+}
+
 // loss += scale * sum (x - y)^2 ; g = 2 scale (x - y). Grid-stride, float4
 // when the three arrays are 16-byte aligned, block reduction, one atomic
 // per block.

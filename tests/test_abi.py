@@ -148,3 +148,25 @@ def test_no_oracle_in_the_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not banned.search(text), f
+
+
+def test_pass_tile_widths_are_separate_and_checked():
+    """The forward and adjoint tile widths are set apart; dvr_set_tile_width
+    sets both; unknown passes or widths are refused and change nothing. No
+    CUDA call is made."""
+    lib = _abi.load()
+    F, A = _abi.DVR_PASS_FORWARD, _abi.DVR_PASS_ADJOINT
+    old = lib.dvr_get_pass_tile_width(F), lib.dvr_get_pass_tile_width(A)
+    try:
+        assert lib.dvr_set_pass_tile_width(F, 16) == 0 and lib.dvr_set_pass_tile_width(A, 4) == 0
+        assert (lib.dvr_get_pass_tile_width(F), lib.dvr_get_pass_tile_width(A)) == (16, 4)
+        assert lib.dvr_get_tile_width() == 16
+        assert lib.dvr_set_pass_tile_width(2, 8) == -1 and b"pass" in lib.dvr_last_error()
+        assert lib.dvr_set_pass_tile_width(A, 3) == -1 and b"width" in lib.dvr_last_error()
+        assert lib.dvr_get_pass_tile_width(7) == -1
+        assert (lib.dvr_get_pass_tile_width(F), lib.dvr_get_pass_tile_width(A)) == (16, 4)
+        assert lib.dvr_set_tile_width(32) == 0
+        assert (lib.dvr_get_pass_tile_width(F), lib.dvr_get_pass_tile_width(A)) == (32, 32)
+    finally:
+        lib.dvr_set_pass_tile_width(F, old[0])
+        lib.dvr_set_pass_tile_width(A, old[1])

@@ -429,7 +429,7 @@ def test_tile_width_changes_nothing_and_autotuner_picks_one():
     sc = dvr.Scene.make(vols, tf, w.model, w.views)
     G = to_dev(seeded_grad_image(100 * 77, 4, 4))
     ref = None
-    old = autotune.get_tile_width()
+    old, old_adj = autotune.get_tile_width(), autotune.get_tile_width(adjoint=True)
     try:
         for width in (1, 2, 4, 8, 16, 32):
             autotune.set_tile_width(width)
@@ -444,10 +444,20 @@ def test_tile_width_changes_nothing_and_autotuner_picks_one():
             assert torch.equal(cur[0], ref[0]), width
             for a, b in zip(cur[1:], ref[1:]):
                 assert_close(a, b, 1e-5, f"width {width}")
+        # forward and adjoint widths set apart give the same results
+        autotune.set_tile_width(32, 2)
+        img, aux = dvr.forward(None, None, None, None, eye, w.step_voxels, scene=sc)
+        g = dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=sc, want=("volume", "tf", "eye"))
+        torch.cuda.synchronize()
+        assert torch.equal(img.cpu(), ref[0])
+        for a, b in zip((g["volume"][0].cpu().numpy(), g["tf"].cpu().numpy(), g["eye"].cpu().numpy()), ref[1:]):
+            assert_close(a, b, 1e-5, "widths 32 / 2")
         res = autotune.autotune(sc, eye, w.step_voxels, want=("tf", "eye"), reps=2)
         assert res["width"] in autotune.CANDIDATES and autotune.get_tile_width() == res["width"]
+        assert res["adjoint_width"] in autotune.CANDIDATES
+        assert autotune.get_tile_width(adjoint=True) == res["adjoint_width"]
     finally:
-        autotune.set_tile_width(old)
+        autotune.set_tile_width(old, old_adj)
 
 
 # ------------------------------------------------ inversion ablation (Sec. 4.4)
