@@ -14,7 +14,7 @@ template <int MODEL, typename VT>
 __global__ void __launch_bounds__(kWarps * 32, DVR_FWD_MIN_BLOCKS)
 forward_kernel(const __grid_constant__ Params p)
 {
-    __shared__ float4 tf_s[MODEL == DVR_EMISSION_ABSORPTION ? 2 * kMaxTF : 1];
+    extern __shared__ float4 tf_s[];            // 2R float4 (emission-absorption only)
     if (MODEL == DVR_EMISSION_ABSORPTION) {
         stage_tf(p, tf_s);
         __syncthreads();
@@ -112,7 +112,10 @@ static cudaError_t launch(const Params& p, cudaStream_t stream)
 {
     auto k = forward_kernel<MODEL, VT>;
     const int blocks = (p.total_tiles + kWarps - 1) / kWarps;
-    k<<<blocks, kWarps * 32, 0, stream>>>(p);
+    // shared memory holds only this TF, the rest of the SM's 256 KB stays
+    // L1 cache for the gathers
+    const size_t smem = MODEL == DVR_EMISSION_ABSORPTION ? 2 * sizeof(float4) * (size_t)p.R : 0;
+    k<<<blocks, kWarps * 32, smem, stream>>>(p);
     return cudaGetLastError();
 }
 

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
 {
     constexpr bool EA = MODEL == DVR_EMISSION_ABSORPTION;
-    __shared__ float4 tf_s[EA ? 2 * kMaxTF : 1];
+    extern __shared__ float4 tf_s[];            // 2R float4 (emission-absorption only)
     if (EA) {
         stage_tf(p, tf_s);
         __syncthreads();
@@ -247,7 +247,8 @@ contract_kernel(const __grid_constant__ Params p, int channels, const float* __r
 template <int MODEL, typename VT>
 static cudaError_t launch_t(const Params& p, float* tangent, cudaStream_t s)
 {
-    tangent_kernel<MODEL, VT><<<(p.total_tiles + kWarps - 1) / kWarps, kWarps * 32, 0, s>>>(p, tangent);
+    const size_t smem = MODEL == DVR_EMISSION_ABSORPTION ? 2 * sizeof(float4) * (size_t)p.R : 0;
+    tangent_kernel<MODEL, VT><<<(p.total_tiles + kWarps - 1) / kWarps, kWarps * 32, smem, s>>>(p, tangent);
     return cudaGetLastError();
 }
 
