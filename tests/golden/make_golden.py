@@ -2,8 +2,9 @@
 the paper's equations in closed form (Sec. 3.1: the Beer-Lambert segment
 opacity and the Riemann sum of Eq. 1 with front-to-back blending).
 
-Each value is computed here from its formula with Python's `math` (binary64); every input is exact in binary32,
-independently of the oracle and of the CUDA path. Geometry common to every
+Each value is computed here from its formula with Python's `math`
+(binary64), independently of the oracle and of the CUDA path; every input
+is exact in binary32. Geometry common to every
 case: a 33^3 vertex grid spans the unit cube [-1/2, 1/2]^3 (vertex spacing
 h = 1/32); a step of 0.5 voxel is dt = 1/64 world units; a ray along -z that
 enters the top face z = 1/2 crosses L = 1 and takes N = L/dt = 64 samples at
