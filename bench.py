@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default 8x4 ray tiles")
     ap.add_argument("--tile-width", type=int, default=0, help="fix the warp tile width (1..32)")
     ap.add_argument("--no-variants", action="store_true", help="skip the BF16/FP16 storage comparison")
+    ap.add_argument("--eager", action="store_true", help="time eagerly launched steps instead of a CUDA graph")
     return ap.parse_args()
 
 
@@ -223,17 +224,30 @@ class Workload:
         self.image = torch.empty((self.scene.pixels, self.scene.channels), device=device)
         self.aux = torch.empty((self.scene.pixels, 2), device=device)
         self.gimg = torch.empty_like(self.image)
-        self.loss = torch.zeros(1, device=device)
         self.want = tuple({"volume": "volume", "tf": "tf", "camera": "eye"}[g] for g in w.grads)
+        # the loss and the small gradients are views of one buffer, zeroed
+        # with one fill per step (each part starts on a 16-byte boundary)
+        parts = [("loss", (1,))]
+        if "tf" in self.want:
+            parts.append(("tf", (self.tf.shape[0], 4)))
+        if "eye" in self.want:
+            parts.append(("eye", tuple(self.eye.shape)))
+            if self.orbit:
+                parts.append(("par", tuple(self.params.shape)))
+        sizes = [int(np.prod(shape)) for _, shape in parts]
+        offs = np.concatenate([[0], np.cumsum([(n + 3) // 4 * 4 for n in sizes])])
+        self.small = torch.zeros(int(offs[-1]), device=device)
+        views = {name: self.small[o:o + n].view(shape) for (name, shape), o, n in zip(parts, offs, sizes)}
+        self.loss = views["loss"]
         self.grads = {}
         if "volume" in self.want:
             self.grads["volume"] = [torch.zeros(v.shape, device=device) for v in self.vol]
         if "tf" in self.want:
-            self.grads["tf"] = torch.zeros((self.tf.shape[0], 4), device=device)
+            self.grads["tf"] = views["tf"]
         if "eye" in self.want:
-            self.grads["eye"] = torch.zeros_like(self.eye)
+            self.grads["eye"] = views["eye"]
             if self.orbit:
-                self.g_par = torch.zeros_like(self.params)
+                self.g_par = views["par"]
         self.count = torch.zeros(1, dtype=torch.int64, device=device)
         self.tf_immediate = tf_immediate
         # target image: the same views with the second TF or the second volume
@@ -256,12 +270,9 @@ class Workload:
         self.launches_per_step = 3 + (2 if self.orbit else 0)
 
     def zero(self):
-        self.loss.zero_()
-        for k, g in self.grads.items():
-            for t in (g if isinstance(g, list) else [g]):
-                t.zero_()
-        if self.orbit and "eye" in self.want:
-            self.g_par.zero_()
+        self.small.zero_()
+        for t in self.grads.get("volume", []):
+            t.zero_()
 
     def step(self, ev=None):
         """One pass of the path. `ev` = (fwd_start, fwd_end, bwd_start,
@@ -411,6 +422,47 @@ def time_steps(wl, K, W, flush, clocks=None, world=1):
     return step_ms, fwd_ms, bwd_ms, wall, clk
 
 
+def time_steps_graph(wl, K, W, flush, clocks=None, world=1):
+    """The same step captured once as a CUDA graph and replayed: K replays
+    each bracketed by CUDA events (L2 flushed between replays, outside the
+    brackets), after W untimed replays. Returns per-step milliseconds and the
+    wall time of the timed region."""
+    import torch
+    import torch.distributed as dist
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            wl.step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        wl.step()
+    for _ in range(W):
+        graph.replay()
+    torch.cuda.synchronize()
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+        clocks.mark()
+    t0 = time.perf_counter()
+    for k in range(K):
+        flush.zero_()
+        st[k].record()
+        graph.replay()
+        en[k].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop() if clocks is not None else None
+    return float(np.mean([s.elapsed_time(e) for s, e in zip(st, en)])), wall, clk
+
+
 def compare_camera_modes(wl, K, W, flush):
     """Camera gradient alone, two ways (Sec. 5.1): the adjoint (forward pass,
     then the adjoint with only the eye gradient) and forward mode (one
@@ -479,8 +531,14 @@ def run_ours(args):
         tuning = {"width": args.tile_width, "adjoint_width": args.tile_width, "fixed": True}
     elif not args.no_autotune:
         from paper_2107_12672_b300 import autotune
-        tuning = autotune.autotune(wl.scene, wl.eye, wl.w.step_voxels, want=wl.want)
-    step_ms, fwd_ms, bwd_ms, wall, clk = time_steps(wl, K, args.warmup, flush, Clocks(local), world)
+        tuning = autotune.autotune(wl.scene, wl.eye, wl.w.step_voxels, want=wl.want, l2_flush=flush)
+    # per-kernel breakdown from eagerly launched steps; the headline step
+    # time from the same step replayed as one CUDA graph
+    eager_ms, fwd_ms, bwd_ms, _, _ = time_steps(wl, K, args.warmup, flush, None, world)
+    if args.eager:
+        step_ms, _, _, wall, clk = time_steps(wl, K, args.warmup, flush, Clocks(local), world)
+    else:
+        step_ms, wall, clk = time_steps_graph(wl, K, args.warmup, flush, Clocks(local), world)
     if world > 1:
         t = torch.tensor([step_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -519,6 +577,7 @@ def run_ours(args):
         achieved = algorithmic_bytes(wl, dom) / (dur * 1e-3) / 1e9
         cfg = wl.describe()
         cfg.update({"l2": "flushed between timed steps (512 MiB write)",
+                    "launch": "eager launches" if args.eager else "the whole step as one CUDA graph, replayed",
                     "tile": tuning,
                     "tf_accumulation": "immediate" if args.tf_immediate else "delayed (shared memory)",
                     "parallelism": f"replicas x{world}"})
@@ -536,6 +595,7 @@ def run_ours(args):
             "dtype": "f32" if wl.vol[0].dtype == torch.float32 else str(wl.vol[0].dtype).replace("torch.", ""),
             "data": "synthetic (seeded generators; no dataset)",
             "config": cfg,
+            "eager_ms_per_step": round(eager_ms, 4),
             "forward_ms": round(fwd_ms, 4),
             "adjoint_ms": round(bwd_ms, 4),
             "forward_gsamples_s": round(samples / (fwd_ms * 1e-3) / 1e9, 3),

@@ -43,12 +43,15 @@ def get_tile_width(adjoint: bool = False) -> int:
 
 
 def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 5,
-             candidates=CANDIDATES, cache_file: str | None = None) -> dict:
+             candidates=CANDIDATES, cache_file: str | None = None, l2_flush: torch.Tensor | None = None) -> dict:
     """Time the forward and the adjoint pass for each tile width (two
     interleaved rounds, the faster of the two kept), set the fastest width
     of each pass, and return {"width": forward width, "adjoint_width": ...,
     "ms": {"forward": {width: ms}, "adjoint": {width: ms}}}. Cached per
-    signature."""
+    signature. With `l2_flush` (a device buffer larger than L2), the buffer
+    is overwritten before each timed pass, so that the passes start with
+    the volume out of L2 as in a loop that touches other data between
+    steps; each pass is then timed on its own."""
     key = signature(scene, want)
     if key not in _cache and cache_file and os.path.exists(cache_file):
         try:
@@ -78,14 +81,23 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
         backward(None, None, None, None, eye, step_voxels, aux, seed, scene=scene, grads=grads, want=w_want)
 
     def timed(fn):
-        start = torch.cuda.Event(enable_timing=True)
-        end = torch.cuda.Event(enable_timing=True)
-        start.record()
-        for _ in range(reps):
+        if l2_flush is None:
+            start = torch.cuda.Event(enable_timing=True)
+            end = torch.cuda.Event(enable_timing=True)
+            start.record()
+            for _ in range(reps):
+                fn()
+            end.record()
+            torch.cuda.synchronize()
+            return start.elapsed_time(end) / reps
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            l2_flush.zero_()
+            a.record()
             fn()
-        end.record()
+            b.record()
         torch.cuda.synchronize()
-        return start.elapsed_time(end) / reps
+        return sum(a.elapsed_time(b) for a, b in ev) / reps
 
     times = {"forward": {}, "adjoint": {}}
     for _ in range(2):

@@ -456,6 +456,12 @@ def test_tile_width_changes_nothing_and_autotuner_picks_one():
         assert res["width"] in autotune.CANDIDATES and autotune.get_tile_width() == res["width"]
         assert res["adjoint_width"] in autotune.CANDIDATES
         assert autotune.get_tile_width(adjoint=True) == res["adjoint_width"]
+        # timed pass by pass with a buffer overwritten before each
+        autotune._cache.clear()
+        res = autotune.autotune(sc, eye, w.step_voxels, want=("tf", "eye"), reps=2,
+                                l2_flush=torch.empty(1 << 20, dtype=torch.uint8, device="cuda"))
+        assert set(res["ms"]["forward"]) == set(res["ms"]["adjoint"]) == {str(c) for c in autotune.CANDIDATES}
+        assert autotune.get_tile_width(adjoint=True) == res["adjoint_width"]
     finally:
         autotune.set_tile_width(old, old_adj)
 
