@@ -64,25 +64,30 @@ def peaks():
     return 6400.0, "fallback"
 
 
-def kernel_source_hash():
+# the device sources a march kernel is compiled from (its own file, the
+# shared device header and the launch declarations)
+KERNEL_SOURCES = {"forward": ("dvr_forward.cu", "dvr_device.cuh", "dvr_launch.h"),
+                  "backward": ("dvr_backward.cu", "dvr_device.cuh", "dvr_launch.h")}
+
+
+def kernel_source_hash(kernel: str):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2107_12672_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str):
+def profiled_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"ncu_{kernel}.md")
+    the current sources of that kernel."""
+    path = os.path.join(ROOT, "profiles", f"ncu_{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     s = re.search(r"source_hash:\s*([0-9a-f]+)", text)
-    if not m or not s or s.group(1) != kernel_source_hash():
+    if not m or not s or s.group(1) != kernel_source_hash(kernel):
         return None
     return float(m.group(1))
 
@@ -609,7 +614,7 @@ def run_ours(args):
                 "unit": "GB/s",
                 "frac": round(achieved / hbm, 4),
                 "peak_source": src,
-                "traffic": profiled_traffic(f"{dom}_{args.workload}"),
+                "traffic": profiled_traffic(dom, args.workload),
                 "bytes_per_sample": 8 * wl.vol[0].element_size(),
             },
             "accuracy": acc,

@@ -39,6 +39,24 @@ bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 // in groups of kMaxViewsPerLaunch), each on its own 128-byte line.
 constexpr size_t kQueueStride = 128;
 
+// Warp tiles of the largest launch (views are launched in groups of
+// kMaxViewsPerLaunch) at the tile width that gives the most tiles.
+long long max_launch_tiles(const dvr_view* views, int n_views)
+{
+    long long most = 0;
+    for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
+        const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
+        for (int tw = 1; tw <= 32; tw *= 2) {
+            const int th = 32 / tw;
+            long long t = 0;
+            for (int i = v0; i < v1; ++i)
+                t += (long long)((views[i].width + tw - 1) / tw) * ((views[i].height + th - 1) / th);
+            if (t > most) most = t;
+        }
+    }
+    return most;
+}
+
 size_t workspace_bytes(int n_views)
 {
     if (n_views < 1) return 0;
@@ -108,6 +126,9 @@ int check_common(const dvr_volume* vols, int nvol, const dvr_tf* tf, int model, 
         const long long end = w.pixel_offset + (long long)w.width * w.height;
         if (end > c.pixels) c.pixels = end;
     }
+    if (max_launch_tiles(views, nviews) > 0x7fffffffll)
+        return fail(DVR_ERR_ARG, "more than 2^31 - 1 ray tiles in one launch of up to %d views",
+                    dvr::kMaxViewsPerLaunch);
     return DVR_OK;
 }
 

@@ -170,3 +170,23 @@ def test_pass_tile_widths_are_separate_and_checked():
     finally:
         lib.dvr_set_pass_tile_width(F, old[0])
         lib.dvr_set_pass_tile_width(A, old[1])
+
+
+@pytest.mark.parametrize("R", [1, 1025])
+def test_tf_row_count_limits(R):
+    """2 <= R <= 1024 TF rows (the shared-memory staging limit); others are
+    refused before any CUDA call."""
+    lib = _abi.load()
+    tf = _abi.DvrTF(R, 0, 4096)
+    rc = _call_forward(_one_volume(), 1, ctypes.byref(tf), 1, _one_view(), 1)
+    assert rc == -1 and b"TF has" in lib.dvr_last_error()
+
+
+def test_tile_count_overflow_refused():
+    """512 views of 65536^2 pixels in one launch would need more than 2^31 - 1
+    warp tiles: refused on the host."""
+    lib = _abi.load()
+    n = 512
+    views = (_abi.DvrView * n)(*[_abi.DvrView(65536, 65536, 0, 0, 0.4, 0, 65536 * 65536 * i) for i in range(n)])
+    rc = _call_forward(_one_volume(), 1, None, 0, views, n)
+    assert rc == -1 and b"tiles" in lib.dvr_last_error()

@@ -511,3 +511,21 @@ def test_non_cubic_volumes(shape, model):
     gpu = _run_gpu(w, want=want)
     ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
     _compare(w, gpu, ref, want)
+
+
+# ------------------------------------------------------------- TF row counts
+@pytest.mark.parametrize("R", [2, 33, 1024])
+def test_tf_sizes_at_the_limits(R):
+    """The smallest TF (one segment), the first size past the per-lane
+    shared-memory copies (R = 33: per-warp copies with register runs) and the
+    largest (R = 1024 rows staged in shared memory)."""
+    rng = np.random.default_rng(R)
+    vol = rng.uniform(0.02, 0.98, (14, 13, 12)).astype(np.float32)
+    tf = syn.random_tf(R, seed=R, tau_max=20.0)
+    w = syn.Workload("tf_rows", "emission_absorption", [vol], tf, [syn.View(23, 17), syn.View(9, 30)],
+                     np.array([[0.9, 0.5, 1.7], [-1.3, 0.8, -1.1]], dtype=np.float32), None, 0.4,
+                     ("volume", "tf", "camera"))
+    want = ("volume", "tf", "eye")
+    gpu = _run_gpu(w, want=want)
+    ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
+    _compare(w, gpu, ref, want)
