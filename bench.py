@@ -334,6 +334,39 @@ def algorithmic_bytes(wl, kernel):
     return b
 
 
+def probe_ceilings(dev):
+    """On-chip ceilings measured with the library's probes on this device
+    (CUDA events around each; best of 3): L2 read GB/s (a 32 MiB buffer,
+    loads that bypass L1), L1 read GB/s (32 KB per block, 4 blocks per SM)
+    and L2 scattered-reduction throughput (Gops/s, 2^22 words)."""
+    import torch
+    from paper_2107_12672_b300 import _abi
+    lib = _abi.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    sink = torch.zeros(1, device=dev)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    cases = {"l2_read_gbs": (_abi.DVR_PROBE_L2_READ, 32 << 20, 40),
+             "l1_read_gbs": (_abi.DVR_PROBE_L1_READ, 4 * nsm * 32768, 400),
+             "l2_red_gops": (_abi.DVR_PROBE_L2_RED, 16 << 20, 8)}
+    out = {}
+    for name, (kind, nbytes, reps) in cases.items():
+        buf = torch.zeros(nbytes // 4, device=dev)
+        best = None
+        for _ in range(4):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            _abi.check(lib.dvr_probe(kind, buf.data_ptr(), nbytes, reps, sink.data_ptr(), stream), "dvr_probe")
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) * 1e-3
+            best = t if best is None else min(best, t)
+        work = nbytes * reps if name != "l2_red_gops" else (nbytes // 4) * reps
+        out[name] = round(work / best / 1e9, 1)
+        del buf
+    return out
+
+
 def accuracy(wl):
     """Errors of one forward + adjoint against the FP64 oracle on identical
     inputs (the workload's seeded eye positions; volume and TF as stored on
@@ -581,6 +614,17 @@ def run_ours(args):
         dom = "backward" if bwd_ms >= fwd_ms else "forward"
         dur = bwd_ms if dom == "backward" else fwd_ms
         achieved = algorithmic_bytes(wl, dom) / (dur * 1e-3) / 1e9
+        ceil = probe_ceilings(dev)
+        levels = {"l2_read": {"peak": ceil["l2_read_gbs"], "unit": "GB/s",
+                              "frac": round(achieved / ceil["l2_read_gbs"], 4)},
+                  "l1_read": {"peak": ceil["l1_read_gbs"], "unit": "GB/s",
+                              "frac": round(achieved / ceil["l1_read_gbs"], 4)},
+                  "peak_source": "measured in this run with dvr_probe"}
+        if dom == "backward" and "volume" in wl.want:
+            # the density-gradient scatter: 8 corner additions per sample
+            ops = wl.samples_per_pass * 8 / (dur * 1e-3) / 1e9
+            levels["l2_red"] = {"achieved": round(ops, 2), "peak": ceil["l2_red_gops"], "unit": "Gops/s",
+                                "frac": round(ops / ceil["l2_red_gops"], 4)}
         cfg = wl.describe()
         cfg.update({"l2": "flushed between timed steps (512 MiB write)",
                     "launch": "eager launches" if args.eager else "the whole step as one CUDA graph, replayed",
@@ -617,6 +661,7 @@ def run_ours(args):
                 "peak_source": src,
                 "traffic": profiled_traffic(dom, args.workload),
                 "bytes_per_sample": 8 * wl.vol[0].element_size(),
+                "levels": levels,
             },
             "accuracy": acc,
             "storage_variants": variants,

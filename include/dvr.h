@@ -73,7 +73,7 @@
 extern "C" {
 #endif
 
-#define DVR_ABI_VERSION 3
+#define DVR_ABI_VERSION 4
 
 /* exported from the shared library (which hides everything else) */
 #if defined(__GNUC__)
@@ -170,6 +170,38 @@ DVR_API int dvr_set_tile_width(int32_t width);
 DVR_API int dvr_get_tile_width(void);
 DVR_API int dvr_set_pass_tile_width(int32_t pass, int32_t width);
 DVR_API int dvr_get_pass_tile_width(int32_t pass);
+
+/*
+ * Bandwidth probes for the roofline of the march kernels (a measurement
+ * utility; the paper has no counterpart). The volume of a march is read
+ * once from DRAM and then served from L2 and L1, so these kernels measure
+ * the on-chip ceilings on the running device; time the call with events on
+ * `stream`.
+ *
+ * kind      DVR_PROBE_L2_READ: every SM streams [buffer, buffer + bytes)
+ *           with 16-byte loads that bypass L1, `reps` times (bytes moved:
+ *           bytes * reps; choose bytes well below the L2 size);
+ *           DVR_PROBE_L1_READ: each of bytes / 32768 blocks re-reads its own
+ *           32 KB slice through L1, `reps` times (bytes moved:
+ *           (bytes / 32768) * 32768 * reps);
+ *           DVR_PROBE_L2_RED: red.global.add.f32 of 1.0 to the bytes / 4
+ *           words, each word `reps` times, in an order that puts the lanes
+ *           of a warp on different 32-byte sectors (operations:
+ *           (bytes / 4) * reps; with bytes / 4 a power of two every word
+ *           ends up increased by exactly `reps`)
+ * buffer    device memory of `bytes` bytes, 16-byte aligned, caller-owned;
+ *           only DVR_PROBE_L2_RED writes it
+ * bytes     32768 <= bytes < 2^33, a multiple of 16
+ * reps      1 <= reps <= 1000000
+ * sink      device float[1]; written only in a case that never occurs
+ *           (it keeps the probe's loads alive)
+ * Errors: DVR_ERR_ARG for an unknown kind or invalid sizes or pointers,
+ * DVR_ERR_CUDA if the launch fails.
+ */
+#define DVR_PROBE_L2_READ 0
+#define DVR_PROBE_L1_READ 1
+#define DVR_PROBE_L2_RED 2
+DVR_API int dvr_probe(int32_t kind, void* buffer, size_t bytes, int32_t reps, float* sink, void* stream);
 
 /* Message for the last failing call on this host thread ("" if none). */
 DVR_API const char* dvr_last_error(void);

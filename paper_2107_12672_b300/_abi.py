@@ -15,11 +15,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # kernel variants); by default the in-tree build is loaded.
 LIB_PATH = os.environ.get("DVR_LIBRARY") or os.path.join(_HERE, "_lib", "libdvr.so")
 
-ABI_VERSION = 3          # DVR_ABI_VERSION of the header these argtypes follow
+ABI_VERSION = 4          # DVR_ABI_VERSION of the header these argtypes follow
 DVR_OK = 0
 DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
 DVR_ABSORPTION, DVR_EMISSION_ABSORPTION, DVR_COLOR_VOLUME = 0, 1, 2
 DVR_PASS_FORWARD, DVR_PASS_ADJOINT = 0, 1
+DVR_PROBE_L2_READ, DVR_PROBE_L1_READ, DVR_PROBE_L2_RED = 0, 1, 2
 DVR_FLAG_TF_IMMEDIATE = 1
 DVR_FLAG_INVERT_ALPHA32 = 2
 DVR_FLAG_INVERT_ALPHA64 = 4
@@ -29,7 +30,7 @@ SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_set_tile_width", "dvr_get_t
            "dvr_set_pass_tile_width", "dvr_get_pass_tile_width", "dvr_forward", "dvr_backward",
            "dvr_backward_workspace_bytes", "dvr_forward_tangent",
            "dvr_tangent_contract", "dvr_loss_l2", "dvr_loss_l1", "dvr_tf_prior", "dvr_volume_prior",
-           "dvr_resample", "dvr_orbit_eye", "dvr_orbit_eye_backward", "dvr_backward_noalloc")
+           "dvr_resample", "dvr_orbit_eye", "dvr_orbit_eye_backward", "dvr_backward_noalloc", "dvr_probe")
 
 
 class DvrVolume(ctypes.Structure):
@@ -83,6 +84,8 @@ def load() -> ctypes.CDLL:
         lib.dvr_backward_workspace_bytes.restype = ctypes.c_size_t
         lib.dvr_backward_noalloc.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, P, P, U32, P]
         lib.dvr_backward_noalloc.restype = ctypes.c_int
+        lib.dvr_probe.argtypes = [I32, P, ctypes.c_size_t, I32, P, P]
+        lib.dvr_probe.restype = ctypes.c_int
         lib.dvr_forward_tangent.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P]
         lib.dvr_tangent_contract.argtypes = [P, I32, I32, P, P, P, P]
         lib.dvr_loss_l2.argtypes = [P, P, I64, F, P, P, P]

@@ -11,6 +11,7 @@
 
 #include "dvr.h"
 #include "dvr_launch.h"
+#include "dvr_probe.h"
 
 namespace {
 
@@ -207,6 +208,20 @@ int dvr_set_tile_width(int32_t width)
 int dvr_get_tile_width(void) { return dvr_get_pass_tile_width(DVR_PASS_FORWARD); }
 
 const char* dvr_last_error(void) { return g_err; }
+
+int dvr_probe(int32_t kind, void* buffer, size_t bytes, int32_t reps, float* sink, void* stream)
+{
+    g_err[0] = 0;
+    if (kind != DVR_PROBE_L2_READ && kind != DVR_PROBE_L1_READ && kind != DVR_PROBE_L2_RED)
+        return fail(DVR_ERR_ARG, "probe kind %d is not DVR_PROBE_L2_READ, DVR_PROBE_L1_READ or DVR_PROBE_L2_RED", kind);
+    if (!buffer || !aligned(buffer, 16)) return fail(DVR_ERR_ARG, "probe buffer is NULL or not 16-byte aligned");
+    if (!sink || !aligned(sink, 4)) return fail(DVR_ERR_ARG, "probe sink is NULL or misaligned");
+    if (bytes < 32768 || bytes >= (1ull << 33) || bytes % 16)
+        return fail(DVR_ERR_ARG, "probe of %zu bytes: 32768 <= bytes < 2^33, a multiple of 16", bytes);
+    if (reps < 1 || reps > 1000000) return fail(DVR_ERR_ARG, "probe reps %d outside [1, 1000000]", reps);
+    cudaError_t e = dvr::launch_probe(kind, buffer, bytes, reps, sink, (cudaStream_t)stream);
+    return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_probe launch");
+}
 
 size_t dvr_backward_workspace_bytes(int32_t n_views) { return workspace_bytes(n_views); }
 

@@ -190,3 +190,14 @@ def test_tile_count_overflow_refused():
     views = (_abi.DvrView * n)(*[_abi.DvrView(65536, 65536, 0, 0, 0.4, 0, 65536 * 65536 * i) for i in range(n)])
     rc = _call_forward(_one_volume(), 1, None, 0, views, n)
     assert rc == -1 and b"tiles" in lib.dvr_last_error()
+
+
+@pytest.mark.parametrize("kind,buf,nbytes,reps", [(3, 4096, 1 << 20, 1), (0, None, 1 << 20, 1), (0, 4104, 1 << 20, 1),
+                                                  (1, 4096, 1024, 1), (2, 4096, 1 << 20, 0), (0, 4096, (1 << 20) + 4, 1)])
+def test_probe_argument_errors(kind, buf, nbytes, reps):
+    """dvr_probe refuses unknown kinds, NULL or misaligned buffers, sizes
+    outside [32768, 2^33) or not multiples of 16, and reps < 1, before any
+    CUDA call."""
+    lib = _abi.load()
+    assert lib.dvr_probe(kind, buf, nbytes, reps, 8192, None) == -1
+    assert lib.dvr_last_error()

@@ -534,3 +534,23 @@ def test_tf_sizes_at_the_limits(R):
     gpu = _run_gpu(w, want=want)
     ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
     _compare(w, gpu, ref, want)
+
+
+# ------------------------------------------------------------------ probes
+def test_bandwidth_probes_run_and_count():
+    """The roofline probes run; the reduction probe adds exactly `reps` to
+    every word of a power-of-two buffer (its scattered order is a
+    permutation of the words)."""
+    from paper_2107_12672_b300 import _abi
+    lib = _abi.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    sink = torch.zeros(1, device="cuda")
+    buf = torch.zeros(1 << 20, device="cuda")            # 4 MiB, 2^20 words
+    _abi.check(lib.dvr_probe(_abi.DVR_PROBE_L2_RED, buf.data_ptr(), buf.numel() * 4, 3, sink.data_ptr(), stream),
+               "dvr_probe")
+    torch.cuda.synchronize()
+    assert torch.equal(buf, torch.full_like(buf, 3.0))
+    for kind in (_abi.DVR_PROBE_L2_READ, _abi.DVR_PROBE_L1_READ):
+        _abi.check(lib.dvr_probe(kind, buf.data_ptr(), buf.numel() * 4, 2, sink.data_ptr(), stream), "dvr_probe")
+    torch.cuda.synchronize()
+    assert float(sink.item()) == 0.0
