@@ -73,7 +73,7 @@
 extern "C" {
 #endif
 
-#define DVR_ABI_VERSION 4
+#define DVR_ABI_VERSION 5
 
 /* exported from the shared library (which hides everything else) */
 #if defined(__GNUC__)
@@ -222,12 +222,44 @@ DVR_API const char* dvr_last_error(void);
  *                      hi + lo of two floats; dvr_backward needs it
  * sample_count         device uint64[1] or NULL: the total number of
  *                      samples taken is ADDED to it
- * Errors: DVR_ERR_ARG for null/invalid descriptors or sizes, DVR_ERR_DTYPE
- * for unsupported dtypes, DVR_ERR_CUDA if the launch fails.
+ * tile_order           device uint32[tile_order_len] or NULL: the order in
+ *                      which the warps take the ray tiles, as written by
+ *                      dvr_tile_order for these views and the forward tile
+ *                      width in force; NULL takes them in a fixed order. The
+ *                      results do not depend on the order (each ray is
+ *                      computed the same way); the time does. Entries must
+ *                      be a permutation: entries out of range are skipped
+ *                      (never an out-of-bounds access), repeated ones render
+ *                      a tile twice
+ * tile_order_len       its length (ignored with NULL)
+ * Errors: DVR_ERR_ARG for null/invalid descriptors or sizes (or a
+ * tile_order whose length does not match the views' tiles at the current
+ * width), DVR_ERR_DTYPE for unsupported dtypes, DVR_ERR_CUDA if the launch
+ * fails.
  */
 DVR_API int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                 const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
-                float* image, float* aux, unsigned long long* sample_count, void* stream);
+                float* image, float* aux, unsigned long long* sample_count, const uint32_t* tile_order,
+                int64_t tile_order_len, void* stream);
+
+/*
+ * Tile order for dvr_forward / dvr_backward (host function, no CUDA call).
+ * Within each launch of up to 512 views, view by view, the view's ray tiles
+ * sorted by the distance of the tile centre from the view centre (ties in
+ * the fixed order): the long rays through the middle of the volume start
+ * first, and tiles taken at the same time lie side by side. Measured on
+ * B300 against the fixed row order: the adjoint of a 512 x 512 view of a
+ * 256^3 volume 4% faster; the forward not faster there and 3% slower on 64
+ * views of uneven sizes. Depends only on the view sizes and the tile width of
+ * `pass` now in force (make it again after dvr_set_tile_width).
+ *
+ * order     host uint32[capacity] or NULL
+ * Returns the number of entries (the tiles of all launches); writes them
+ * only if order is not NULL and capacity is at least that. A negative
+ * DVR_ERR_ARG for an unknown pass or invalid views.
+ */
+DVR_API int64_t dvr_tile_order(const dvr_view* views, int32_t n_views, int32_t pass, uint32_t* order,
+                               int64_t capacity);
 
 /*
  * Adjoint pass: Alg. 2 for every pixel of every view (one launch). Each
@@ -247,6 +279,8 @@ DVR_API int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_
  * aux                  device float[P][2] written by dvr_forward
  * grad_image           device float[P][C]: dL/d(image)
  * flags                bitwise OR of DVR_FLAG_*
+ * tile_order, tile_order_len
+ *                      as for dvr_forward, made for the adjoint tile width
  * workspace            device scratch of at least
  *                      dvr_backward_workspace_bytes(n_views) bytes, 16-byte
  *                      aligned, owned by the caller. The call zeroes it on
@@ -264,6 +298,7 @@ DVR_API int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr
                  const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
                  const float* aux, const float* grad_image, float* const* grad_volumes,
                  float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags,
+                 const uint32_t* tile_order, int64_t tile_order_len,
                  void* workspace, size_t workspace_bytes, void* stream);
 
 /* Bytes of device workspace a dvr_backward call over n_views views needs
@@ -352,7 +387,8 @@ DVR_API int dvr_orbit_eye_backward(const float* params, const float* grad_eye, i
  * device. Such callers cannot provide the workspace dvr_backward asks for.
  *
  * Arguments, results and errors are those of dvr_backward without
- * `workspace` and `workspace_bytes`. The tile-queue counters live instead in
+ * `tile_order`, `tile_order_len`, `workspace` and `workspace_bytes` (the
+ * tiles go in the fixed order). The tile-queue counters live instead in
  * a fixed 256-byte array in the library's device memory (each GPU that
  * loads the library holds it until the process exits), so one call covers
  * at most 1024 views; larger calls return DVR_ERR_ARG and launch nothing.

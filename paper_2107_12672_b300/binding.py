@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import _abi
@@ -104,6 +105,26 @@ class Scene:
     def tf_ref(self):
         return ctypes.byref(self.tf_desc) if self.tf_desc is not None else None
 
+    def tile_order(self, lib, adjoint: bool):
+        """(device uint32 tensor, length) of the centre-out tile order for
+        the tile width now in force for the pass (dvr_tile_order), made
+        once per scene and width."""
+        pass_ = _abi.DVR_PASS_ADJOINT if adjoint else _abi.DVR_PASS_FORWARD
+        width = int(lib.dvr_get_pass_tile_width(pass_))
+        cache = self.__dict__.setdefault("_orders", {})
+        key = (pass_, width)
+        if key not in cache:
+            n = int(lib.dvr_tile_order(self.view_desc, len(self.views), pass_, None, 0))
+            if n < 0:
+                raise _abi.DVRError(f"dvr_tile_order: {lib.dvr_last_error().decode()}")
+            host = np.empty(n, dtype=np.uint32)
+            got = int(lib.dvr_tile_order(self.view_desc, len(self.views), pass_, host.ctypes.data, n))
+            if got != n:
+                raise _abi.DVRError(f"dvr_tile_order: {lib.dvr_last_error().decode()}")
+            dev = torch.from_numpy(host.view(np.int32)).to(self.volumes[0].device)
+            cache[key] = (dev, n)
+        return cache[key]
+
     def workspace(self, lib, stream=None) -> torch.Tensor:
         """Fresh adjoint workspace (tile-queue counters) from the caching
         allocator, tied to the stream the call runs on."""
@@ -126,9 +147,11 @@ def forward(volumes, tf, model, views, eye, step_voxels, *, scene: Scene | None 
         image = torch.empty((sc.pixels, sc.channels), device=dev, dtype=torch.float32)
     if aux is None:
         aux = torch.empty((sc.pixels, 2), device=dev, dtype=torch.float32)
+    # the forward keeps the fixed tile order: the centre-out order measured no
+    # faster on one 512^2 view and 3% slower on 64 uneven views (B300)
     rc = _abi.load().dvr_forward(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
                                  len(sc.views), _ptr(eye), float(step_voxels), _ptr(image), _ptr(aux),
-                                 _ptr(sample_count), _stream_ptr(stream))
+                                 _ptr(sample_count), None, 0, _stream_ptr(stream))
     _abi.check(rc, "dvr_forward")
     return image, aux
 
@@ -159,10 +182,14 @@ def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, wa
     flags |= {"depth": 0, "alpha32": _abi.DVR_FLAG_INVERT_ALPHA32, "alpha64": _abi.DVR_FLAG_INVERT_ALPHA64}[inversion]
     lib = _abi.load()
     ws = sc.workspace(lib, stream)
+    # centre-out tile order: adjoint 0.365 -> 0.351 ms on a 512^2 view of a
+    # 256^3 volume (B300), neutral on 64 uneven views
+    order, n_order = sc.tile_order(lib, adjoint=True)
     rc = lib.dvr_backward(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
                           len(sc.views), _ptr(eye), float(step_voxels), _ptr(aux),
                           _ptr(grad_image), gv, _ptr(g.get("tf")), _ptr(g.get("eye")),
-                          _ptr(g.get("step")), flags, _ptr(ws), ws.numel(), _stream_ptr(stream))
+                          _ptr(g.get("step")), flags, _ptr(order), n_order, _ptr(ws), ws.numel(),
+                          _stream_ptr(stream))
     _abi.check(rc, "dvr_backward")
     return g
 

@@ -5,9 +5,12 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "dvr.h"
 #include "dvr_launch.h"
@@ -176,6 +179,37 @@ void pack(dvr::Params& p, int pass, const dvr_volume* vols, int nvol, const dvr_
     }
 }
 
+// Centre-out rank -> index, as the kernels' tile_pixel maps tiles.
+int center_out_host(int r, int n)
+{
+    const int c = (n - 1) >> 1;
+    const int k = (r + 1) >> 1;
+    return (r & 1) ? c + k : c - k;
+}
+
+// Tiles of all launches of a call over `views` at the pass's tile width.
+long long pass_tiles(const dvr_view* views, int n_views, int pass)
+{
+    const int tw = g_tile_w[pass].load(std::memory_order_relaxed), th = 32 / tw;
+    long long t = 0;
+    for (int i = 0; i < n_views; ++i)
+        t += (long long)((views[i].width + tw - 1) / tw) * ((views[i].height + th - 1) / th);
+    return t;
+}
+
+// Check a caller's tile order against the views and the pass's tile width.
+int check_order(const uint32_t* order, long long len, const dvr_view* views, int n_views, int pass,
+                const char* who)
+{
+    if (!order) return DVR_OK;
+    if (!aligned(order, 4)) return fail(DVR_ERR_ARG, "%s: tile_order is not 4-byte aligned", who);
+    const long long need = pass_tiles(views, n_views, pass);
+    if (len != need)
+        return fail(DVR_ERR_ARG, "%s: tile_order has %lld entries, these views have %lld tiles at tile width %d "
+                    "(made for other views or another width?)", who, len, need, g_tile_w[pass].load());
+    return DVR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -225,22 +259,74 @@ int dvr_probe(int32_t kind, void* buffer, size_t bytes, int32_t reps, float* sin
 
 size_t dvr_backward_workspace_bytes(int32_t n_views) { return workspace_bytes(n_views); }
 
+int64_t dvr_tile_order(const dvr_view* views, int32_t n_views, int32_t pass, uint32_t* order, int64_t capacity)
+{
+    g_err[0] = 0;
+    if (pass != DVR_PASS_FORWARD && pass != DVR_PASS_ADJOINT)
+        return fail(DVR_ERR_ARG, "pass %d is not DVR_PASS_FORWARD or DVR_PASS_ADJOINT", pass);
+    if (!views || n_views < 1 || n_views > 4096)
+        return fail(DVR_ERR_ARG, "n_views %d outside [1, 4096] or views is NULL", n_views);
+    for (int i = 0; i < n_views; ++i)
+        if (views[i].width < 1 || views[i].height < 1 || views[i].width > 65536 || views[i].height > 65536)
+            return fail(DVR_ERR_ARG, "view %d: size %d x %d outside [1, 65536]", i, views[i].width, views[i].height);
+    if (max_launch_tiles(views, n_views) > 0x7fffffffll)
+        return fail(DVR_ERR_ARG, "more than 2^31 - 1 ray tiles in one launch of up to %d views",
+                    dvr::kMaxViewsPerLaunch);
+    const long long total = pass_tiles(views, n_views, pass);
+    if (!order || capacity < total) return total;
+    const int tw = g_tile_w[pass].load(std::memory_order_relaxed), th = 32 / tw;
+    std::vector<std::pair<long long, uint32_t>> key;
+    long long out = 0;
+    for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
+        const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
+        uint32_t start = 0;                      // first tile of the view within its launch
+        for (int i = v0; i < v1; ++i) {
+            const int W = views[i].width, H = views[i].height;
+            const int tx_n = (W + tw - 1) / tw, ty_n = (H + th - 1) / th;
+            const uint32_t n = (uint32_t)tx_n * (uint32_t)ty_n;
+            key.resize(n);
+            for (uint32_t l = 0; l < n; ++l) {
+                const long long tx = center_out_host((int)(l % (uint32_t)tx_n), tx_n);
+                const long long ty = center_out_host((int)(l / (uint32_t)tx_n), ty_n);
+                // twice the offset of the tile centre from the view centre, in pixels
+                const long long dx = 2 * tx * tw + tw - W, dy = 2 * ty * th + th - H;
+                key[l] = {dx * dx + dy * dy, start + l};
+            }
+            std::stable_sort(key.begin(), key.end(),
+                             [](const std::pair<long long, uint32_t>& a, const std::pair<long long, uint32_t>& b) {
+                                 return a.first < b.first;
+                             });
+            for (uint32_t l = 0; l < n; ++l) order[out++] = key[l].second;
+            start += n;
+        }
+    }
+    return total;
+}
+
 int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                 const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
-                float* image, float* aux, unsigned long long* sample_count, void* stream)
+                float* image, float* aux, unsigned long long* sample_count, const uint32_t* tile_order,
+                int64_t tile_order_len, void* stream)
 {
     g_err[0] = 0;
     Common c;
     int rc = check_common(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, c);
     if (rc) return rc;
+    rc = check_order(tile_order, tile_order_len, views, n_views, DVR_PASS_FORWARD, "dvr_forward");
+    if (rc) return rc;
     if (!image) return fail(DVR_ERR_ARG, "image is NULL");
     if (!aligned(image, c.channels == 4 ? 16 : 4)) return fail(DVR_ERR_ARG, "image is not 16-byte aligned");
     if (aux && !aligned(aux, 8)) return fail(DVR_ERR_ARG, "aux is not 8-byte aligned");
     dvr::Params p;
+    long long order_off = 0;
     for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
         const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
         pack(p, DVR_PASS_FORWARD, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
              step_voxels);
+        if (tile_order) {
+            p.order = tile_order + order_off;
+            order_off += p.total_tiles;
+        }
         p.image = image;
         p.aux = aux;
         p.sample_count = sample_count;
@@ -254,8 +340,8 @@ int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, 
 int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                  const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
                  const float* aux, const float* grad_image, float* const* grad_volumes,
-                 float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags,
-                 void* workspace, size_t workspace_bytes_, void* stream)
+                 float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags, const uint32_t* tile_order,
+                 int64_t tile_order_len, void* workspace, size_t workspace_bytes_, void* stream)
 {
     g_err[0] = 0;
     if (flags & ~(DVR_FLAG_TF_IMMEDIATE | DVR_FLAG_INVERT_ALPHA32 | DVR_FLAG_INVERT_ALPHA64))
@@ -271,6 +357,8 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
                                   (flags & DVR_FLAG_TF_IMMEDIATE)))
         return fail(DVR_ERR_UNSUPPORTED, "inversion ablations: emission-absorption, FP32 volume, delayed TF "
                     "gradient only");
+    rc = check_order(tile_order, tile_order_len, views, n_views, DVR_PASS_ADJOINT, "dvr_backward");
+    if (rc) return rc;
     if (!aux || !grad_image) return fail(DVR_ERR_ARG, "aux and grad_image are required");
     if (!aligned(aux, 8)) return fail(DVR_ERR_ARG, "aux is not 8-byte aligned");
     if (!aligned(grad_image, c.channels == 4 ? 16 : 4))
@@ -302,12 +390,17 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
     cudaError_t e0 = cudaMemsetAsync(workspace, 0, ws, (cudaStream_t)stream);
     if (e0 != cudaSuccess) return cuda_fail(e0, "dvr_backward workspace");
     dvr::Params p;
+    long long order_off = 0;
     for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
         const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
         pack(p, DVR_PASS_ADJOINT, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
              step_voxels);
         p.queue = reinterpret_cast<unsigned*>(static_cast<char*>(workspace)
                                               + (size_t)(v0 / dvr::kMaxViewsPerLaunch) * kQueueStride);
+        if (tile_order) {
+            p.order = tile_order + order_off;
+            order_off += p.total_tiles;
+        }
         if (grad_volumes)
             for (int i = 0; i < n_volumes; ++i) {
                 p.vol[i].grad = grad_volumes[i];
@@ -513,6 +606,6 @@ extern "C" int dvr_backward_noalloc(const dvr_volume* volumes, int32_t n_volumes
     if (rc) return rc;
     // dvr_backward zeroes the counters on `stream` before it launches
     return dvr_backward(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, aux, grad_image,
-                        grad_volumes, grad_tf, grad_eye, grad_step, flags, scratch, kNoallocScratchBytes,
-                        stream);
+                        grad_volumes, grad_tf, grad_eye, grad_step, flags, nullptr, 0, scratch,
+                        kNoallocScratchBytes, stream);
 }

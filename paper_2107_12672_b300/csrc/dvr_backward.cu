@@ -124,8 +124,10 @@ backward_kernel(const __grid_constant__ Params p)
     // (GVOL) keep one tile per warp (measured faster there: with the queue a
     // block's warps no longer march neighbouring tiles together)
     constexpr bool QUEUE = !GVOL;
-    for (int tile = QUEUE ? next_tile(p.queue, lane) : blockIdx.x * kWarps + warp; tile < p.total_tiles;
-         tile = QUEUE ? next_tile(p.queue, lane) : p.total_tiles) {
+    for (int rank = QUEUE ? next_tile(p.queue, lane) : blockIdx.x * kWarps + warp; rank < p.total_tiles;
+         rank = QUEUE ? next_tile(p.queue, lane) : p.total_tiles) {
+        const int tile = tile_at(p, rank);
+        if (tile < 0) continue;                 // warp-uniform
         const int v = find_view(p, tile);
         const ViewDesc& vw = p.view[v];
         int px, py;

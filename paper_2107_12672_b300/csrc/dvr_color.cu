@@ -110,9 +110,9 @@ forward_color_kernel(const __grid_constant__ Params p)
 {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int tile = blockIdx.x * kWarps + warp;
+    const int tile = blockIdx.x * kWarps + warp < p.total_tiles ? tile_at(p, blockIdx.x * kWarps + warp) : -1;
     unsigned long long taken = 0;
-    if (tile < p.total_tiles) {
+    if (tile >= 0) {
         const int v = find_view(p, tile);
         const ViewDesc& vw = p.view[v];
         int px, py;
@@ -172,8 +172,8 @@ backward_color_kernel(const __grid_constant__ Params p)
 {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int tile = blockIdx.x * kWarps + warp;
-    if (tile >= p.total_tiles) return;          // no block-wide synchronisation below
+    const int tile = blockIdx.x * kWarps + warp < p.total_tiles ? tile_at(p, blockIdx.x * kWarps + warp) : -1;
+    if (tile < 0) return;                       // no block-wide synchronisation below
     const int v = find_view(p, tile);
     const ViewDesc& vw = p.view[v];
     int px, py;

@@ -66,6 +66,7 @@ struct Params {
     float* grad_step;
     unsigned long long* sample_count;
     unsigned* queue;                 // adjoint tile queue: a counter zeroed before the launch
+    const unsigned* order;           // tile taken at each rank of the launch, or null: rank order
 };
 
 // ---------------------------------------------------------------- storage
@@ -501,6 +502,16 @@ __device__ __forceinline__ int next_tile(unsigned* queue, int lane)
     unsigned t = 0;
     if (lane == 0) t = atomicAdd(queue, 1u);
     return (int)__shfl_sync(0xffffffffu, t, 0);
+}
+
+// Tile handed out at position `rank` of a launch: the caller's order when
+// there is one (dvr_tile_order), else rank order; -1 for an entry outside
+// the launch's tiles, which the kernels skip.
+__device__ __forceinline__ int tile_at(const Params& p, int rank)
+{
+    if (!p.order) return rank;
+    const unsigned t = __ldg(p.order + rank);
+    return t < (unsigned)p.total_tiles ? (int)t : -1;
 }
 
 // Warp tile -> (view, pixel) mapping.

@@ -23,7 +23,9 @@ forward_kernel(const __grid_constant__ Params p)
     const int warp = threadIdx.x >> 5;
     unsigned long long taken = 0;
 
-    for (int tile = blockIdx.x * kWarps + warp; tile < p.total_tiles; tile += gridDim.x * kWarps) {
+    for (int rank = blockIdx.x * kWarps + warp; rank < p.total_tiles; rank += gridDim.x * kWarps) {
+        const int tile = tile_at(p, rank);
+        if (tile < 0) continue;                 // warp-uniform
         const int v = find_view(p, tile);
         const ViewDesc& vw = p.view[v];
         int px, py;

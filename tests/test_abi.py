@@ -59,7 +59,7 @@ def test_struct_layout_matches_header(tmp_path):
 
 def _call_forward(vols, nvol, tf, model, views, nviews, eye=1, step=0.5, image=16):
     lib = _abi.load()
-    return lib.dvr_forward(vols, nvol, tf, model, views, nviews, eye, step, image, None, None, None)
+    return lib.dvr_forward(vols, nvol, tf, model, views, nviews, eye, step, image, None, None, None, 0, None)
 
 
 def _one_volume(nx=8, dtype=_abi.DVR_F32, data=4096):
@@ -118,7 +118,7 @@ def test_argument_errors_need_no_gpu(case, code):
 def _call_backward(workspace=4096, nbytes=256, flags=0):
     lib = _abi.load()
     return lib.dvr_backward(_one_volume(), 1, None, 0, _one_view(), 1, 16, 0.5, 64, 64, None, None,
-                            128, None, flags, workspace, nbytes, None)
+                            128, None, flags, None, 0, workspace, nbytes, None)
 
 
 def test_backward_rejects_unknown_flags():
@@ -201,3 +201,48 @@ def test_probe_argument_errors(kind, buf, nbytes, reps):
     lib = _abi.load()
     assert lib.dvr_probe(kind, buf, nbytes, reps, 8192, None) == -1
     assert lib.dvr_last_error()
+
+
+def test_tile_order_is_a_centre_out_permutation():
+    """dvr_tile_order (host only): a permutation of each launch's tiles,
+    view by view, by non-decreasing distance of the tile centre from the
+    view centre; the size query writes nothing; bad arguments are refused."""
+    import numpy as np
+    lib = _abi.load()
+    old = lib.dvr_get_pass_tile_width(_abi.DVR_PASS_FORWARD)
+    try:
+        lib.dvr_set_pass_tile_width(_abi.DVR_PASS_FORWARD, 8)          # tiles of 8 x 4 pixels
+        views = (_abi.DvrView * 2)(_abi.DvrView(37, 21, 0, 0, 0.4, 0, 0), _abi.DvrView(16, 9, 0, 0, 0.4, 0, 777))
+        n = lib.dvr_tile_order(views, 2, _abi.DVR_PASS_FORWARD, None, 0)
+        t0, t1 = 5 * 6, 2 * 3                                           # ceil(37/8) x ceil(21/4), ceil(16/8) x ceil(9/4)
+        assert n == t0 + t1
+        out = np.zeros(n, dtype=np.uint32)
+        assert lib.dvr_tile_order(views, 2, _abi.DVR_PASS_FORWARD, out.ctypes.data, n - 1) == n
+        assert not out.any()
+        assert lib.dvr_tile_order(views, 2, _abi.DVR_PASS_FORWARD, out.ctypes.data, n) == n
+        assert sorted(out[:t0]) == list(range(t0)) and sorted(out[t0:]) == list(range(t0, n))
+
+        def co(r, k):
+            c = (k - 1) >> 1
+            return c + ((r + 1) >> 1) if r & 1 else c - ((r + 1) >> 1)
+
+        def dist(t, W, H, off):
+            tx_n, ty_n = (W + 7) // 8, (H + 3) // 4
+            l = t - off
+            tx, ty = co(l % tx_n, tx_n), co(l // tx_n, ty_n)
+            return (2 * tx * 8 + 8 - W) ** 2 + (2 * ty * 4 + 4 - H) ** 2
+
+        d0 = [dist(int(t), 37, 21, 0) for t in out[:t0]]
+        d1 = [dist(int(t), 16, 9, t0) for t in out[t0:]]
+        assert d0 == sorted(d0) and d1 == sorted(d1)
+        assert lib.dvr_tile_order(views, 2, 5, None, 0) == -1
+        assert lib.dvr_tile_order(views, 0, _abi.DVR_PASS_FORWARD, None, 0) == -1
+    finally:
+        lib.dvr_set_pass_tile_width(_abi.DVR_PASS_FORWARD, old)
+
+
+def test_forward_refuses_a_tile_order_of_the_wrong_length():
+    lib = _abi.load()
+    n = lib.dvr_tile_order(_one_view(), 1, _abi.DVR_PASS_FORWARD, None, 0)
+    rc = lib.dvr_forward(_one_volume(), 1, None, 0, _one_view(), 1, 16, 0.5, 16, None, None, 4096, n + 1, None)
+    assert rc == -1 and b"tile_order" in lib.dvr_last_error()

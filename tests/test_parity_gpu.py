@@ -554,3 +554,54 @@ def test_bandwidth_probes_run_and_count():
         _abi.check(lib.dvr_probe(kind, buf.data_ptr(), buf.numel() * 4, 2, sink.data_ptr(), stream), "dvr_probe")
     torch.cuda.synchronize()
     assert float(sink.item()) == 0.0
+
+
+# ------------------------------------------------------------ tile order
+@pytest.mark.parametrize("width", [1, 8, 32])
+def test_tile_order_changes_nothing(width):
+    """With the centre-out tile order of dvr_tile_order, dvr_forward writes
+    every pixel of a NaN-filled image, counts the same samples (a tile taken
+    twice would count twice) and gives the same bits as the fixed order; the
+    adjoint's gradients agree up to the order of atomic additions."""
+    import ctypes
+    from paper_2107_12672_b300 import _abi, autotune
+    w = syn.workload("ea_256", scale=0.125)
+    views = [syn.View(37, 29), syn.View(1, 1), syn.View(64, 3), syn.View(3, 64), syn.View(50, 50)]
+    eye = to_dev(2.5 * syn.fibonacci_sphere(9)[:len(views)])
+    vol, tf = to_dev(w.volumes[0]), to_dev(w.tf)
+    sc = dvr.Scene.make([vol], tf, w.model, views)
+    lib = _abi.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    old = autotune.get_tile_width(), autotune.get_tile_width(adjoint=True)
+    out = []
+    try:
+        autotune.set_tile_width(width)
+        for use_order in (False, True):
+            order, n = sc.tile_order(lib, adjoint=False) if use_order else (None, 0)
+            img = torch.full((sc.pixels, 4), float("nan"), device="cuda")
+            aux = torch.full((sc.pixels, 2), float("nan"), device="cuda")
+            count = torch.zeros(1, dtype=torch.int64, device="cuda")
+            rc = lib.dvr_forward(sc.vol_desc, 1, sc.tf_ref(), sc.model, sc.view_desc, len(views), eye.data_ptr(),
+                                 ctypes.c_float(w.step_voxels), img.data_ptr(), aux.data_ptr(), count.data_ptr(),
+                                 None if order is None else order.data_ptr(), n, stream)
+            _abi.check(rc, "dvr_forward")
+            G = to_dev(seeded_grad_image(sc.pixels, 4, 3))
+            ordered, n_b = sc.tile_order(lib, adjoint=True) if use_order else (None, 0)
+            grads = {"tf": torch.zeros((w.tf.shape[0], 4), device="cuda"), "eye": torch.zeros((len(views), 3), device="cuda")}
+            ws = sc.workspace(lib)
+            rc = lib.dvr_backward(sc.vol_desc, 1, sc.tf_ref(), sc.model, sc.view_desc, len(views), eye.data_ptr(),
+                                  ctypes.c_float(w.step_voxels), aux.data_ptr(), G.data_ptr(), None,
+                                  grads["tf"].data_ptr(), grads["eye"].data_ptr(), None, 0,
+                                  None if ordered is None else ordered.data_ptr(), n_b, ws.data_ptr(), ws.numel(),
+                                  stream)
+            _abi.check(rc, "dvr_backward")
+            torch.cuda.synchronize()
+            out.append((img.cpu(), aux.cpu(), int(count.item()), grads["tf"].cpu().numpy(), grads["eye"].cpu().numpy()))
+    finally:
+        autotune.set_tile_width(*old)
+    (i0, a0, c0, t0, e0), (i1, a1, c1, t1, e1) = out
+    assert not torch.isnan(i1).any() and not torch.isnan(a1).any()
+    assert c0 == c1 > 0
+    assert torch.equal(i0, i1) and torch.equal(a0, a1)
+    assert_close(t1, t0, 1e-5, "grad tf")
+    assert_close(e1, e0, 1e-5, "grad eye")

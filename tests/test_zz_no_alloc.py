@@ -75,8 +75,8 @@ def test_noalloc_matches_workspace_entry_point_twice(want):
     for call in range(2):
         ref = _zero_grads(sc, want)
         got = _zero_grads(sc, want)
-        _abi.check(lib.dvr_backward(*_args(sc, eye, step, aux, seed, ref), ws.data_ptr(), ws.numel(), stream),
-                   "dvr_backward")
+        _abi.check(lib.dvr_backward(*_args(sc, eye, step, aux, seed, ref), None, 0, ws.data_ptr(), ws.numel(),
+                                    stream), "dvr_backward")
         _abi.check(lib.dvr_backward_noalloc(*_args(sc, eye, step, aux, seed, got), stream),
                    "dvr_backward_noalloc")
         torch.cuda.synchronize()
