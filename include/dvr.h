@@ -73,7 +73,7 @@
 extern "C" {
 #endif
 
-#define DVR_ABI_VERSION 5
+#define DVR_ABI_VERSION 6
 
 /* exported from the shared library (which hides everything else) */
 #if defined(__GNUC__)
@@ -300,6 +300,43 @@ DVR_API int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr
                  float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags,
                  const uint32_t* tile_order, int64_t tile_order_len,
                  void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Per-K-step checkpoints for the paper's alpha-form opacity recovery (an
+ * ablation; Sec. 4.4). dvr_backward recovers the transmittance before each
+ * sample from the stored optical depth, which neither cancels nor drifts and
+ * needs no checkpoint. The paper's recovery A_i = (alpha_i - A_{i+1}) /
+ * (alpha_i - 1) (DVR_FLAG_INVERT_ALPHA32 / _ALPHA64) loses accuracy with
+ * every step; with checkpoints it restarts from the forward's own value
+ * before samples 0, K, 2K, ..., so its error spans at most K steps, at a
+ * memory cost of ceil(N / K) floats per ray instead of N. Only the opacity
+ * is checkpointed: the adjoint of the blend needs no recovered colour.
+ *
+ * dvr_checkpoint_slots: floats per pixel that hold the checkpoints of any
+ *   ray through these volumes at this step (the box diagonal / dt, / K);
+ *   DVR_ERR_ARG for invalid arguments.
+ * dvr_forward_checkpointed: dvr_forward (emission-absorption, FP32 volume,
+ *   no tile order) that also writes, for each pixel p, the transmittance
+ *   1 - A before sample m K into checkpoints[p * slots + m] (device float
+ *   [P][slots], slots >= dvr_checkpoint_slots(..., K); caller-owned).
+ * dvr_backward_checkpointed: dvr_backward with an alpha-form flag (required)
+ *   and those checkpoints (same K and slots; no tile order).
+ * Errors as dvr_forward / dvr_backward; DVR_ERR_UNSUPPORTED outside the
+ * emission-absorption FP32 case; DVR_ERR_ARG for K < 1, too few slots, or a
+ * NULL checkpoint array.
+ */
+DVR_API int32_t dvr_checkpoint_slots(const dvr_volume* volumes, int32_t n_volumes, float step_voxels, int32_t k);
+DVR_API int dvr_forward_checkpointed(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
+                                     int32_t model, const dvr_view* views, int32_t n_views, const float* eye,
+                                     float step_voxels, float* image, float* aux,
+                                     unsigned long long* sample_count, int32_t k, float* checkpoints,
+                                     int32_t slots, void* stream);
+DVR_API int dvr_backward_checkpointed(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
+                                      int32_t model, const dvr_view* views, int32_t n_views, const float* eye,
+                                      float step_voxels, const float* aux, const float* grad_image,
+                                      float* const* grad_volumes, float* grad_tf, float* grad_eye,
+                                      float* grad_step, uint32_t flags, int32_t k, const float* checkpoints,
+                                      int32_t slots, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Bytes of device workspace a dvr_backward call over n_views views needs
  * (a multiple of 256; 0 if n_views < 1). */

@@ -135,9 +135,20 @@ class Scene:
         return ws
 
 
+def checkpoint_slots(scene: "Scene", step_voxels, k: int) -> int:
+    """Floats per pixel for the per-K-step opacity checkpoints of the
+    alpha-form recovery (dvr_checkpoint_slots)."""
+    n = int(_abi.load().dvr_checkpoint_slots(scene.vol_desc, len(scene.volumes), float(step_voxels), int(k)))
+    if n < 0:
+        raise _abi.DVRError(f"dvr_checkpoint_slots: {_abi.load().dvr_last_error().decode()}")
+    return n
+
+
 def forward(volumes, tf, model, views, eye, step_voxels, *, scene: Scene | None = None, image=None,
-            aux=None, sample_count=None, stream=None):
-    """Alg. 1 for all views in one launch. Returns (image [P][C], aux [P][2])."""
+            aux=None, sample_count=None, stream=None, checkpoints=None):
+    """Alg. 1 for all views in one launch. Returns (image [P][C], aux [P][2]).
+    `checkpoints` = (tensor [P][slots], K): also record the transmittance
+    before every K-th sample (dvr_forward_checkpointed)."""
     sc = scene or Scene.make(volumes, tf, model, views)
     dev = sc.volumes[0].device
     _require_cuda(eye, "eye")
@@ -147,23 +158,34 @@ def forward(volumes, tf, model, views, eye, step_voxels, *, scene: Scene | None 
         image = torch.empty((sc.pixels, sc.channels), device=dev, dtype=torch.float32)
     if aux is None:
         aux = torch.empty((sc.pixels, 2), device=dev, dtype=torch.float32)
+    lib = _abi.load()
+    if checkpoints is not None:
+        ck, k = checkpoints
+        rc = lib.dvr_forward_checkpointed(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
+                                          len(sc.views), _ptr(eye), float(step_voxels), _ptr(image), _ptr(aux),
+                                          _ptr(sample_count), int(k), _ptr(ck), int(ck.shape[1]),
+                                          _stream_ptr(stream))
+        _abi.check(rc, "dvr_forward_checkpointed")
+        return image, aux
     # the forward keeps the fixed tile order: the centre-out order measured no
     # faster on one 512^2 view and 3% slower on 64 uneven views (B300)
-    rc = _abi.load().dvr_forward(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
-                                 len(sc.views), _ptr(eye), float(step_voxels), _ptr(image), _ptr(aux),
-                                 _ptr(sample_count), None, 0, _stream_ptr(stream))
+    rc = lib.dvr_forward(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
+                         len(sc.views), _ptr(eye), float(step_voxels), _ptr(image), _ptr(aux),
+                         _ptr(sample_count), None, 0, _stream_ptr(stream))
     _abi.check(rc, "dvr_forward")
     return image, aux
 
 
 def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, want=("volume", "tf", "eye"),
              scene: Scene | None = None, grads: dict | None = None, tf_immediate=False, inversion="depth",
-             stream=None):
+             stream=None, checkpoints=None):
     """Alg. 2 for all views in one launch. Returns a dict with float32
     gradients for the requested parameters ("volume" -> list, "tf", "eye",
     "step"); buffers passed in `grads` are accumulated into. `inversion`
     selects how the opacity before each sample is recovered: "depth"
-    (default), or the ablations "alpha32" / "alpha64" (the paper's form)."""
+    (default), or the ablations "alpha32" / "alpha64" (the paper's form),
+    which with `checkpoints` = (tensor, K) from a checkpointed forward
+    restart from the forward's value every K samples."""
     sc = scene or Scene.make(volumes, tf, model, views)
     dev = sc.volumes[0].device
     g = dict(grads or {})
@@ -182,6 +204,15 @@ def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, wa
     flags |= {"depth": 0, "alpha32": _abi.DVR_FLAG_INVERT_ALPHA32, "alpha64": _abi.DVR_FLAG_INVERT_ALPHA64}[inversion]
     lib = _abi.load()
     ws = sc.workspace(lib, stream)
+    if checkpoints is not None:
+        ck, k = checkpoints
+        rc = lib.dvr_backward_checkpointed(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
+                                           len(sc.views), _ptr(eye), float(step_voxels), _ptr(aux),
+                                           _ptr(grad_image), gv, _ptr(g.get("tf")), _ptr(g.get("eye")),
+                                           _ptr(g.get("step")), flags, int(k), _ptr(ck), int(ck.shape[1]),
+                                           _ptr(ws), ws.numel(), _stream_ptr(stream))
+        _abi.check(rc, "dvr_backward_checkpointed")
+        return g
     # centre-out tile order: adjoint 0.365 -> 0.351 ms on a 512^2 view of a
     # 256^3 volume (B300), neutral on 64 uneven views
     order, n_order = sc.tile_order(lib, adjoint=True)

@@ -210,6 +210,164 @@ int check_order(const uint32_t* order, long long len, const dvr_view* views, int
     return DVR_OK;
 }
 
+// dvr_forward, and with `ckpt` dvr_forward_checkpointed.
+int forward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
+                 const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
+                 float* image, float* aux, unsigned long long* sample_count, const uint32_t* tile_order,
+                 int64_t tile_order_len, float* ckpt, int32_t ck_k, int32_t ck_slots, void* stream)
+{
+    Common c;
+    int rc = check_common(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, c);
+    if (rc) return rc;
+    rc = check_order(tile_order, tile_order_len, views, n_views, DVR_PASS_FORWARD, "dvr_forward");
+    if (rc) return rc;
+    if (!image) return fail(DVR_ERR_ARG, "image is NULL");
+    if (!aligned(image, c.channels == 4 ? 16 : 4)) return fail(DVR_ERR_ARG, "image is not 16-byte aligned");
+    if (aux && !aligned(aux, 8)) return fail(DVR_ERR_ARG, "aux is not 8-byte aligned");
+    dvr::Params p;
+    long long order_off = 0;
+    for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
+        const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
+        pack(p, DVR_PASS_FORWARD, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
+             step_voxels);
+        if (tile_order) {
+            p.order = tile_order + order_off;
+            order_off += p.total_tiles;
+        }
+        p.image = image;
+        p.aux = aux;
+        p.sample_count = sample_count;
+        p.ckpt = ckpt;
+        p.ckpt_k = ck_k;
+        p.ckpt_slots = ck_slots;
+        cudaError_t e = model == DVR_COLOR_VOLUME ? dvr::launch_forward_color(p, c.dtype, (cudaStream_t)stream)
+                                                  : dvr::launch_forward(p, model, c.dtype, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dvr_forward launch");
+    }
+    return DVR_OK;
+}
+
+
+// dvr_backward, and with `ckpt` dvr_backward_checkpointed.
+int backward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
+                  const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
+                  const float* aux, const float* grad_image, float* const* grad_volumes,
+                  float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags, const uint32_t* tile_order,
+                  int64_t tile_order_len, const float* ckpt, int32_t ck_k, int32_t ck_slots, void* workspace,
+                  size_t workspace_bytes_, void* stream)
+{
+    if (flags & ~(DVR_FLAG_TF_IMMEDIATE | DVR_FLAG_INVERT_ALPHA32 | DVR_FLAG_INVERT_ALPHA64))
+        return fail(DVR_ERR_ARG, "unknown flag bits 0x%x", flags);
+    if ((flags & DVR_FLAG_INVERT_ALPHA32) && (flags & DVR_FLAG_INVERT_ALPHA64))
+        return fail(DVR_ERR_ARG, "choose one inversion ablation");
+    const int inv = (flags & DVR_FLAG_INVERT_ALPHA32) ? dvr::kInvAlpha32
+                  : (flags & DVR_FLAG_INVERT_ALPHA64) ? dvr::kInvAlpha64 : dvr::kInvDepth;
+    Common c;
+    int rc = check_common(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, c);
+    if (rc) return rc;
+    if (inv != dvr::kInvDepth && (model != DVR_EMISSION_ABSORPTION || c.dtype != DVR_F32 || !grad_tf ||
+                                  (flags & DVR_FLAG_TF_IMMEDIATE)))
+        return fail(DVR_ERR_UNSUPPORTED, "inversion ablations: emission-absorption, FP32 volume, delayed TF "
+                    "gradient only");
+    rc = check_order(tile_order, tile_order_len, views, n_views, DVR_PASS_ADJOINT, "dvr_backward");
+    if (rc) return rc;
+    if (!aux || !grad_image) return fail(DVR_ERR_ARG, "aux and grad_image are required");
+    if (!aligned(aux, 8)) return fail(DVR_ERR_ARG, "aux is not 8-byte aligned");
+    if (!aligned(grad_image, c.channels == 4 ? 16 : 4))
+        return fail(DVR_ERR_ARG, "grad_image is not 16-byte aligned");
+    if (model != DVR_EMISSION_ABSORPTION && grad_tf)
+        return fail(DVR_ERR_ARG, "grad_tf needs the emission-absorption model");
+    bool gvol = false;
+    if (grad_volumes)
+        for (int i = 0; i < n_volumes; ++i) {
+            gvol |= grad_volumes[i] != nullptr;
+            if (grad_volumes[i] && !aligned(grad_volumes[i], model == DVR_COLOR_VOLUME ? 16 : 4))
+                return fail(DVR_ERR_ARG, "grad volume %d is not aligned to its vertex", i);
+        }
+    const int tfm = grad_tf ? ((flags & DVR_FLAG_TF_IMMEDIATE) ? dvr::kTFImmediate : dvr::kTFDelayed)
+                            : dvr::kTFNone;
+    const bool pos = grad_eye != nullptr || grad_step != nullptr;
+    const size_t ws = workspace_bytes(n_views);
+    if (!workspace || workspace_bytes_ < ws)
+        return fail(DVR_ERR_ARG, "workspace %p of %zu bytes: %zu bytes needed", workspace, workspace_bytes_, ws);
+    if (!aligned(workspace, 16)) return fail(DVR_ERR_ARG, "workspace is not 16-byte aligned");
+    if (!gvol && tfm == dvr::kTFNone && !pos) return DVR_OK;   // nothing requested
+    // the scattering kernel variant is chosen per launch: when any volume
+    // takes a gradient, every rendered volume needs a buffer
+    if (gvol)
+        for (int i = 0; i < n_views; ++i)
+            if (!grad_volumes[views[i].volume])
+                return fail(DVR_ERR_ARG, "view %d renders volume %d, which has no gradient buffer "
+                            "while another volume has one", i, views[i].volume);
+    cudaError_t e0 = cudaMemsetAsync(workspace, 0, ws, (cudaStream_t)stream);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "dvr_backward workspace");
+    dvr::Params p;
+    long long order_off = 0;
+    for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
+        const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
+        pack(p, DVR_PASS_ADJOINT, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
+             step_voxels);
+        p.queue = reinterpret_cast<unsigned*>(static_cast<char*>(workspace)
+                                              + (size_t)(v0 / dvr::kMaxViewsPerLaunch) * kQueueStride);
+        if (tile_order) {
+            p.order = tile_order + order_off;
+            order_off += p.total_tiles;
+        }
+        if (grad_volumes)
+            for (int i = 0; i < n_volumes; ++i) {
+                p.vol[i].grad = grad_volumes[i];
+                const long long bytes = 4ll * volumes[i].nx * volumes[i].ny * volumes[i].nz;
+                p.vol[i].grad_vec = bytes <= dvr::l2_bytes();
+            }
+        p.aux = const_cast<float*>(aux);
+        p.grad_image = grad_image;
+        p.grad_tf = grad_tf;
+        p.grad_eye = grad_eye;
+        p.grad_step = grad_step;
+        p.ckpt = const_cast<float*>(ckpt);
+        p.ckpt_k = ck_k;
+        p.ckpt_slots = ck_slots;
+        cudaError_t e = model == DVR_COLOR_VOLUME
+            ? dvr::launch_backward_color(p, c.dtype, gvol, pos, (cudaStream_t)stream)
+            : dvr::launch_backward(p, model, c.dtype, gvol, tfm, pos, inv, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dvr_backward launch");
+    }
+    return DVR_OK;
+}
+
+
+// Checkpoint slots per pixel for K: one per K samples of the longest ray
+// any view of these volumes can have (the box diagonal divided by dt).
+int32_t checkpoint_slots(const dvr_volume* volumes, int32_t n_volumes, float step_voxels, int32_t k)
+{
+    long long best = 0;
+    for (int i = 0; i < n_volumes; ++i) {
+        const double ex = volumes[i].nx - 1.0, ey = volumes[i].ny - 1.0, ez = volumes[i].nz - 1.0;
+        const long long n = (long long)std::ceil(std::sqrt(ex * ex + ey * ey + ez * ez) / (double)step_voxels) + 2;
+        const long long slots = (n + k - 1) / k;
+        if (slots > best) best = slots;
+    }
+    return best > 0x7fffffffll ? -1 : (int32_t)best;
+}
+
+int check_ckpt(const dvr_volume* volumes, int32_t n_volumes, int32_t model, float step_voxels, const void* ckpt,
+               int32_t k, int32_t slots, const char* who)
+{
+    if (!volumes || n_volumes < 1 || n_volumes > dvr::kMaxVolumes)
+        return fail(DVR_ERR_ARG, "%s: n_volumes %d outside [1, %d] or volumes is NULL", who, n_volumes, dvr::kMaxVolumes);
+    if (model != DVR_EMISSION_ABSORPTION || volumes[0].dtype != DVR_F32)
+        return fail(DVR_ERR_UNSUPPORTED, "%s: checkpoints serve the alpha-form ablations (emission-absorption, "
+                    "FP32 volume)", who);
+    if (!ckpt || !aligned(ckpt, 4)) return fail(DVR_ERR_ARG, "%s: checkpoints NULL or misaligned", who);
+    if (k < 1) return fail(DVR_ERR_ARG, "%s: K = %d < 1", who, k);
+    if (!(step_voxels >= 0x1p-10f) || !std::isfinite(step_voxels))
+        return fail(DVR_ERR_ARG, "%s: step_voxels %g must be finite and >= 2^-10", who, (double)step_voxels);
+    const int32_t need = checkpoint_slots(volumes, n_volumes, step_voxels, k);
+    if (need < 0 || slots < need)
+        return fail(DVR_ERR_ARG, "%s: %d slots per pixel, %d needed for K = %d", who, slots, need, k);
+    return DVR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -309,34 +467,31 @@ int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, 
                 int64_t tile_order_len, void* stream)
 {
     g_err[0] = 0;
-    Common c;
-    int rc = check_common(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, c);
-    if (rc) return rc;
-    rc = check_order(tile_order, tile_order_len, views, n_views, DVR_PASS_FORWARD, "dvr_forward");
-    if (rc) return rc;
-    if (!image) return fail(DVR_ERR_ARG, "image is NULL");
-    if (!aligned(image, c.channels == 4 ? 16 : 4)) return fail(DVR_ERR_ARG, "image is not 16-byte aligned");
-    if (aux && !aligned(aux, 8)) return fail(DVR_ERR_ARG, "aux is not 8-byte aligned");
-    dvr::Params p;
-    long long order_off = 0;
-    for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
-        const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
-        pack(p, DVR_PASS_FORWARD, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
-             step_voxels);
-        if (tile_order) {
-            p.order = tile_order + order_off;
-            order_off += p.total_tiles;
-        }
-        p.image = image;
-        p.aux = aux;
-        p.sample_count = sample_count;
-        cudaError_t e = model == DVR_COLOR_VOLUME ? dvr::launch_forward_color(p, c.dtype, (cudaStream_t)stream)
-                                                  : dvr::launch_forward(p, model, c.dtype, (cudaStream_t)stream);
-        if (e != cudaSuccess) return cuda_fail(e, "dvr_forward launch");
-    }
-    return DVR_OK;
+    return forward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, image, aux, sample_count,
+                        tile_order, tile_order_len, nullptr, 0, 0, stream);
 }
 
+int32_t dvr_checkpoint_slots(const dvr_volume* volumes, int32_t n_volumes, float step_voxels, int32_t k)
+{
+    g_err[0] = 0;
+    if (!volumes || n_volumes < 1 || n_volumes > dvr::kMaxVolumes || k < 1 || !(step_voxels >= 0x1p-10f) ||
+        !std::isfinite(step_voxels))
+        return fail(DVR_ERR_ARG, "dvr_checkpoint_slots: invalid volumes, step or K");
+    return checkpoint_slots(volumes, n_volumes, step_voxels, k);
+}
+
+int dvr_forward_checkpointed(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
+                             const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
+                             float* image, float* aux, unsigned long long* sample_count, int32_t k,
+                             float* checkpoints, int32_t slots, void* stream)
+{
+    g_err[0] = 0;
+    const int rc = check_ckpt(volumes, n_volumes, model, step_voxels, checkpoints, k, slots,
+                              "dvr_forward_checkpointed");
+    if (rc) return rc;
+    return forward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, image, aux, sample_count,
+                        nullptr, 0, checkpoints, k, slots, stream);
+}
 int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                  const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
                  const float* aux, const float* grad_image, float* const* grad_volumes,
@@ -344,82 +499,29 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
                  int64_t tile_order_len, void* workspace, size_t workspace_bytes_, void* stream)
 {
     g_err[0] = 0;
-    if (flags & ~(DVR_FLAG_TF_IMMEDIATE | DVR_FLAG_INVERT_ALPHA32 | DVR_FLAG_INVERT_ALPHA64))
-        return fail(DVR_ERR_ARG, "unknown flag bits 0x%x", flags);
-    if ((flags & DVR_FLAG_INVERT_ALPHA32) && (flags & DVR_FLAG_INVERT_ALPHA64))
-        return fail(DVR_ERR_ARG, "choose one inversion ablation");
-    const int inv = (flags & DVR_FLAG_INVERT_ALPHA32) ? dvr::kInvAlpha32
-                  : (flags & DVR_FLAG_INVERT_ALPHA64) ? dvr::kInvAlpha64 : dvr::kInvDepth;
-    Common c;
-    int rc = check_common(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, c);
-    if (rc) return rc;
-    if (inv != dvr::kInvDepth && (model != DVR_EMISSION_ABSORPTION || c.dtype != DVR_F32 || !grad_tf ||
-                                  (flags & DVR_FLAG_TF_IMMEDIATE)))
-        return fail(DVR_ERR_UNSUPPORTED, "inversion ablations: emission-absorption, FP32 volume, delayed TF "
-                    "gradient only");
-    rc = check_order(tile_order, tile_order_len, views, n_views, DVR_PASS_ADJOINT, "dvr_backward");
-    if (rc) return rc;
-    if (!aux || !grad_image) return fail(DVR_ERR_ARG, "aux and grad_image are required");
-    if (!aligned(aux, 8)) return fail(DVR_ERR_ARG, "aux is not 8-byte aligned");
-    if (!aligned(grad_image, c.channels == 4 ? 16 : 4))
-        return fail(DVR_ERR_ARG, "grad_image is not 16-byte aligned");
-    if (model != DVR_EMISSION_ABSORPTION && grad_tf)
-        return fail(DVR_ERR_ARG, "grad_tf needs the emission-absorption model");
-    bool gvol = false;
-    if (grad_volumes)
-        for (int i = 0; i < n_volumes; ++i) {
-            gvol |= grad_volumes[i] != nullptr;
-            if (grad_volumes[i] && !aligned(grad_volumes[i], model == DVR_COLOR_VOLUME ? 16 : 4))
-                return fail(DVR_ERR_ARG, "grad volume %d is not aligned to its vertex", i);
-        }
-    const int tfm = grad_tf ? ((flags & DVR_FLAG_TF_IMMEDIATE) ? dvr::kTFImmediate : dvr::kTFDelayed)
-                            : dvr::kTFNone;
-    const bool pos = grad_eye != nullptr || grad_step != nullptr;
-    const size_t ws = workspace_bytes(n_views);
-    if (!workspace || workspace_bytes_ < ws)
-        return fail(DVR_ERR_ARG, "workspace %p of %zu bytes: %zu bytes needed", workspace, workspace_bytes_, ws);
-    if (!aligned(workspace, 16)) return fail(DVR_ERR_ARG, "workspace is not 16-byte aligned");
-    if (!gvol && tfm == dvr::kTFNone && !pos) return DVR_OK;   // nothing requested
-    // the scattering kernel variant is chosen per launch: when any volume
-    // takes a gradient, every rendered volume needs a buffer
-    if (gvol)
-        for (int i = 0; i < n_views; ++i)
-            if (!grad_volumes[views[i].volume])
-                return fail(DVR_ERR_ARG, "view %d renders volume %d, which has no gradient buffer "
-                            "while another volume has one", i, views[i].volume);
-    cudaError_t e0 = cudaMemsetAsync(workspace, 0, ws, (cudaStream_t)stream);
-    if (e0 != cudaSuccess) return cuda_fail(e0, "dvr_backward workspace");
-    dvr::Params p;
-    long long order_off = 0;
-    for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
-        const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
-        pack(p, DVR_PASS_ADJOINT, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
-             step_voxels);
-        p.queue = reinterpret_cast<unsigned*>(static_cast<char*>(workspace)
-                                              + (size_t)(v0 / dvr::kMaxViewsPerLaunch) * kQueueStride);
-        if (tile_order) {
-            p.order = tile_order + order_off;
-            order_off += p.total_tiles;
-        }
-        if (grad_volumes)
-            for (int i = 0; i < n_volumes; ++i) {
-                p.vol[i].grad = grad_volumes[i];
-                const long long bytes = 4ll * volumes[i].nx * volumes[i].ny * volumes[i].nz;
-                p.vol[i].grad_vec = bytes <= dvr::l2_bytes();
-            }
-        p.aux = const_cast<float*>(aux);
-        p.grad_image = grad_image;
-        p.grad_tf = grad_tf;
-        p.grad_eye = grad_eye;
-        p.grad_step = grad_step;
-        cudaError_t e = model == DVR_COLOR_VOLUME
-            ? dvr::launch_backward_color(p, c.dtype, gvol, pos, (cudaStream_t)stream)
-            : dvr::launch_backward(p, model, c.dtype, gvol, tfm, pos, inv, (cudaStream_t)stream);
-        if (e != cudaSuccess) return cuda_fail(e, "dvr_backward launch");
-    }
-    return DVR_OK;
+    return backward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, aux, grad_image,
+                         grad_volumes, grad_tf, grad_eye, grad_step, flags, tile_order, tile_order_len, nullptr, 0,
+                         0, workspace, workspace_bytes_, stream);
 }
 
+int dvr_backward_checkpointed(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
+                              const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
+                              const float* aux, const float* grad_image, float* const* grad_volumes,
+                              float* grad_tf, float* grad_eye, float* grad_step, uint32_t flags, int32_t k,
+                              const float* checkpoints, int32_t slots, void* workspace, size_t workspace_bytes_,
+                              void* stream)
+{
+    g_err[0] = 0;
+    if (!(flags & (DVR_FLAG_INVERT_ALPHA32 | DVR_FLAG_INVERT_ALPHA64)))
+        return fail(DVR_ERR_ARG, "dvr_backward_checkpointed: checkpoints serve the alpha-form recovery "
+                    "(DVR_FLAG_INVERT_ALPHA32 or _ALPHA64); the default recovery needs none");
+    const int rc = check_ckpt(volumes, n_volumes, model, step_voxels, checkpoints, k, slots,
+                              "dvr_backward_checkpointed");
+    if (rc) return rc;
+    return backward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, aux, grad_image,
+                         grad_volumes, grad_tf, grad_eye, grad_step, flags, nullptr, 0, checkpoints, k, slots,
+                         workspace, workspace_bytes_, stream);
+}
 int dvr_forward_tangent(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                         const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
                         float* image, float* tangent, void* stream)

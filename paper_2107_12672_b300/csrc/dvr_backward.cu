@@ -166,6 +166,16 @@ backward_kernel(const __grid_constant__ Params p)
         // wrote) or, with the binary64 guard, from the optical depth
         float Af = INV == kInvAlpha32 ? -expm1f(-(sh + sl)) : 0.f;
         double Ad = INV == kInvAlpha64 ? -expm1(-((double)sh + (double)sl)) : 0.0;
+        // with forward checkpoints (alpha forms only): the recovered opacity
+        // is replaced by the forward's own value before samples m K, so the
+        // recovery drifts over at most K samples
+        const float* ck = nullptr;
+        int ck_i = -1, ck_m = -1;      // next checkpointed sample below the march, its slot
+        if (INV != kInvDepth && p.ckpt && N > 0) {
+            ck = p.ckpt + (vw.pixel_offset + (long long)py * vw.width + px) * p.ckpt_slots;
+            ck_m = min((N - 1) / p.ckpt_k, p.ckpt_slots - 1);
+            ck_i = ck_m * p.ckpt_k;
+        }
         const float dconst = EA ? 0.f : Ah * expf(-(sh + sl)) * G.dt;   // absorption: d^_i
         float gs[3] = {0.f, 0.f, 0.f}, gi[3] = {0.f, 0.f, 0.f};
         float dt_hat = 0.f;
@@ -220,12 +230,22 @@ backward_kernel(const __grid_constant__ Params p)
                     T = expf(-(sh + sl));
                 } else if (INV == kInvAlpha32) {
                     Af = (alpha - Af) / (alpha - 1.f);  // Eq. inv-blend-forward, binary32
+                    if (i == ck_i) {
+                        Af = 1.f - ck[ck_m];
+                        --ck_m;
+                        ck_i -= p.ckpt_k;
+                    }
                     T = 1.f - Af;
                 } else {
                     if (Ad > 0.99) {
                         Ad = ((double)alpha - Ad) / ((double)alpha - 1.0);
                     } else {
                         Ad = (double)((alpha - (float)Ad) / (alpha - 1.f));
+                    }
+                    if (i == ck_i) {
+                        Ad = 1.0 - (double)ck[ck_m];
+                        --ck_m;
+                        ck_i -= p.ckpt_k;
                     }
                     T = (float)(1.0 - Ad);
                 }

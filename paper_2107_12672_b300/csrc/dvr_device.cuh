@@ -67,6 +67,9 @@ struct Params {
     unsigned long long* sample_count;
     unsigned* queue;                 // adjoint tile queue: a counter zeroed before the launch
     const unsigned* order;           // tile taken at each rank of the launch, or null: rank order
+    float* ckpt;                     // transmittance before samples 0, K, 2K, ... ([pixel][ckpt_slots]) or null
+    int ckpt_k;
+    int ckpt_slots;
 };
 
 // ---------------------------------------------------------------- storage

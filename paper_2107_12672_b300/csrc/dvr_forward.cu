@@ -10,7 +10,10 @@
 
 namespace dvr {
 
-template <int MODEL, typename VT>
+// CKPT: also record the transmittance 1 - A_i before every K-th sample
+// (i = 0, K, 2K, ...) of each ray, for the adjoint's opacity recovery in
+// the paper's alpha form.
+template <int MODEL, typename VT, bool CKPT = false>
 __global__ void __launch_bounds__(kWarps * 32, DVR_FWD_MIN_BLOCKS)
 forward_kernel(const __grid_constant__ Params p)
 {
@@ -47,6 +50,10 @@ forward_kernel(const __grid_constant__ Params p)
 
         float sh = 0.f, sl = 0.f;    // optical depth, hi + lo
         float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+        // checkpoints of this ray: slot m holds 1 - A before sample m K
+        float* ck = CKPT && valid ? p.ckpt + (vw.pixel_offset + (long long)py * vw.width + px) * p.ckpt_slots
+                                  : nullptr;
+        int ck_left = 0, ck_m = 0;   // samples until the next checkpoint, its slot
         // software pipeline: the corners of samples i+1 and i+2 are in
         // flight while sample i is composited (positions past the ray end are
         // clamped to the box, so the extra fetches stay in bounds); a sample
@@ -61,6 +68,14 @@ forward_kernel(const __grid_constant__ Params p)
         }
 #pragma unroll 3
         for (int i = 0; i < N; ++i) {
+            if (CKPT) {
+                if (ck_left == 0) {
+                    if (ck && ck_m < p.ckpt_slots) ck[ck_m] = T;
+                    ++ck_m;
+                    ck_left = p.ckpt_k;
+                }
+                --ck_left;
+            }
             MCell cur = n1;
             cell_resolve(cur, last_v);
 #pragma unroll
@@ -109,10 +124,10 @@ forward_kernel(const __grid_constant__ Params p)
     }
 }
 
-template <int MODEL, typename VT>
+template <int MODEL, typename VT, bool CKPT = false>
 static cudaError_t launch(const Params& p, cudaStream_t stream)
 {
-    auto k = forward_kernel<MODEL, VT>;
+    auto k = forward_kernel<MODEL, VT, CKPT>;
     const int blocks = (p.total_tiles + kWarps - 1) / kWarps;
     // shared memory holds only this TF, the rest of the SM's 256 KB stays
     // L1 cache for the gathers
@@ -123,6 +138,10 @@ static cudaError_t launch(const Params& p, cudaStream_t stream)
 
 cudaError_t launch_forward(const Params& p, int model, int vol_dtype, cudaStream_t stream)
 {
+    if (p.ckpt) {
+        if (model != DVR_EMISSION_ABSORPTION || vol_dtype != DVR_F32) return cudaErrorNotSupported;
+        return launch<DVR_EMISSION_ABSORPTION, float, true>(p, stream);
+    }
     if (model == DVR_EMISSION_ABSORPTION) {
         switch (vol_dtype) {
         case DVR_F32: return launch<DVR_EMISSION_ABSORPTION, float>(p, stream);

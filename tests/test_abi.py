@@ -246,3 +246,26 @@ def test_forward_refuses_a_tile_order_of_the_wrong_length():
     n = lib.dvr_tile_order(_one_view(), 1, _abi.DVR_PASS_FORWARD, None, 0)
     rc = lib.dvr_forward(_one_volume(), 1, None, 0, _one_view(), 1, 16, 0.5, 16, None, None, 4096, n + 1, None)
     assert rc == -1 and b"tile_order" in lib.dvr_last_error()
+
+
+def test_checkpoint_slots_and_argument_errors():
+    """dvr_checkpoint_slots: ceil((ceil(box diagonal / step) + 2) / K) per
+    pixel; the checkpointed entry points refuse other models, K < 1, too few
+    slots and the default recovery, before any CUDA call."""
+    lib = _abi.load()
+    vols = _one_volume(nx=64)
+    # 64^3: diagonal sqrt(3) * 63 = 109.12 voxels; / 0.5 -> 219 steps + 2 = 221; / 16 -> 14
+    assert lib.dvr_checkpoint_slots(vols, 1, 0.5, 16) == 14
+    assert lib.dvr_checkpoint_slots(vols, 1, 0.5, 0) == -1
+    assert lib.dvr_checkpoint_slots(None, 1, 0.5, 16) == -1
+    view = _one_view()
+    tf = _abi.DvrTF(4, 0, 4096)
+    fwd = lambda model, k, slots: lib.dvr_forward_checkpointed(vols, 1, ctypes.byref(tf), model, view, 1, 16, 0.5, 16,
+                                                               None, None, k, 8192, slots, None)
+    assert fwd(_abi.DVR_ABSORPTION, 16, 14) == -4
+    assert fwd(_abi.DVR_EMISSION_ABSORPTION, 0, 14) == -1
+    assert fwd(_abi.DVR_EMISSION_ABSORPTION, 16, 13) == -1 and b"slots" in lib.dvr_last_error()
+    bwd = lambda flags: lib.dvr_backward_checkpointed(vols, 1, ctypes.byref(tf), _abi.DVR_EMISSION_ABSORPTION, view, 1,
+                                                      16, 0.5, 64, 64, None, 128, None, None, flags, 16, 8192, 14,
+                                                      4096, 256, None)
+    assert bwd(0) == -1 and b"alpha" in lib.dvr_last_error()
