@@ -418,6 +418,16 @@ def accuracy(wl):
                                       want=("tf",), inversion=mode)
                     inv[{"alpha64": "alpha_form_fp64_above_0.99", "alpha32": "alpha_form_fp32"}[mode]] = \
                         rel(gm["tf"].cpu().numpy(), ref_tf)
+                # the binary32 alpha form restarted from forward checkpoints every K samples
+                for k in (256, 16):
+                    ck = torch.empty((wl.scene.pixels, dvr.checkpoint_slots(wl.scene, w.step_voxels, k)),
+                                     device=wl.device)
+                    _, aux_k = dvr.forward(None, None, None, None, eye, w.step_voxels, scene=wl.scene,
+                                           checkpoints=(ck, k))
+                    gm = dvr.backward(None, None, None, None, eye, w.step_voxels, aux_k, G, scene=wl.scene,
+                                      want=("tf",), inversion="alpha32", checkpoints=(ck, k))
+                    inv[f"alpha_form_fp32_checkpoints_K{k}"] = rel(gm["tf"].cpu().numpy(), ref_tf)
+                    del ck
                 out["grad_tf_by_inversion"] = inv
     if ref_eye:
         out["grad_eye"] = max(rel(g["eye"].cpu().numpy()[k], r) for k, r in ref_eye)
