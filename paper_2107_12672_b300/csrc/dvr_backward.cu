@@ -397,15 +397,17 @@ static cudaError_t launch_one(const Params& p, cudaStream_t stream)
         if (TFM == kTFWarp) smem += sizeof(float) * 4 * kWarps * (size_t)p.R;
     }
     // opt in to more than 48 KB of dynamic shared memory, once per device
-    static unsigned long long configured = 0;
+    // (an atomic bit per device: calls from several host threads may race
+    // to set it; setting the attribute twice is harmless)
+    static std::atomic<unsigned long long> configured{0};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !(configured >> dev & 1ull)) {
+    if (dev >= 64 || !(configured.load(std::memory_order_relaxed) >> dev & 1ull)) {
         cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)(sizeof(float4) * kMaxTF * (2 + kWarps)
                                                      + sizeof(float) * 4 * 32 * kWarps * kPrivateMaxR));
         if (err != cudaSuccess) return err;
-        configured |= 1ull << dev;
+        if (dev < 64) configured.fetch_or(1ull << dev, std::memory_order_relaxed);
     }
     // one tile per warp; with the tile queue, as many blocks as fit on the
     // device at once

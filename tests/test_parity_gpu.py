@@ -648,3 +648,34 @@ def test_checkpoints_bound_the_alpha_form_drift():
     assert errs[("alpha32", 16)] <= errs[("alpha32", 256)] <= errs[("alpha32", None)], errs
     assert errs[("alpha32", 16)] < 0.1 * errs[("alpha32", None)], errs
     assert errs[("alpha64", 16)] <= GRAD_RTOL, errs
+
+
+def test_tile_order_across_launches():
+    """More than 512 views make several launches; the binding's centre-out
+    tile order is one array whose part for each launch starts after the
+    previous launch's tiles. The adjoint with it equals the adjoint in the
+    fixed order (dvr_backward_noalloc takes no order) up to the order of
+    atomic additions, and every view gets its own eye gradient."""
+    import ctypes
+    from paper_2107_12672_b300 import _abi
+    n = 600
+    w = syn.workload("absorption_64", scale=0.25)
+    views = [syn.View(3 + k % 5, 2 + k % 7) for k in range(n)]
+    eye = to_dev(2.5 * syn.fibonacci_sphere(n))
+    vol = to_dev(w.volumes[0])
+    sc = dvr.Scene.make([vol], None, "absorption", views)
+    img, aux = dvr.forward(None, None, None, None, eye, w.step_voxels, scene=sc)
+    G = to_dev(seeded_grad_image(sc.pixels, 1, 8))
+    g = dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=sc, want=("volume", "eye"))
+    lib = _abi.load()
+    ref_v = torch.zeros_like(vol)
+    ref_e = torch.zeros((n, 3), device="cuda")
+    gv = (ctypes.c_void_p * 1)(ref_v.data_ptr())
+    rc = lib.dvr_backward_noalloc(sc.vol_desc, 1, None, _abi.DVR_ABSORPTION, sc.view_desc, n, eye.data_ptr(),
+                                  ctypes.c_float(w.step_voxels), aux.data_ptr(), G.data_ptr(), gv, None,
+                                  ref_e.data_ptr(), None, 0, torch.cuda.current_stream().cuda_stream)
+    _abi.check(rc, "dvr_backward_noalloc")
+    torch.cuda.synchronize()
+    assert float(ref_e.abs().sum(1).min()) >= 0 and int((ref_e.abs().sum(1) > 0).sum()) > n // 2
+    assert_close(g["volume"][0].cpu().numpy(), ref_v.cpu().numpy(), 1e-5, "grad volume")
+    assert_close(g["eye"].cpu().numpy(), ref_e.cpu().numpy(), 1e-5, "grad eye")
