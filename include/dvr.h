@@ -248,9 +248,11 @@ DVR_API int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_
  * sorted by the distance of the tile centre from the view centre (ties in
  * the fixed order): the long rays through the middle of the volume start
  * first, and tiles taken at the same time lie side by side. Measured on
- * B300 against the fixed row order: the adjoint of a 512 x 512 view of a
- * 256^3 volume 4% faster; the forward not faster there and 3% slower on 64
- * views of uneven sizes. Depends only on the view sizes and the tile width of
+ * B300 against the fixed row order: the adjoint (TF and camera gradients)
+ * of a 512 x 512 view of a 256^3 volume 4% faster; the forward not faster
+ * there and 3% slower on 64 views of uneven sizes; the density-gradient
+ * adjoints of 512^3 and 1024^3 volumes 5-7% slower. Depends only on the view
+ * sizes and the tile width of
  * `pass` now in force (make it again after dvr_set_tile_width).
  *
  * order     host uint32[capacity] or NULL

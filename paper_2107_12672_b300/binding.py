@@ -213,9 +213,11 @@ def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, wa
                                            _ptr(ws), ws.numel(), _stream_ptr(stream))
         _abi.check(rc, "dvr_backward_checkpointed")
         return g
-    # centre-out tile order: adjoint 0.365 -> 0.351 ms on a 512^2 view of a
-    # 256^3 volume (B300), neutral on 64 uneven views
-    order, n_order = sc.tile_order(lib, adjoint=True)
+    # centre-out tile order for the adjoints without a density gradient: 0.365
+    # -> 0.351 ms on a 512^2 view of a 256^3 volume (B300). The scattering
+    # adjoints keep the fixed order, in which the density gradients of
+    # 512^3 and 1024^3 volumes (in HBM) accumulate 5-7% faster.
+    order, n_order = (None, 0) if "volume" in g else sc.tile_order(lib, adjoint=True)
     rc = lib.dvr_backward(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
                           len(sc.views), _ptr(eye), float(step_voxels), _ptr(aux),
                           _ptr(grad_image), gv, _ptr(g.get("tf")), _ptr(g.get("eye")),
