@@ -4,10 +4,26 @@
 One step = one pass of the whole hot path over the 256^3 emission-absorption
 workload: orbit camera -> forward march (Alg. 1) -> L2 loss seed ->
 constant-memory adjoint (Alg. 2) with TF and camera gradients -> orbit
-camera adjoint. Metric: ray samples (forward + adjoint) per second, in
-Gsamples/s, i.e. samples / (t_forward + t_adjoint + the small kernels).
+camera adjoint. Metric: ray samples (each visited by the forward and by the
+adjoint) per second of step, in Gsamples/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload ea_256|absorption_64|tomo_256x64|ea_bf16_512|ea_fp16_1024]
+
+Timing: the tile widths are autotuned per pass (L2 flushed before each timed
+pass); W warm-up steps, then K steps each bracketed by CUDA events with a
+512 MiB write flushing L2 between steps, outside the brackets. `value` comes
+from the step captured once as a CUDA graph and replayed (--eager: launched
+step by step); forward_ms / adjoint_ms come from eager steps. NVML samples
+the SM clock and throttle reasons during the timed region. The roofline
+divides the adjoint's algorithmic bytes by its event time and compares them
+with the measured HBM copy bandwidth (MEASURED_PEAKS.json) and with the L2 /
+L1 / reduction ceilings measured in the same run (dvr_probe); `traffic` is
+the DRAM bytes of the committed ncu summary of that kernel, when it was
+taken on the kernel's current sources. `e2e` copies the step's inputs from
+pinned host memory and reads the results back every step, through the
+public binding. `cpu_baseline` times the FP64 oracle on a strided sample of
+the same rays on the host cores.
 
 Under torchrun each rank renders its own replica of the workload (the rays
 of different problems are independent; no collective on the data path) and
