@@ -137,7 +137,7 @@ int check_common(const dvr_volume* vols, int nvol, const dvr_tf* tf, int model, 
 }
 
 // Fill the launch parameters for views [v0, v1).
-void pack(dvr::Params& p, int pass, const dvr_volume* vols, int nvol, const dvr_tf* tf, const dvr_view* views,
+void pack(dvr::Params& p, int tw, const dvr_volume* vols, int nvol, const dvr_tf* tf, const dvr_view* views,
           int v0, int v1, const float* eye, float step)
 {
     memset(&p, 0, sizeof(p));
@@ -149,7 +149,7 @@ void pack(dvr::Params& p, int pass, const dvr_volume* vols, int nvol, const dvr_
         int m = vols[i].nx > vols[i].ny ? vols[i].nx : vols[i].ny;
         p.vol[i].nmax = vols[i].nz > m ? vols[i].nz : m;
     }
-    const int tw = g_tile_w[pass].load(std::memory_order_relaxed), th = 32 / tw;
+    const int th = 32 / tw;
     p.tile_w = tw;
     p.tile_h = th;
     int tiles = 0;
@@ -188,9 +188,9 @@ int center_out_host(int r, int n)
 }
 
 // Tiles of all launches of a call over `views` at the pass's tile width.
-long long pass_tiles(const dvr_view* views, int n_views, int pass)
+long long pass_tiles(const dvr_view* views, int n_views, int tw)
 {
-    const int tw = g_tile_w[pass].load(std::memory_order_relaxed), th = 32 / tw;
+    const int th = 32 / tw;
     long long t = 0;
     for (int i = 0; i < n_views; ++i)
         t += (long long)((views[i].width + tw - 1) / tw) * ((views[i].height + th - 1) / th);
@@ -198,15 +198,15 @@ long long pass_tiles(const dvr_view* views, int n_views, int pass)
 }
 
 // Check a caller's tile order against the views and the pass's tile width.
-int check_order(const uint32_t* order, long long len, const dvr_view* views, int n_views, int pass,
+int check_order(const uint32_t* order, long long len, const dvr_view* views, int n_views, int tw,
                 const char* who)
 {
     if (!order) return DVR_OK;
     if (!aligned(order, 4)) return fail(DVR_ERR_ARG, "%s: tile_order is not 4-byte aligned", who);
-    const long long need = pass_tiles(views, n_views, pass);
+    const long long need = pass_tiles(views, n_views, tw);
     if (len != need)
         return fail(DVR_ERR_ARG, "%s: tile_order has %lld entries, these views have %lld tiles at tile width %d "
-                    "(made for other views or another width?)", who, len, need, g_tile_w[pass].load());
+                    "(made for other views or another width?)", who, len, need, tw);
     return DVR_OK;
 }
 
@@ -219,7 +219,10 @@ int forward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
     Common c;
     int rc = check_common(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, c);
     if (rc) return rc;
-    rc = check_order(tile_order, tile_order_len, views, n_views, DVR_PASS_FORWARD, "dvr_forward");
+    // the tile width is read once: the order's length check and the launches
+    // must agree even if another thread changes it meanwhile
+    const int tw = g_tile_w[DVR_PASS_FORWARD].load(std::memory_order_relaxed);
+    rc = check_order(tile_order, tile_order_len, views, n_views, tw, "dvr_forward");
     if (rc) return rc;
     if (!image) return fail(DVR_ERR_ARG, "image is NULL");
     if (!aligned(image, c.channels == 4 ? 16 : 4)) return fail(DVR_ERR_ARG, "image is not 16-byte aligned");
@@ -228,7 +231,7 @@ int forward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
     long long order_off = 0;
     for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
         const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
-        pack(p, DVR_PASS_FORWARD, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
+        pack(p, tw, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
              step_voxels);
         if (tile_order) {
             p.order = tile_order + order_off;
@@ -269,7 +272,8 @@ int backward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf
                                   (flags & DVR_FLAG_TF_IMMEDIATE)))
         return fail(DVR_ERR_UNSUPPORTED, "inversion ablations: emission-absorption, FP32 volume, delayed TF "
                     "gradient only");
-    rc = check_order(tile_order, tile_order_len, views, n_views, DVR_PASS_ADJOINT, "dvr_backward");
+    const int tw = g_tile_w[DVR_PASS_ADJOINT].load(std::memory_order_relaxed);   // read once (see forward_impl)
+    rc = check_order(tile_order, tile_order_len, views, n_views, tw, "dvr_backward");
     if (rc) return rc;
     if (!aux || !grad_image) return fail(DVR_ERR_ARG, "aux and grad_image are required");
     if (!aligned(aux, 8)) return fail(DVR_ERR_ARG, "aux is not 8-byte aligned");
@@ -305,7 +309,7 @@ int backward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf
     long long order_off = 0;
     for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
         const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
-        pack(p, DVR_PASS_ADJOINT, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
+        pack(p, tw, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
              step_voxels);
         p.queue = reinterpret_cast<unsigned*>(static_cast<char*>(workspace)
                                               + (size_t)(v0 / dvr::kMaxViewsPerLaunch) * kQueueStride);
@@ -430,9 +434,9 @@ int64_t dvr_tile_order(const dvr_view* views, int32_t n_views, int32_t pass, uin
     if (max_launch_tiles(views, n_views) > 0x7fffffffll)
         return fail(DVR_ERR_ARG, "more than 2^31 - 1 ray tiles in one launch of up to %d views",
                     dvr::kMaxViewsPerLaunch);
-    const long long total = pass_tiles(views, n_views, pass);
-    if (!order || capacity < total) return total;
     const int tw = g_tile_w[pass].load(std::memory_order_relaxed), th = 32 / tw;
+    const long long total = pass_tiles(views, n_views, tw);
+    if (!order || capacity < total) return total;
     std::vector<std::pair<long long, uint32_t>> key;
     long long out = 0;
     for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
@@ -538,7 +542,7 @@ int dvr_forward_tangent(const dvr_volume* volumes, int32_t n_volumes, const dvr_
     dvr::Params p;
     for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
         const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
-        pack(p, DVR_PASS_FORWARD, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
+        pack(p, g_tile_w[DVR_PASS_FORWARD].load(std::memory_order_relaxed), volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
              step_voxels);
         p.image = image;
         cudaError_t e = dvr::launch_tangent(p, model, c.dtype, tangent, (cudaStream_t)stream);
