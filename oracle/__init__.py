@@ -288,6 +288,30 @@ def volume_prior(volume):
     return loss, grad
 
 
+def opacity_entropy(alpha, a_min=1e-12):
+    """Opacity entropy of one view (Sec. 5.1, the viewpoint-selection
+    objective) and its gradient, binary64. Over the view's N pixels,
+    p_i = A_i / sum_j A_j and H = -(1 / log2 N) sum_i p_i log2 p_i with
+    0 log 0 = 0 (the minus sign: the paper prints H without it but reports a
+    best value of 1.72 > 0, and the normalised entropy lies in [0, 1]).
+    Written out: H = -(sum_i p_i ln p_i) / ln N. Its derivative is the
+    quotient rule applied to p_i: dH/dA_k = -(ln p_k - sum_i p_i ln p_i) /
+    (S ln N) with S = sum_j A_j; at A_k = 0, where ln p_k is -inf, the
+    logarithm is taken at a_min (pixels no ray lights). Returns (H, dH/dA)."""
+    a = np.asarray(alpha, dtype=np.float64).reshape(-1)
+    n = a.size
+    S = a.sum()
+    if n < 2 or S <= 0.0:
+        return 0.0, np.zeros_like(a)
+    p = a / S
+    plogp = np.where(a > 0, p * np.log(np.where(a > 0, p, 1.0)), 0.0)
+    E = plogp.sum()
+    H = -E / np.log(n)
+    lnp = np.log(np.maximum(a, a_min) / S)
+    grad = -(lnp - E) / (S * np.log(n))
+    return float(H), grad
+
+
 def tf_prior(tf):
     """Eq. tf-loss prior without its normalisation: sum_c sum_r
     (T[r+1][c] - T[r][c])^2, and its gradient."""

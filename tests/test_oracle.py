@@ -480,3 +480,39 @@ def test_resample_reproduces_linear_fields():
     Z9, Y9, X9 = np.meshgrid(xs9, xs9, xs9, indexing="ij")
     np.testing.assert_allclose(up, 0.3 + 1.1 * X9 - 0.7 * Y9 + 0.4 * Z9, atol=1e-13)
     np.testing.assert_allclose(oracle.resample(v, v.shape), v, atol=1e-14)
+
+
+# ------------------------------------------------------- opacity entropy (Sec. 5.1)
+def test_opacity_entropy_extremes():
+    """Normalised entropy of the alpha channel: 1 for a uniform opacity, 0
+    when one pixel holds all of it, and in between otherwise."""
+    H, _ = oracle.opacity_entropy(np.full(64, 0.37))
+    assert abs(H - 1.0) < 1e-14
+    a = np.zeros(64)
+    a[17] = 0.8
+    H, _ = oracle.opacity_entropy(a)
+    assert H == 0.0
+    a[:8] = 0.5                                 # 9 lit pixels, not all equal
+    H, _ = oracle.opacity_entropy(a)
+    assert 0.0 < H < np.log(9) / np.log(64)
+
+
+def test_opacity_entropy_gradient():
+    """The gradient matches central differences at lit pixels, and since H
+    does not change when every opacity is scaled by the same factor, Euler's
+    identity sum_k A_k dH/dA_k = 0 holds."""
+    rng = np.random.default_rng(7)
+    a = rng.uniform(0.05, 0.95, 40)
+    H, g = oracle.opacity_entropy(a)
+    assert abs(float((a * g).sum())) < 1e-13
+    h = 1e-6
+    for k in (0, 13, 39):
+        ap, am = a.copy(), a.copy()
+        ap[k] += h
+        am[k] -= h
+        fd = (oracle.opacity_entropy(ap)[0] - oracle.opacity_entropy(am)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-7 * max(1.0, abs(g[k])), (k, fd, g[k])
+    # an unlit pixel: lighting it raises the entropy (logarithm at a_min)
+    a[5] = 0.0
+    _, g = oracle.opacity_entropy(a)
+    assert g[5] > 0 and np.isfinite(g[5])
