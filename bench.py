@@ -288,7 +288,8 @@ class Workload:
                     aux=self.aux, sample_count=self.count)
         torch.cuda.synchronize()
         self.samples_per_pass = int(self.count.item())
-        self.launches_per_step = 3 + (2 if self.orbit else 0)
+        # our kernels per step: forward, loss (the entropy loss is two), adjoint, orbit and its adjoint
+        self.launches_per_step = 3 + (1 if w.loss == "entropy" else 0) + (2 if self.orbit else 0)
 
     def zero(self):
         self.small.zero_()
@@ -309,7 +310,10 @@ class Workload:
         dvr.forward(None, None, None, None, self.eye, w.step_voxels, scene=sc, image=self.image, aux=self.aux)
         if ev:
             ev[1].record()
-        dvr.loss_l2(self.image, self.target, 1.0 / self.image.numel(), grad_image=self.gimg, loss=self.loss)
+        if w.loss == "entropy":
+            dvr.loss_entropy(self.image, sc, 1.0 / len(w.views), grad_image=self.gimg, loss=self.loss)
+        else:
+            dvr.loss_l2(self.image, self.target, 1.0 / self.image.numel(), grad_image=self.gimg, loss=self.loss)
         if ev:
             ev[2].record()
         dvr.backward(None, None, None, None, self.eye, w.step_voxels, self.aux, self.gimg, scene=sc,
@@ -333,6 +337,7 @@ class Workload:
             "step_voxels": w.step_voxels,
             "gradients": list(w.grads),
             "samples_per_pass": self.samples_per_pass,
+            "loss": {"l2": "L2 against the target image", "entropy": "opacity entropy (Sec. 5.1), maximised"}[w.loss],
             "note": w.note,
         }
 

@@ -73,7 +73,7 @@
 extern "C" {
 #endif
 
-#define DVR_ABI_VERSION 6
+#define DVR_ABI_VERSION 7
 
 /* exported from the shared library (which hides everything else) */
 #if defined(__GNUC__)
@@ -373,6 +373,28 @@ DVR_API int dvr_tangent_contract(const dvr_view* views, int32_t n_views, int32_t
  */
 DVR_API int dvr_loss_l2(const float* image, const float* target, int64_t n, float scale,
                 float* grad_image, float* loss, void* stream);
+
+/*
+ * Opacity-entropy loss of Sec. 5.1 (the viewpoint-selection objective) and
+ * its gradient, the seed of Alg. 2. For each view, over its N pixels of
+ * opacity A_i (the last of `channels`): S = sum A_i, T = sum A_i ln A_i
+ * (0 ln 0 = 0), p_i = A_i / S and the normalised entropy
+ * H = -(1 / log2 N) sum p_i log2 p_i = -(T / S - ln S) / ln N, in [0, 1]
+ * (the paper prints H without the minus sign but reports positive values).
+ * The entropy is maximised: loss += scale * sum over views of (-H), and
+ * grad_image = scale * (ln A_k - T / S) / (S ln N) in the opacity channel
+ * (ln A_k taken at 1e-12 where A_k = 0), 0 in the colour channels. Views
+ * with N < 2 or S = 0 contribute nothing.
+ *
+ * image        device float[P][channels], channels 1 or 4 (as dvr_forward)
+ * views        host array as for dvr_forward (sizes and pixel offsets)
+ * grad_image   device float[P][channels], overwritten for the views' pixels
+ * loss         device float[1] or NULL
+ * stats        device double[n_views][2], caller-owned scratch: receives
+ *              (S, T) of each view
+ */
+DVR_API int dvr_loss_entropy(const float* image, int32_t channels, const dvr_view* views, int32_t n_views,
+                             float scale, float* grad_image, float* loss, double* stats, void* stream);
 
 /*
  * L1 image loss of Eq. tf-loss and its subgradient:

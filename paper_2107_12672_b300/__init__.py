@@ -10,7 +10,8 @@ from . import synthetic
 from .synthetic import View
 
 __all__ = ["synthetic", "View", "forward", "backward", "forward_tangent", "tangent_contract", "render", "loss_l2", "orbit_eye",
-           "orbit_eye_backward", "orbit_camera", "Scene", "split_views", "checkpoint_slots", "lib"]
+           "orbit_eye_backward", "orbit_camera", "Scene", "split_views", "checkpoint_slots",
+           "loss_entropy", "lib"]
 
 
 def __getattr__(name):
@@ -18,7 +19,8 @@ def __getattr__(name):
     # the input generators can be imported without CUDA
     if name in ("forward", "backward", "forward_tangent", "tangent_contract", "render", "loss_l2", "loss_l1",
                 "tf_prior", "volume_prior", "resample", "volume_smoothness", "orbit_eye",
-                "orbit_eye_backward", "orbit_camera", "Scene", "split_views", "MODELS", "checkpoint_slots"):
+                "orbit_eye_backward", "orbit_camera", "Scene", "split_views", "MODELS", "checkpoint_slots",
+                "loss_entropy"):
         from . import binding as _r
         return getattr(_r, name)
     if name == "lib":

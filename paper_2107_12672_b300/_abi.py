@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # kernel variants); by default the in-tree build is loaded.
 LIB_PATH = os.environ.get("DVR_LIBRARY") or os.path.join(_HERE, "_lib", "libdvr.so")
 
-ABI_VERSION = 6          # DVR_ABI_VERSION of the header these argtypes follow
+ABI_VERSION = 7          # DVR_ABI_VERSION of the header these argtypes follow
 DVR_OK = 0
 DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
 DVR_ABSORPTION, DVR_EMISSION_ABSORPTION, DVR_COLOR_VOLUME = 0, 1, 2
@@ -31,7 +31,8 @@ SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_set_tile_width", "dvr_get_t
            "dvr_backward_workspace_bytes", "dvr_forward_tangent",
            "dvr_tangent_contract", "dvr_loss_l2", "dvr_loss_l1", "dvr_tf_prior", "dvr_volume_prior",
            "dvr_resample", "dvr_orbit_eye", "dvr_orbit_eye_backward", "dvr_backward_noalloc", "dvr_probe",
-           "dvr_tile_order", "dvr_checkpoint_slots", "dvr_forward_checkpointed", "dvr_backward_checkpointed")
+           "dvr_tile_order", "dvr_checkpoint_slots", "dvr_forward_checkpointed", "dvr_backward_checkpointed",
+           "dvr_loss_entropy")
 
 
 class DvrVolume(ctypes.Structure):
@@ -89,6 +90,8 @@ def load() -> ctypes.CDLL:
         lib.dvr_backward_checkpointed.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, P, P, U32, I32, P, I32,
                                                   P, ctypes.c_size_t, P]
         lib.dvr_backward_checkpointed.restype = ctypes.c_int
+        lib.dvr_loss_entropy.argtypes = [P, I32, P, I32, F, P, P, P, P]
+        lib.dvr_loss_entropy.restype = ctypes.c_int
         lib.dvr_tile_order.argtypes = [P, I32, I32, P, I64]
         lib.dvr_tile_order.restype = ctypes.c_int64
         lib.dvr_backward_workspace_bytes.argtypes = [I32]

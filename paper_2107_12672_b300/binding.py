@@ -264,6 +264,20 @@ def loss_l2(image, target, scale=1.0, *, grad_image=None, loss=None, stream=None
     return grad_image
 
 
+def loss_entropy(image, scene: "Scene", scale=1.0, *, grad_image=None, loss=None, stream=None):
+    """Opacity-entropy loss of Sec. 5.1 (maximised): loss += scale * sum over
+    the scene's views of -H, with H the normalised entropy of the view's
+    opacities; returns grad_image (dL/d(image), zero in colour channels)."""
+    if grad_image is None:
+        grad_image = torch.empty_like(image)
+    stats = torch.empty((len(scene.views), 2), dtype=torch.float64, device=image.device)
+    rc = _abi.load().dvr_loss_entropy(_ptr(image), int(image.shape[1]), scene.view_desc, len(scene.views),
+                                      float(scale), _ptr(grad_image), _ptr(loss), _ptr(stats),
+                                      _stream_ptr(stream))
+    _abi.check(rc, "dvr_loss_entropy")
+    return grad_image
+
+
 def loss_l1(image, target, scale=1.0, *, grad_image=None, loss=None, stream=None):
     """L1 loss of Eq. tf-loss: loss += scale*sum|x-y|, grad = scale*sign(x-y)."""
     if grad_image is None:

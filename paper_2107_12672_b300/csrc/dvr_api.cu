@@ -14,6 +14,7 @@
 
 #include "dvr.h"
 #include "dvr_launch.h"
+#include "dvr_loss.h"
 #include "dvr_probe.h"
 
 namespace {
@@ -589,6 +590,38 @@ int dvr_loss_l2(const float* image, const float* target, int64_t n, float scale,
     if (!image || !target || !grad_image) return fail(DVR_ERR_ARG, "image, target and grad_image are required");
     cudaError_t e = dvr::launch_loss_l2(image, target, n, scale, grad_image, loss, (cudaStream_t)stream);
     return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_loss_l2 launch");
+}
+
+int dvr_loss_entropy(const float* image, int32_t channels, const dvr_view* views, int32_t n_views, float scale,
+                     float* grad_image, float* loss, double* stats, void* stream)
+{
+    g_err[0] = 0;
+    if (!image || !grad_image || !stats) return fail(DVR_ERR_ARG, "dvr_loss_entropy: image, grad_image and stats are required");
+    if (channels != 1 && channels != 4) return fail(DVR_ERR_ARG, "dvr_loss_entropy: channels %d is not 1 or 4", channels);
+    if (!aligned(image, 4) || !aligned(grad_image, 4) || !aligned(stats, 8) || (loss && !aligned(loss, 4)))
+        return fail(DVR_ERR_ARG, "dvr_loss_entropy: misaligned pointer");
+    if (!views || n_views < 1 || n_views > 4096)
+        return fail(DVR_ERR_ARG, "n_views %d outside [1, 4096] or views is NULL", n_views);
+    for (int i = 0; i < n_views; ++i) {
+        if (views[i].width < 1 || views[i].height < 1 || views[i].width > 65536 || views[i].height > 65536 ||
+            (long long)views[i].width * views[i].height > 0x7fffffffll)
+            return fail(DVR_ERR_ARG, "view %d: size %d x %d outside [1, 65536] or over 2^31 - 1 pixels", i,
+                        views[i].width, views[i].height);
+        if (views[i].pixel_offset < 0) return fail(DVR_ERR_ARG, "view %d: negative pixel_offset", i);
+    }
+    cudaError_t e = cudaMemsetAsync(stats, 0, sizeof(double) * 2 * (size_t)n_views, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "dvr_loss_entropy stats");
+    dvr::EntropyViews v;
+    for (int v0 = 0; v0 < n_views; v0 += dvr::kEntropyViews) {
+        v.n = n_views - v0 < dvr::kEntropyViews ? n_views - v0 : dvr::kEntropyViews;
+        for (int i = 0; i < v.n; ++i) {
+            v.offset[i] = views[v0 + i].pixel_offset;
+            v.pixels[i] = views[v0 + i].width * views[v0 + i].height;
+        }
+        e = dvr::launch_entropy(v, image, channels, scale, grad_image, loss, stats + 2 * v0, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "dvr_loss_entropy launch");
+    }
+    return DVR_OK;
 }
 
 int dvr_loss_l1(const float* image, const float* target, int64_t n, float scale, float* grad_image,

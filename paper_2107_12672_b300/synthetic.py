@@ -177,6 +177,7 @@ class Workload:
     grads: tuple                    # subset of ("volume", "tf", "camera")
     target: dict = field(default_factory=dict)  # what the loss compares to
     note: str = ""
+    loss: str = "l2"                # "l2" against the target, or "entropy" (opacity entropy, maximised)
 
 
 def _orbit_params(rng, count, distance):
@@ -250,7 +251,9 @@ def workload(name: str, scale: float = 1.0) -> Workload:
         return Workload(name, "emission_absorption", [], tf, views, eye, None, 0.25,
                         ("volume", "tf", "camera"), target={"n": n},
                         note="1024^3 FP16 value noise plus 32 Gaussian blobs, 32-point TF, "
-                             "32 views 2048^2, step 0.25 voxel (~4000 steps on axis-aligned rays)")
+                             "32 views 2048^2, step 0.25 voxel (~4000 steps on axis-aligned rays), "
+                             "opacity-entropy loss",
+                        loss="entropy")
     raise KeyError(name)
 
 

@@ -269,3 +269,12 @@ def test_checkpoint_slots_and_argument_errors():
                                                       16, 0.5, 64, 64, None, 128, None, None, flags, 16, 8192, 14,
                                                       4096, 256, None)
     assert bwd(0) == -1 and b"alpha" in lib.dvr_last_error()
+
+
+@pytest.mark.parametrize("channels,stats", [(3, 8192), (4, None), (1, 8196)])
+def test_loss_entropy_argument_errors(channels, stats):
+    """dvr_loss_entropy refuses channel counts other than 1 and 4, a missing
+    or misaligned stats array, before any CUDA call."""
+    lib = _abi.load()
+    rc = lib.dvr_loss_entropy(4096, channels, _one_view(), 1, 1.0, 4096, None, stats, None)
+    assert rc == -1 and lib.dvr_last_error()

@@ -679,3 +679,32 @@ def test_tile_order_across_launches():
     assert int((ref_e.abs().sum(1) > 0).sum()) > n // 2
     assert_close(g["eye"].cpu().numpy(), ref_e.cpu().numpy(), 1e-5, "grad eye")
     assert_close(g["step"].cpu().numpy(), ref_s.cpu().numpy(), 1e-5, "grad step")
+
+
+# ------------------------------------------------ opacity entropy (Sec. 5.1)
+@pytest.mark.parametrize("channels", [1, 4])
+def test_loss_entropy_matches_oracle(channels):
+    """Per view (uneven sizes, one with unlit pixels, one of a single pixel):
+    the loss scale * sum(-H) and the opacity gradient match the oracle's
+    binary64 definition; the colour channels of the gradient are zero."""
+    rng = np.random.default_rng(11 + channels)
+    views = [syn.View(37, 23), syn.View(1, 1), syn.View(64, 50), syn.View(9, 4)]
+    sc_views = dvr.Scene.make([to_dev(np.zeros((4, 4, 4), np.float32))], None, "absorption", views)
+    P = sc_views.pixels
+    img = rng.uniform(0.0, 1.0, (P, channels)).astype(np.float32)
+    off = sc_views.offsets
+    img[off[2]:off[2] + 500, channels - 1] = 0.0          # unlit pixels
+    scale = 0.7
+    loss = torch.zeros(1, device="cuda")
+    g = dvr.loss_entropy(to_dev(img), sc_views, scale, loss=loss)
+    torch.cuda.synchronize()
+    g = g.cpu().numpy()
+    ref_loss, ref_g = 0.0, np.zeros((P, channels))
+    for k, v in enumerate(views):
+        n = v.width * v.height
+        H, dH = oracle.opacity_entropy(img[off[k]:off[k] + n, channels - 1].astype(np.float64))
+        ref_loss += -scale * H
+        ref_g[off[k]:off[k] + n, channels - 1] = -scale * dH
+    assert abs(float(loss.item()) - ref_loss) <= 1e-5 * max(1.0, abs(ref_loss))
+    assert np.all(g[:, :channels - 1] == 0.0)
+    assert_close(g, ref_g, 1e-5, "entropy gradient")
