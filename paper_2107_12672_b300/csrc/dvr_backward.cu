@@ -8,7 +8,12 @@
 // of the blend of Sec. 4.4 (Eq. inv-blend-forward) carried out on the
 // logarithm of the transmittance, where it neither cancels nor underflows.
 // Only the accumulated opacity is needed by the adjoint of the blend; the
-// colour adjoint is constant along the ray (Eq. adj-blend-forward).
+// colour adjoint is constant along the ray (Eq. adj-blend-forward). With
+// T_i = 1 - A_i and T^_i the adjoint of T_i, the blend adjoint is carried
+// scaled by the transmittance: the sample's weight (1 - A_i) alpha_i is
+// T_i - T_{i+1}, U_i = T_i T^_i obeys U_i = U_{i+1} + (T_i - T_{i+1})
+// rgb_i . C^, and tau^_i = dt (T_{i+1} rgb_i . C^ - U_{i+1}): Alg. 2's
+// updates multiplied through by T_i, with no alpha and no division.
 //
 // Gradients (all "+=", Alg. 2):
 //  - TF ("adjoint-delayed", Sec. 5.2): for R <= 32 every lane owns a copy
@@ -95,7 +100,7 @@ __device__ __forceinline__ void cell_run_flush(float* g, bool v16, uint32_t nvox
 }
 
 template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV = kInvDepth>
-__global__ void __launch_bounds__(kWarps * 32, DVR_BWD_MIN_BLOCKS)
+__global__ void __launch_bounds__(kWarps * 32, GVOL ? DVR_BWD_MIN_BLOCKS : DVR_BWD_QUEUE_MIN_BLOCKS)
 backward_kernel(const __grid_constant__ Params p)
 {
     constexpr bool EA = MODEL == DVR_EMISSION_ABSORPTION;
@@ -161,6 +166,13 @@ backward_kernel(const __grid_constant__ Params p)
             sh = s2.x; sl = s2.y;
         }
         float Th = -Ah;                         // adjoint of the transmittance 1 - A
+        // optical-depth recovery: T_{i+1} = 1 - A_{i+1} of the sample after
+        // the current one, and U = T_{i+1} T^_{i+1}
+        float Tn = 0.f, U = 0.f;
+        if (EA && INV == kInvDepth) {
+            Tn = transmittance(sh, sl);
+            U = Tn * Th;
+        }
         // ablations: accumulated opacity A_{i+1} carried as in the paper,
         // starting from the binary32 image opacity (the value dvr_forward
         // wrote) or, with the binary64 guard, from the optical depth
@@ -218,44 +230,53 @@ backward_kernel(const __grid_constant__ Params p)
                 TFSample s;
                 tf_lookup(tf_s, p.R, d, tfc, s);
                 const float x = G.dt * s.c.w;
-                const float em = neg_expm1_br(x);
-                const float alpha = -em;
-                const float ea = 1.f + em;            // 1 - alpha
-                float T;                              // 1 - A_i
-                if (INV == kInvDepth) {
-                    float s2, err;
-                    two_sum(sh, -x, s2, err);         // S_i = S_{i+1} - dt tau_i
-                    sh = s2;
-                    sl += err;
-                    T = expf(-(sh + sl));
-                } else if (INV == kInvAlpha32) {
-                    Af = (alpha - Af) / (alpha - 1.f);  // Eq. inv-blend-forward, binary32
-                    if (i == ck_i) {
-                        Af = 1.f - ck[ck_m];
-                        --ck_m;
-                        ck_i -= p.ckpt_k;
-                    }
-                    T = 1.f - Af;
-                } else {
-                    if (Ad > 0.99) {
-                        Ad = ((double)alpha - Ad) / ((double)alpha - 1.0);
-                    } else {
-                        Ad = (double)((alpha - (float)Ad) / (alpha - 1.f));
-                    }
-                    if (i == ck_i) {
-                        Ad = 1.0 - (double)ck[ck_m];
-                        --ck_m;
-                        ck_i -= p.ckpt_k;
-                    }
-                    T = (float)(1.0 - Ad);
-                }
                 const float cC = fmaf(s.c.z, Ch2, fmaf(s.c.y, Ch1, s.c.x * Ch0));
-                const float Ta = T * alpha;
-                const float a_hat = T * (cC - Th);     // adjoint of alpha_i
-                Th = fmaf(alpha, cC, ea * Th);
-                const float tau_hat = a_hat * G.dt * ea;
-                if (POS) dt_hat = fmaf(a_hat * s.c.w, ea, dt_hat);
-                const float h0 = Ta * Ch0, h1 = Ta * Ch1, h2 = Ta * Ch2;   // rgb^
+                float wgt, tau_hat;                   // (1 - A_i) alpha_i; adjoint of tau_i
+                if (INV == kInvDepth) {
+                    // with T_i = exp(-S_i): (1 - A_i) alpha_i = T_i - T_{i+1}, and the
+                    // transmittance adjoint enters only as U = T_{i+1} T^_{i+1}, so the
+                    // sample needs no alpha and no division
+                    depth_add(sh, sl, -x);            // S_i = S_{i+1} - dt tau_i
+                    const float T = transmittance(sh, sl);   // 1 - A_i
+                    wgt = T - Tn;
+                    const float q = fmaf(Tn, cC, -U);   // (1 - A_{i+1}) (rgb . C^ - T^_{i+1})
+                    tau_hat = G.dt * q;
+                    if (POS) dt_hat = fmaf(s.c.w, q, dt_hat);
+                    U = fmaf(wgt, cC, U);             // U_i = U_{i+1} + (1 - A_i) alpha_i rgb . C^
+                    Tn = T;
+                } else {
+                    const float em = neg_expm1_br(x);
+                    const float alpha = -em;
+                    const float ea = 1.f + em;        // 1 - alpha
+                    float T;                          // 1 - A_i
+                    if (INV == kInvAlpha32) {
+                        Af = (alpha - Af) / (alpha - 1.f);  // Eq. inv-blend-forward, binary32
+                        if (i == ck_i) {
+                            Af = 1.f - ck[ck_m];
+                            --ck_m;
+                            ck_i -= p.ckpt_k;
+                        }
+                        T = 1.f - Af;
+                    } else {
+                        if (Ad > 0.99) {
+                            Ad = ((double)alpha - Ad) / ((double)alpha - 1.0);
+                        } else {
+                            Ad = (double)((alpha - (float)Ad) / (alpha - 1.f));
+                        }
+                        if (i == ck_i) {
+                            Ad = 1.0 - (double)ck[ck_m];
+                            --ck_m;
+                            ck_i -= p.ckpt_k;
+                        }
+                        T = (float)(1.0 - Ad);
+                    }
+                    wgt = T * alpha;
+                    const float a_hat = T * (cC - Th);     // adjoint of alpha_i
+                    Th = fmaf(alpha, cC, ea * Th);
+                    tau_hat = a_hat * G.dt * ea;
+                    if (POS) dt_hat = fmaf(a_hat * s.c.w, ea, dt_hat);
+                }
+                const float h0 = wgt * Ch0, h1 = wgt * Ch1, h2 = wgt * Ch2;   // rgb^
                 if (TFM == kTFPrivate) {
                     // the lane's own copy: plain adds, no two lanes share a
                     // bank (measured faster than shared-memory reductions)

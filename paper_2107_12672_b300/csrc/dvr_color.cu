@@ -137,17 +137,13 @@ forward_color_kernel(const __grid_constant__ Params p)
             const Cell4 c = nxt;
             fetch4<VT>(vol, G, m, i + 1, nxt);
             const float4 s = cell4_value(c);
-            const float x = G.dt * s.w;
-            const float em = neg_expm1_sel(x);
-            const float wgt = -T * em;
+            depth_add(sh, sl, G.dt * s.w);
+            const float Tn = transmittance(sh, sl);
+            const float wgt = T - Tn;                  // (1 - A_i) alpha_i
             C0 = fmaf(wgt, s.x, C0);
             C1 = fmaf(wgt, s.y, C1);
             C2 = fmaf(wgt, s.z, C2);
-            T = fmaf(T, em, T);
-            float s2, err;
-            two_sum(sh, x, s2, err);
-            sh = s2;
-            sl += err;
+            T = Tn;
         }
         if (valid) {
             const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
@@ -200,7 +196,8 @@ backward_color_kernel(const __grid_constant__ Params p)
         const float2 s2 = __ldg(reinterpret_cast<const float2*>(p.aux) + pix);
         sh = s2.x; sl = s2.y;
     }
-    float Th = -Ah;
+    float Tn = transmittance(sh, sl);           // 1 - A_{i+1}
+    float U = -Tn * Ah;
     float gs[3] = {0.f, 0.f, 0.f}, gi[3] = {0.f, 0.f, 0.f};
     float dt_hat = 0.f;
     const uint32_t sy = (uint32_t)G.n[0], sz = sy * (uint32_t)G.n[1];
@@ -212,21 +209,18 @@ backward_color_kernel(const __grid_constant__ Params p)
         const Cell4 c = nxt;
         fetch4<VT>(vol, G, m, i - 1, nxt);
         const float4 s = cell4_value(c);
-        const float x = G.dt * s.w;
-        const float em = neg_expm1_br(x);
-        const float alpha = -em;
-        const float ea = 1.f + em;
-        float s2, err;
-        two_sum(sh, -x, s2, err);
-        sh = s2;
-        sl += err;
-        const float T = expf(-(sh + sl));
+        // the emission-absorption adjoint in the transmittance-difference
+        // form of the TF kernels: (1 - A_i) alpha_i = T_i - T_{i+1},
+        // U = T_{i+1} T^_{i+1}
+        depth_add(sh, sl, -G.dt * s.w);         // S_i
+        const float T = transmittance(sh, sl);
+        const float wgt = T - Tn;
         const float cC = fmaf(s.z, Ch2, fmaf(s.y, Ch1, s.x * Ch0));
-        const float Ta = T * alpha;
-        const float a_hat = T * (cC - Th);
-        Th = fmaf(alpha, cC, ea * Th);
-        const float4 ch = make_float4(Ta * Ch0, Ta * Ch1, Ta * Ch2, a_hat * G.dt * ea);   // channel adjoints
-        if (POS) dt_hat = fmaf(a_hat * s.w, ea, dt_hat);
+        const float q = fmaf(Tn, cC, -U);
+        U = fmaf(wgt, cC, U);
+        Tn = T;
+        const float4 ch = make_float4(wgt * Ch0, wgt * Ch1, wgt * Ch2, G.dt * q);   // channel adjoints
+        if (POS) dt_hat = fmaf(s.w, q, dt_hat);
         if (GVOL) {
             const float a0 = 1.f - c.fz, a1 = c.fz;
             const float w[8] = {a0 * (1.f - c.fy) * (1.f - c.fx), a0 * (1.f - c.fy) * c.fx,

@@ -29,6 +29,11 @@ constexpr int kMaxTF = 1024;         // transfer-function rows staged in shared 
 #ifndef DVR_BWD_MIN_BLOCKS
 #define DVR_BWD_MIN_BLOCKS 1
 #endif
+// the adjoint without a volume gradient (tile queue): 3 blocks of 4 warps
+// per SM, at most 168 registers a thread
+#ifndef DVR_BWD_QUEUE_MIN_BLOCKS
+#define DVR_BWD_QUEUE_MIN_BLOCKS 3
+#endif
 
 struct VolumeDesc {
     const void* data;
@@ -105,14 +110,12 @@ __device__ __forceinline__ float2 p2sub(float2 a, float2 b)
 __device__ __forceinline__ float2 p2dup(float a) { return make_float2(a, a); }
 
 // expm1(-x), the negated opacity -alpha of a segment with optical depth x
-// (Sec. 3.1, alpha = 1 - exp(-dt tau)). For |x| <= 1/8 the Taylor series of
+// (Sec. 3.1, alpha = 1 - exp(-dt tau)), for the adjoint's alpha-form
+// inversion ablations (the other passes blend with differences of
+// transmittances and need no alpha). For |x| <= 1/8 the Taylor series of
 // e^y - 1 at y = -x to degree 7 in Horner form (truncation below 2^-33
 // relative, far under one binary32 ulp); beyond, exp(-x) - 1 with CUDA's
-// expf (exact subtraction there, within ~1e-6 relative). Two forms with the
-// same value: a select for the forward marches, whose loop bodies schedule
-// best without a branch, and a branch for the adjoints, which then skip the
-// unused expf. Every kernel takes alpha from one of them, so forward,
-// adjoint, forward-mode and colour-volume passes see the same opacities.
+// expf (exact subtraction there, within ~1e-6 relative).
 __device__ __forceinline__ float expm1_taylor(float y)
 {
     float q = fmaf(y, 1.f / 5040.f, 1.f / 720.f);
@@ -125,13 +128,6 @@ __device__ __forceinline__ float expm1_taylor(float y)
 }
 
 static __device__ __noinline__ float neg_expm1_wide(float x) { return expf(-x) - 1.f; }
-
-__device__ __forceinline__ float neg_expm1_sel(float x)
-{
-    const float t = expm1_taylor(-x);
-    const float w = expf(-x) - 1.f;
-    return fabsf(x) <= 0.125f ? t : w;
-}
 
 __device__ __forceinline__ float neg_expm1_br(float x)
 {
@@ -264,6 +260,18 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
+
+// S += x on the optical depth carried as the unevaluated pair (sh, sl).
+__device__ __forceinline__ void depth_add(float& sh, float& sl, float x)
+{
+    float s2, err;
+    two_sum(sh, x, s2, err);
+    sh = s2;
+    sl += err;
+}
+
+// Transmittance 1 - A = exp(-S) of the optical depth (sh, sl).
+__device__ __forceinline__ float transmittance(float sh, float sl) { return expf(-(sh + sl)); }
 
 __device__ __forceinline__ void make_march(const Ray& R, const Grid& g, March& m)
 {

@@ -1,10 +1,13 @@
 // Forward pass (Alg. 1): one thread per ray, one warp per 8 x 4 pixel tile,
-// all views of the launch in one grid, tiles issued centre-out. For each sample: position, trilinear
+// all views of the launch in one grid. For each sample: position, trilinear
 // density, TF lookup from shared memory, Beer-Lambert opacity and
 // front-to-back blending (Eq. blend-forward) in registers. The ray's optical
 // depth S = sum dt tau_i is accumulated as an unevaluated float pair and
 // stored, so the adjoint can recover every transmittance exp(-S_i) without
-// a per-step record (Sec. 4.4).
+// a per-step record (Sec. 4.4). The blend weight (1 - A_i) alpha_i is taken
+// as the difference of consecutive transmittances exp(-S_i) - exp(-S_{i+1}),
+// the same value as the product form, with one exponential per sample; its
+// rounding errors telescope in the colour sum.
 #include "dvr_device.cuh"
 #include "dvr_launch.h"
 
@@ -84,24 +87,19 @@ forward_kernel(const __grid_constant__ Params p)
             fetch_sample_reuse<VT>(vol, G, m, i + 2, n1.c.base, n2);
             const Cell& c = cur.c;
             const float d = cell_value(c);
-            float x;
             if (MODEL == DVR_EMISSION_ABSORPTION) {
                 TFSample s;
                 tf_lookup(tf_s, p.R, d, tfc, s);
-                x = G.dt * s.c.w;
-                const float em = neg_expm1_sel(x);        // -alpha_i
-                const float wgt = -T * em;            // (1 - A_i) alpha_i
+                depth_add(sh, sl, G.dt * s.c.w);      // S_{i+1} = S_i + dt tau_i
+                const float Tn = transmittance(sh, sl);   // 1 - A_{i+1}
+                const float wgt = T - Tn;             // (1 - A_i) alpha_i
                 C0 = fmaf(wgt, s.c.x, C0);
                 C1 = fmaf(wgt, s.c.y, C1);
                 C2 = fmaf(wgt, s.c.z, C2);
-                T = fmaf(T, em, T);                   // (1 - A_{i+1})
+                T = Tn;
             } else {
-                x = G.dt * d;
+                depth_add(sh, sl, G.dt * d);
             }
-            float s2, err;
-            two_sum(sh, x, s2, err);
-            sh = s2;
-            sl += err;
         }
         if (valid) {
             const long long pix = vw.pixel_offset + (long long)py * vw.width + px;

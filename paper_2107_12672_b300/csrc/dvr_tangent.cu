@@ -158,39 +158,34 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
             for (int a = 0; a < 3; ++a) acc = fmaf(dg[a], fmaf(ti, dw[a][k], dxo[a][k]), acc);
             dd[k] = acc * G.inv_h;
         }
-        float x;
         if (EA) {
             TFSample s;
             tf_lookup(tf_s, p.R, d, tfc, s);
-            x = G.dt * s.c.w;
-            const float em = neg_expm1_sel(x);
-            const float alpha = -em, ea = 1.f + em;
+            depth_add(sh, sl, G.dt * s.c.w);         // S_{i+1}
+            const float Tn = transmittance(sh, sl);  // the forward kernel's roundings
+            const float wgt = T - Tn;
             const float sl_ = s.slope ? Rm1 : 0.f;
-            const float wgt = -T * em;               // the forward kernel's roundings
-
+            const float dtau = G.dt * s.dc.w;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const float dk = sl_ * dd[k];        // d(segment position)/d(eye)
-                const float dalpha = ea * G.dt * s.dc.w * dk;
-                const float dwgt = fmaf(dT[k], alpha, T * dalpha);
+                dS[k] = fmaf(dtau, dk, dS[k]);       // d S_{i+1} / d(eye)
+                const float dTn = -Tn * dS[k];
+                const float dwgt = dT[k] - dTn;
                 dC[0][k] = fmaf(dwgt, s.c.x, fmaf(wgt * s.dc.x, dk, dC[0][k]));
                 dC[1][k] = fmaf(dwgt, s.c.y, fmaf(wgt * s.dc.y, dk, dC[1][k]));
                 dC[2][k] = fmaf(dwgt, s.c.z, fmaf(wgt * s.dc.z, dk, dC[2][k]));
-                dT[k] = fmaf(dT[k], ea, -T * dalpha);
+                dT[k] = dTn;
             }
             C0 = fmaf(wgt, s.c.x, C0);
             C1 = fmaf(wgt, s.c.y, C1);
             C2 = fmaf(wgt, s.c.z, C2);
-            T = fmaf(T, em, T);
+            T = Tn;
         } else {
-            x = G.dt * d;
 #pragma unroll
             for (int k = 0; k < 3; ++k) dS[k] = fmaf(G.dt, dd[k], dS[k]);
+            depth_add(sh, sl, G.dt * d);
         }
-        float s2, err;
-        two_sum(sh, x, s2, err);
-        sh = s2;
-        sl += err;
     }
     const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
     const float S = sh + sl;
