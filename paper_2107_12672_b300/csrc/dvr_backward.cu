@@ -56,10 +56,12 @@ __device__ __forceinline__ void tf_run_flush(float* rows, TFRun& r)
     for (int j = 0; j < 8; ++j) r.a[j] = 0.f;
 }
 
-// Register run of volume-gradient contributions to the 8 corners of one cell.
+// Register run of volume-gradient contributions to the 8 corners of one
+// cell, as x pairs: a[k] holds corners (0, y, z) and (1, y, z) of row
+// k = y + 2 z.
 struct CellRun {
     uint32_t base;
-    float a[8];
+    float2 a[4];
 };
 
 // Adds a to g[i] and b to g[i + 1]. With v16 (g 16-byte aligned and the
@@ -90,13 +92,13 @@ __device__ __forceinline__ void cell_run_flush(float* g, bool v16, uint32_t nvox
                                                CellRun& r)
 {
     if (r.base != 0xffffffffu) {
-        red_pair(g, v16, r.base, nvox, r.a[0], r.a[1]);
-        red_pair(g, v16, r.base + sy, nvox, r.a[2], r.a[3]);
-        red_pair(g, v16, r.base + sz, nvox, r.a[4], r.a[5]);
-        red_pair(g, v16, r.base + sz + sy, nvox, r.a[6], r.a[7]);
+        red_pair(g, v16, r.base, nvox, r.a[0].x, r.a[0].y);
+        red_pair(g, v16, r.base + sy, nvox, r.a[1].x, r.a[1].y);
+        red_pair(g, v16, r.base + sz, nvox, r.a[2].x, r.a[2].y);
+        red_pair(g, v16, r.base + sz + sy, nvox, r.a[3].x, r.a[3].y);
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) r.a[j] = 0.f;
+    for (int j = 0; j < 4; ++j) r.a[j] = make_float2(0.f, 0.f);
 }
 
 template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV = kInvDepth>
@@ -198,7 +200,7 @@ backward_kernel(const __grid_constant__ Params p)
         CellRun cr;
         cr.base = 0xffffffffu;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) cr.a[j] = 0.f;
+        for (int j = 0; j < 4; ++j) cr.a[j] = make_float2(0.f, 0.f);
         const uint32_t vsy = (uint32_t)G.n[0], vsz = vsy * (uint32_t)G.n[1];
         const uint32_t vnvox = vsz * (uint32_t)G.n[2];
         const bool gv16 = vd.grad_vec && ((uintptr_t)gvol & 15u) == 0;
@@ -326,18 +328,15 @@ backward_kernel(const __grid_constant__ Params p)
                     cell_run_flush(gvol, gv16, vnvox, vsy, vsz, cr);
                     cr.base = c.base;
                 }
-                const float a0 = d_hat * (1.f - c.fz), a1 = d_hat * c.fz;
-                const float b00 = a0 * (1.f - c.fy), b01 = a0 * c.fy;
-                const float b10 = a1 * (1.f - c.fy), b11 = a1 * c.fy;
-                const float ox = 1.f - c.fx;
-                cr.a[0] = fmaf(b00, ox, cr.a[0]);
-                cr.a[1] = fmaf(b00, c.fx, cr.a[1]);
-                cr.a[2] = fmaf(b01, ox, cr.a[2]);
-                cr.a[3] = fmaf(b01, c.fx, cr.a[3]);
-                cr.a[4] = fmaf(b10, ox, cr.a[4]);
-                cr.a[5] = fmaf(b10, c.fx, cr.a[5]);
-                cr.a[6] = fmaf(b11, ox, cr.a[6]);
-                cr.a[7] = fmaf(b11, c.fx, cr.a[7]);
+                // trilinear weights times d^, z then y then x, as packed pairs
+                const float2 az = p2mul(p2dup(d_hat), make_float2(1.f - c.fz, c.fz));    // (z0, z1)
+                const float2 by0 = p2mul(az, p2dup(1.f - c.fy));                        // y = 0
+                const float2 by1 = p2mul(az, p2dup(c.fy));                              // y = 1
+                const float2 wx = make_float2(1.f - c.fx, c.fx);
+                cr.a[0] = p2fma(p2dup(by0.x), wx, cr.a[0]);
+                cr.a[1] = p2fma(p2dup(by1.x), wx, cr.a[1]);
+                cr.a[2] = p2fma(p2dup(by0.y), wx, cr.a[2]);
+                cr.a[3] = p2fma(p2dup(by1.y), wx, cr.a[3]);
             }
             if (POS) {
 #pragma unroll
