@@ -56,6 +56,21 @@ __device__ __forceinline__ void tf_run_flush(float* rows, TFRun& r)
     for (int j = 0; j < 8; ++j) r.a[j] = 0.f;
 }
 
+// kTFPrivate: adds a run to the lane's own copy (plain adds, no atomics).
+__device__ __forceinline__ void tf_run_flush_private(float4* my_tfp, TFRun& r)
+{
+    if (r.k >= 0) {
+        float4* q = my_tfp + r.k * 32;
+        float4 a = q[0], b = q[32];
+        a.x += r.a[0]; a.y += r.a[1]; a.z += r.a[2]; a.w += r.a[3];
+        b.x += r.a[4]; b.y += r.a[5]; b.z += r.a[6]; b.w += r.a[7];
+        q[0] = a;
+        q[32] = b;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r.a[j] = 0.f;
+}
+
 // Register run of volume-gradient contributions to the 8 corners of one
 // cell, as x pairs: a[k] holds corners (0, y, z) and (1, y, z) of row
 // k = y + 2 z.
@@ -279,9 +294,29 @@ backward_kernel(const __grid_constant__ Params p)
                     if (POS) dt_hat = fmaf(a_hat * s.c.w, ea, dt_hat);
                 }
                 const float h0 = wgt * Ch0, h1 = wgt * Ch1, h2 = wgt * Ch2;   // rgb^
-                if (TFM == kTFPrivate) {
-                    // the lane's own copy: plain adds, no two lanes share a
-                    // bank (measured faster than shared-memory reductions)
+                if (TFM == kTFPrivate && !GVOL) {
+                    // summed in registers while the density stays in one TF
+                    // segment (on a typical march the segment changes on a
+                    // few percent of the samples), added to the lane's own
+                    // copy when it leaves: a fraction of the shared-memory
+                    // traffic of per-sample adds
+                    if (s.k != tr.k) {
+                        tf_run_flush_private(my_tfp, tr);
+                        tr.k = s.k;
+                    }
+                    const float w0 = 1.f - s.fr, w1 = s.fr;
+                    tr.a[0] = fmaf(w0, h0, tr.a[0]);
+                    tr.a[1] = fmaf(w0, h1, tr.a[1]);
+                    tr.a[2] = fmaf(w0, h2, tr.a[2]);
+                    tr.a[3] = fmaf(w0, tau_hat, tr.a[3]);
+                    tr.a[4] = fmaf(w1, h0, tr.a[4]);
+                    tr.a[5] = fmaf(w1, h1, tr.a[5]);
+                    tr.a[6] = fmaf(w1, h2, tr.a[6]);
+                    tr.a[7] = fmaf(w1, tau_hat, tr.a[7]);
+                } else if (TFM == kTFPrivate) {
+                    // the volume-gradient kernels need their registers for
+                    // the cell run: each sample adds to the lane's own copy
+                    // directly (plain adds, no two lanes share a bank)
                     const float w0 = 1.f - s.fr, w1 = s.fr;
                     float4* q = my_tfp + s.k * 32;
                     float4 a = q[0], b = q[32];
@@ -349,12 +384,26 @@ backward_kernel(const __grid_constant__ Params p)
         }
 
         if (TFM == kTFWarp) tf_run_flush(my_tfg, tr);
+        if (TFM == kTFPrivate && !GVOL) tf_run_flush_private(my_tfp, tr);
         if (GVOL) cell_run_flush(gvol, gv16, vnvox, vsy, vsz, cr);
 
         if (POS) {
             if (!EA) dt_hat *= expf(-(sh + sl));          // absorption: T_N sum_i A^ d_i
             float e_hat[3] = {0.f, 0.f, 0.f};
             if (N > 0) {
+                if (!GVOL) {
+                    // the tile-queue kernels set the ray up again for its
+                    // camera adjoint (the same operations on the same inputs,
+                    // so the same bits) so that no ray quantity occupies
+                    // registers during the march, which the TF register run
+                    // needs; the inputs pass through empty asm so that the
+                    // compiler cannot keep the first set-up alive instead.
+                    // (The volume-gradient kernels measured slower this way.)
+                    float e2[3] = {e[0], e[1], e[2]};
+                    int px2 = px, py2 = py;
+                    asm volatile("" : "+f"(e2[0]), "+f"(e2[1]), "+f"(e2[2]), "+r"(px2), "+r"(py2));
+                    ray_setup(e2, px2, py2, vw, G, R);
+                }
                 const float xo_hat[3] = {gs[0] * G.inv_h, gs[1] * G.inv_h, gs[2] * G.inv_h};
                 const float s = G.inv_h * G.dt;
                 const float w_hat[3] = {gi[0] * s, gi[1] * s, gi[2] * s};
