@@ -27,7 +27,11 @@
  *   -ext_a/2 + j*h with h = 1/(max(nx,ny,nz)-1). Densities between
  *   vertices are trilinear.
  * - Step: `step_voxels` is the sample spacing in units of h; the world
- *   step is dt = step_voxels / (max(nx,ny,nz) - 1).
+ *   step is dt = step_voxels / (max(nx,ny,nz) - 1). It must be finite and
+ *   >= 2^-10, and no ray may take 2^24 samples or more:
+ *   sqrt((nx-1)^2 + (ny-1)^2 + (nz-1)^2) / step_voxels + 2 < 2^24 for
+ *   every volume (the kernels carry the sample index as an exact binary32
+ *   integer); otherwise the calls that march return DVR_ERR_ARG.
  * - Ray (Alg. 1, f_camera): the camera of a view sits at eye[v] (world
  *   coordinates, device memory) and looks at the origin with world up +y
  *   (right vector +x when the view axis is within 2^-13 rad of y). Pixel
@@ -214,7 +218,7 @@ DVR_API const char* dvr_last_error(void);
  * model                DVR_ABSORPTION, DVR_EMISSION_ABSORPTION or DVR_COLOR_VOLUME
  * views[n_views]       host array, 1 <= n_views <= 4096
  * eye                  device float[n_views][3], camera positions
- * step_voxels          sample spacing in voxels, > 0
+ * step_voxels          sample spacing in voxels (limits under Step above)
  * image                device float[P][C], C = 1 (absorption) or 4,
  *                      P = max over views of pixel_offset + width*height
  * aux                  device float[P][2] or NULL: optical depth

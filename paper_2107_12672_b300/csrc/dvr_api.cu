@@ -96,6 +96,11 @@ int check_common(const dvr_volume* vols, int nvol, const dvr_tf* tf, int model, 
             return fail(DVR_ERR_ARG, "volume %d: every dimension must be >= 2 (got %d x %d x %d)", i, v.nx, v.ny, v.nz);
         if ((double)v.nx * v.ny * v.nz >= 4294967296.0)
             return fail(DVR_ERR_ARG, "volume %d: more than 2^32 - 1 voxels", i);
+        const double ex = v.nx - 1.0, ey = v.ny - 1.0, ez = v.nz - 1.0;
+        if (std::sqrt(ex * ex + ey * ey + ez * ez) / (double)step + 2.0 >= 16777216.0)
+            return fail(DVR_ERR_ARG,
+                        "volume %d: at step_voxels %g a ray could take 2^24 or more samples (sample indices "
+                        "are exact binary32 integers)", i, (double)step);
         if (v.dtype != DVR_F32 && v.dtype != DVR_F16 && v.dtype != DVR_BF16)
             return fail(DVR_ERR_DTYPE, "volume %d: dtype %d unsupported", i, v.dtype);
         if (v.dtype != c.dtype)

@@ -227,18 +227,18 @@ backward_kernel(const __grid_constant__ Params p)
         MCell n1, n2;
         float2 last_v[4];
         if (N > 0) {
-            fetch_sample_reuse<VT>(vol, G, m, N - 1, 0xffffffffu, n1);
-            fetch_sample_reuse<VT>(vol, G, m, N - 2, n1.c.base, n2);
+            fetch_sample_reuse<VT>(vol, G, m, (float)(N - 1), 0xffffffffu, n1);
+            fetch_sample_reuse<VT>(vol, G, m, (float)(N - 2), n1.c.base, n2);
         }
+        float fi = (float)(N - 1);     // sample index i as a float (exact below 2^24)
 #pragma unroll (GVOL ? 1 : 3)
-        for (int i = N - 1; i >= 0; --i) {
-            const float fi = (float)i;
+        for (int i = N - 1; i >= 0; --i, fi -= 1.f) {
             MCell cur = n1;
             cell_resolve(cur, last_v);
 #pragma unroll
             for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
             n1 = n2;
-            fetch_sample_reuse<VT>(vol, G, m, i - 2, n1.c.base, n2);
+            fetch_sample_reuse<VT>(vol, G, m, fi - 2.f, n1.c.base, n2);
             const Cell& c = cur.c;
             float dg[3];
             const float d = POS ? cell_value_grad(c, dg) : cell_value(c);
@@ -253,7 +253,7 @@ backward_kernel(const __grid_constant__ Params p)
                     // with T_i = exp(-S_i): (1 - A_i) alpha_i = T_i - T_{i+1}, and the
                     // transmittance adjoint enters only as U = T_{i+1} T^_{i+1}, so the
                     // sample needs no alpha and no division
-                    depth_add(sh, sl, -x);            // S_i = S_{i+1} - dt tau_i
+                    depth_add(sh, sl, -G.dt, s.c.w);  // S_i = S_{i+1} - dt tau_i
                     const float T = transmittance(sh, sl);   // 1 - A_i
                     wgt = T - Tn;
                     const float q = fmaf(Tn, cC, -U);   // (1 - A_{i+1}) (rgb . C^ - T^_{i+1})

@@ -137,7 +137,7 @@ forward_color_kernel(const __grid_constant__ Params p)
             const Cell4 c = nxt;
             fetch4<VT>(vol, G, m, i + 1, nxt);
             const float4 s = cell4_value(c);
-            depth_add(sh, sl, G.dt * s.w);
+            depth_add(sh, sl, G.dt, s.w);
             const float Tn = transmittance(sh, sl);
             const float wgt = T - Tn;                  // (1 - A_i) alpha_i
             C0 = fmaf(wgt, s.x, C0);
@@ -212,7 +212,7 @@ backward_color_kernel(const __grid_constant__ Params p)
         // the emission-absorption adjoint in the transmittance-difference
         // form of the TF kernels: (1 - A_i) alpha_i = T_i - T_{i+1},
         // U = T_{i+1} T^_{i+1}
-        depth_add(sh, sl, -G.dt * s.w);         // S_i
+        depth_add(sh, sl, -G.dt, s.w);         // S_i
         const float T = transmittance(sh, sl);
         const float wgt = T - Tn;
         const float cC = fmaf(s.z, Ch2, fmaf(s.y, Ch1, s.x * Ch0));

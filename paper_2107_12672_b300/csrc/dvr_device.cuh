@@ -254,20 +254,31 @@ struct March {
     float g0h[3], g0l[3], gdh[3], gdl[3];
 };
 
+// Knuth's two-sum, s + e = a + b exactly. Every operation is a rounded
+// intrinsic: the compiler may not fuse a product that feeds b (the callers
+// pass dt tau) into the first addition, which would change s and let the
+// forward, forward-mode and adjoint kernels round the same sum differently.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// S += x on the optical depth carried as the unevaluated pair (sh, sl).
-__device__ __forceinline__ void depth_add(float& sh, float& sl, float x)
+// S += dt tau on the optical depth carried as the unevaluated pair
+// (sh, sl): the two-sum of sh and the exact product dt tau, each step an
+// explicit rounded operation (the product enters both fused multiply-adds
+// unrounded), so that every kernel forms the same pair from the same
+// samples, whatever the compiler would fuse on its own. The pair follows
+// sum_i dt tau_i to within a rounding of its low part (~2^-48 relative);
+// the adjoint removes each sample with -dt.
+__device__ __forceinline__ void depth_add(float& sh, float& sl, float dt, float tau)
 {
-    float s2, err;
-    two_sum(sh, x, s2, err);
-    sh = s2;
-    sl += err;
+    const float s = __fmaf_rn(dt, tau, sh);
+    const float bb = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fmaf_rn(dt, tau, -bb));
+    sh = s;
+    sl = __fadd_rn(sl, err);
 }
 
 // Transmittance 1 - A = exp(-S) of the optical depth (sh, sl).
@@ -279,12 +290,12 @@ __device__ __forceinline__ void make_march(const Ray& R, const Grid& g, March& m
     for (int a = 0; a < 3; ++a) {
         float sh, sl;
         two_sum(R.xo[a], g.half[a], sh, sl);
-        m.g0h[a] = sh * g.inv_h;
-        m.g0l[a] = __fmaf_rn(sh, g.inv_h, -m.g0h[a]) + sl * g.inv_h;
-        const float ph = R.w[a] * g.dt;
+        m.g0h[a] = __fmul_rn(sh, g.inv_h);
+        m.g0l[a] = __fadd_rn(__fmaf_rn(sh, g.inv_h, -m.g0h[a]), __fmul_rn(sl, g.inv_h));
+        const float ph = __fmul_rn(R.w[a], g.dt);
         const float pl = __fmaf_rn(R.w[a], g.dt, -ph);
-        m.gdh[a] = ph * g.inv_h;
-        m.gdl[a] = __fmaf_rn(ph, g.inv_h, -m.gdh[a]) + pl * g.inv_h;
+        m.gdh[a] = __fmul_rn(ph, g.inv_h);
+        m.gdl[a] = __fadd_rn(__fmaf_rn(ph, g.inv_h, -m.gdh[a]), __fmul_rn(pl, g.inv_h));
     }
 }
 
@@ -314,8 +325,8 @@ __device__ __forceinline__ void cell_locate(const Grid& G, const float gc[3], Ce
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float hi = (float)(G.n[a] - 1);
-        c.in[a] = (gc[a] >= 0.f) && (gc[a] <= hi);
         const float gg = fminf(fmaxf(gc[a], 0.f), hi);
+        c.in[a] = gg == gc[a];        // 0 <= gc <= hi (false for NaN, as the comparisons)
         j[a] = min((int)gg, G.n[a] - 2);
         fr[a] = gg - (float)j[a];
     }
@@ -401,9 +412,8 @@ struct MCell {
 
 template <typename VT>
 __device__ __forceinline__ void fetch_sample_reuse(const VT* __restrict__ vol, const Grid& G, const March& m,
-                                                   int i, uint32_t prev_base, MCell& mc)
+                                                   float fi, uint32_t prev_base, MCell& mc)
 {
-    const float fi = (float)i;
     const float gc[3] = {march_coord(m, 0, fi), march_coord(m, 1, fi), march_coord(m, 2, fi)};
     cell_locate(G, gc, mc.c);
     mc.reuse = mc.c.base == prev_base;
@@ -445,11 +455,11 @@ __device__ __forceinline__ void tf_cache_init(TFCache& t) { t.k = -1; }
 __device__ __forceinline__ void tf_lookup(const float4* __restrict__ tf, int R, float d, TFCache& t,
                                           TFSample& s)
 {
-    s.slope = (d >= 0.f) && (d <= 1.f);
     const float dc = fminf(fmaxf(d, 0.f), 1.f);
-    const float u = dc * (float)(R - 1);
+    s.slope = dc == d;                // 0 <= d <= 1
+    const float u = __fmul_rn(dc, (float)(R - 1));   // rounded, then the exact difference
     s.k = min((int)u, R - 2);
-    s.fr = u - (float)s.k;
+    s.fr = __fsub_rn(u, (float)s.k);
     if (s.k != t.k) {
         t.a = tf[2 * s.k];
         t.dc = tf[2 * s.k + 1];

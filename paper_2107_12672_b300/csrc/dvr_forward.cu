@@ -66,11 +66,12 @@ forward_kernel(const __grid_constant__ Params p)
         MCell n1, n2;
         float2 last_v[4];
         if (N > 0) {
-            fetch_sample_reuse<VT>(vol, G, m, 0, 0xffffffffu, n1);
-            fetch_sample_reuse<VT>(vol, G, m, 1, n1.c.base, n2);
+            fetch_sample_reuse<VT>(vol, G, m, 0.f, 0xffffffffu, n1);
+            fetch_sample_reuse<VT>(vol, G, m, 1.f, n1.c.base, n2);
         }
+        float f2 = 2.f;                // sample index i + 2 (exact below 2^24)
 #pragma unroll 3
-        for (int i = 0; i < N; ++i) {
+        for (int i = 0; i < N; ++i, f2 += 1.f) {
             if (CKPT) {
                 if (ck_left == 0) {
                     if (ck && ck_m < p.ckpt_slots) ck[ck_m] = T;
@@ -84,13 +85,13 @@ forward_kernel(const __grid_constant__ Params p)
 #pragma unroll
             for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
             n1 = n2;
-            fetch_sample_reuse<VT>(vol, G, m, i + 2, n1.c.base, n2);
+            fetch_sample_reuse<VT>(vol, G, m, f2, n1.c.base, n2);
             const Cell& c = cur.c;
             const float d = cell_value(c);
             if (MODEL == DVR_EMISSION_ABSORPTION) {
                 TFSample s;
                 tf_lookup(tf_s, p.R, d, tfc, s);
-                depth_add(sh, sl, G.dt * s.c.w);      // S_{i+1} = S_i + dt tau_i
+                depth_add(sh, sl, G.dt, s.c.w);      // S_{i+1} = S_i + dt tau_i
                 const float Tn = transmittance(sh, sl);   // 1 - A_{i+1}
                 const float wgt = T - Tn;             // (1 - A_i) alpha_i
                 C0 = fmaf(wgt, s.c.x, C0);
@@ -98,7 +99,7 @@ forward_kernel(const __grid_constant__ Params p)
                 C2 = fmaf(wgt, s.c.z, C2);
                 T = Tn;
             } else {
-                depth_add(sh, sl, G.dt * d);
+                depth_add(sh, sl, G.dt, d);
             }
         }
         if (valid) {

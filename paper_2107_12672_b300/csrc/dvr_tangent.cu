@@ -161,7 +161,7 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
         if (EA) {
             TFSample s;
             tf_lookup(tf_s, p.R, d, tfc, s);
-            depth_add(sh, sl, G.dt * s.c.w);         // S_{i+1}
+            depth_add(sh, sl, G.dt, s.c.w);         // S_{i+1}
             const float Tn = transmittance(sh, sl);  // the forward kernel's roundings
             const float wgt = T - Tn;
             const float sl_ = s.slope ? Rm1 : 0.f;
@@ -184,7 +184,7 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
         } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k) dS[k] = fmaf(G.dt, dd[k], dS[k]);
-            depth_add(sh, sl, G.dt * d);
+            depth_add(sh, sl, G.dt, d);
         }
     }
     const long long pix = vw.pixel_offset + (long long)py * vw.width + px;

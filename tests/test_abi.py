@@ -82,6 +82,7 @@ def _one_view(w=4, h=4, volume=0, lens=0.4, ortho=0):
     ("bad_view_volume", -1),
     ("bad_lens", -1),
     ("tiny_step", -1),
+    ("too_many_samples", -1),
     ("null_image", -1),
     ("ea_without_tf", -1),
     ("misaligned_image", -1),
@@ -104,6 +105,13 @@ def test_argument_errors_need_no_gpu(case, code):
         rc = _call_forward(vols, 1, None, 0, _one_view(lens=-1.0), 1)
     elif case == "tiny_step":
         rc = _call_forward(vols, 1, None, 0, view, 1, step=1e-6)
+    elif case == "too_many_samples":
+        # a 16385 x 2 x 2 box at the smallest step: its diagonal, 16384.0001
+        # voxels, takes 2^24 + 2 samples, past the binary32 sample index
+        long_box = (_abi.DvrVolume * 1)()
+        long_box[0] = _abi.DvrVolume(16385, 2, 2, _abi.DVR_F32, 4096)
+        rc = _call_forward(long_box, 1, None, 0, view, 1, step=2.0 ** -10)
+        assert "2^24" in lib.dvr_last_error().decode()
     elif case == "null_image":
         rc = _call_forward(vols, 1, None, 0, view, 1, image=None)
     elif case == "ea_without_tf":
