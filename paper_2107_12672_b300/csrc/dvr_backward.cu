@@ -39,21 +39,58 @@
 namespace dvr {
 
 // Register run of TF-gradient contributions: rows k (weight 1 - fr) and
-// k + 1 (weight fr), channels r, g, b, tau.
+// k + 1 (weight fr), as channel pairs: a[0] = row k (r, g), a[1] = row k
+// (b, tau), a[2], a[3] the same for row k + 1 (updated with packed FMAs).
 struct TFRun {
     int k;
-    float a[8];
+    float2 a[4];
 };
 
+__device__ __forceinline__ void tf_run_clear(TFRun& r)
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) r.a[j] = make_float2(0.f, 0.f);
+}
+
+// Adds the contributions of one sample: rgb^ = (h0, h1, h2), tau^.
+__device__ __forceinline__ void tf_run_add(TFRun& r, float fr, float h0, float h1, float h2, float tau_hat)
+{
+    const float2 w0 = p2dup(1.f - fr), w1 = p2dup(fr);
+    const float2 hrg = make_float2(h0, h1), hbt = make_float2(h2, tau_hat);
+    r.a[0] = p2fma(w0, hrg, r.a[0]);
+    r.a[1] = p2fma(w0, hbt, r.a[1]);
+    r.a[2] = p2fma(w1, hrg, r.a[2]);
+    r.a[3] = p2fma(w1, hbt, r.a[3]);
+}
+
+// The same with scalar FMAs (the volume-gradient kernels, where the packed
+// form takes more registers than the 3 blocks per SM allow).
+__device__ __forceinline__ void tf_run_add_scalar(TFRun& r, float fr, float h0, float h1, float h2,
+                                                  float tau_hat)
+{
+    const float w0 = 1.f - fr, w1 = fr;
+    r.a[0].x = fmaf(w0, h0, r.a[0].x);
+    r.a[0].y = fmaf(w0, h1, r.a[0].y);
+    r.a[1].x = fmaf(w0, h2, r.a[1].x);
+    r.a[1].y = fmaf(w0, tau_hat, r.a[1].y);
+    r.a[2].x = fmaf(w1, h0, r.a[2].x);
+    r.a[2].y = fmaf(w1, h1, r.a[2].y);
+    r.a[3].x = fmaf(w1, h2, r.a[3].x);
+    r.a[3].y = fmaf(w1, tau_hat, r.a[3].y);
+}
+
+// kTFWarp: adds a run to the warp's copy ([row][channel]) with shared atomics.
 __device__ __forceinline__ void tf_run_flush(float* rows, TFRun& r)
 {
     if (r.k >= 0) {
         float* b = rows + 4 * r.k;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) atomicAdd(b + j, r.a[j]);
+        for (int j = 0; j < 4; ++j) {
+            atomicAdd(b + 2 * j, r.a[j].x);
+            atomicAdd(b + 2 * j + 1, r.a[j].y);
+        }
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) r.a[j] = 0.f;
+    tf_run_clear(r);
 }
 
 // kTFPrivate: adds a run to the lane's own copy (plain adds, no atomics).
@@ -62,13 +99,12 @@ __device__ __forceinline__ void tf_run_flush_private(float4* my_tfp, TFRun& r)
     if (r.k >= 0) {
         float4* q = my_tfp + r.k * 32;
         float4 a = q[0], b = q[32];
-        a.x += r.a[0]; a.y += r.a[1]; a.z += r.a[2]; a.w += r.a[3];
-        b.x += r.a[4]; b.y += r.a[5]; b.z += r.a[6]; b.w += r.a[7];
+        a.x += r.a[0].x; a.y += r.a[0].y; a.z += r.a[1].x; a.w += r.a[1].y;
+        b.x += r.a[2].x; b.y += r.a[2].y; b.z += r.a[3].x; b.w += r.a[3].y;
         q[0] = a;
         q[32] = b;
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) r.a[j] = 0.f;
+    tf_run_clear(r);
 }
 
 // Register run of volume-gradient contributions to the 8 corners of one
@@ -210,8 +246,7 @@ backward_kernel(const __grid_constant__ Params p)
         float dt_hat = 0.f;
         TFRun tr;
         tr.k = -1;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) tr.a[j] = 0.f;
+        tf_run_clear(tr);
         CellRun cr;
         cr.base = 0xffffffffu;
 #pragma unroll
@@ -304,15 +339,7 @@ backward_kernel(const __grid_constant__ Params p)
                         tf_run_flush_private(my_tfp, tr);
                         tr.k = s.k;
                     }
-                    const float w0 = 1.f - s.fr, w1 = s.fr;
-                    tr.a[0] = fmaf(w0, h0, tr.a[0]);
-                    tr.a[1] = fmaf(w0, h1, tr.a[1]);
-                    tr.a[2] = fmaf(w0, h2, tr.a[2]);
-                    tr.a[3] = fmaf(w0, tau_hat, tr.a[3]);
-                    tr.a[4] = fmaf(w1, h0, tr.a[4]);
-                    tr.a[5] = fmaf(w1, h1, tr.a[5]);
-                    tr.a[6] = fmaf(w1, h2, tr.a[6]);
-                    tr.a[7] = fmaf(w1, tau_hat, tr.a[7]);
+                    tf_run_add(tr, s.fr, h0, h1, h2, tau_hat);
                 } else if (TFM == kTFPrivate) {
                     // the volume-gradient kernels need their registers for
                     // the cell run: each sample adds to the lane's own copy
@@ -331,15 +358,7 @@ backward_kernel(const __grid_constant__ Params p)
                         tf_run_flush(my_tfg, tr);
                         tr.k = s.k;
                     }
-                    const float w0 = 1.f - s.fr, w1 = s.fr;
-                    tr.a[0] = fmaf(w0, h0, tr.a[0]);
-                    tr.a[1] = fmaf(w0, h1, tr.a[1]);
-                    tr.a[2] = fmaf(w0, h2, tr.a[2]);
-                    tr.a[3] = fmaf(w0, tau_hat, tr.a[3]);
-                    tr.a[4] = fmaf(w1, h0, tr.a[4]);
-                    tr.a[5] = fmaf(w1, h1, tr.a[5]);
-                    tr.a[6] = fmaf(w1, h2, tr.a[6]);
-                    tr.a[7] = fmaf(w1, tau_hat, tr.a[7]);
+                    tf_run_add_scalar(tr, s.fr, h0, h1, h2, tau_hat);
                 } else if (TFM == kTFImmediate) {
                     const float w0 = 1.f - s.fr, w1 = s.fr;
                     float* b0 = p.grad_tf + 4 * s.k;
