@@ -281,7 +281,6 @@ backward_kernel(const __grid_constant__ Params p)
             if (EA) {
                 TFSample s;
                 tf_lookup(tf_s, p.R, d, tfc, s);
-                const float x = G.dt * s.c.w;
                 const float cC = fmaf(s.c.z, Ch2, fmaf(s.c.y, Ch1, s.c.x * Ch0));
                 float wgt, tau_hat;                   // (1 - A_i) alpha_i; adjoint of tau_i
                 if (INV == kInvDepth) {
@@ -297,6 +296,7 @@ backward_kernel(const __grid_constant__ Params p)
                     U = fmaf(wgt, cC, U);             // U_i = U_{i+1} + (1 - A_i) alpha_i rgb . C^
                     Tn = T;
                 } else {
+                    const float x = G.dt * s.c.w;
                     const float em = neg_expm1_br(x);
                     const float alpha = -em;
                     const float ea = 1.f + em;        // 1 - alpha
