@@ -153,7 +153,8 @@ __device__ __forceinline__ void cell_run_flush(float* g, bool v16, uint32_t nvox
 }
 
 template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV = kInvDepth>
-__global__ void __launch_bounds__(kWarps * 32, GVOL ? DVR_BWD_MIN_BLOCKS : DVR_BWD_QUEUE_MIN_BLOCKS)
+__global__ void __launch_bounds__(kWarps * 32, GVOL ? (sizeof(VT) == 2 ? DVR_BWD_MIN_BLOCKS_16 : DVR_BWD_MIN_BLOCKS)
+                                                    : DVR_BWD_QUEUE_MIN_BLOCKS)
 backward_kernel(const __grid_constant__ Params p)
 {
     constexpr bool EA = MODEL == DVR_EMISSION_ABSORPTION;

@@ -22,12 +22,20 @@ constexpr int kTileH = 4;            // set per launch)
 constexpr int kMaxTF = 1024;         // transfer-function rows staged in shared memory
 
 // Minimum resident blocks per SM the compiler must allow (register budget
-// of __launch_bounds__), chosen by measurement.
+// of __launch_bounds__), chosen by measurement. The forward: 4 blocks of 4
+// warps, at most 128 registers a thread (the binary32 kernels need 122; the
+// 16-bit storage kernels took 138 unbounded, hence 3 blocks: bounded, the
+// BF16 forward of a 256^3 volume at 512^2 went 0.305 -> 0.295 ms).
 #ifndef DVR_FWD_MIN_BLOCKS
-#define DVR_FWD_MIN_BLOCKS 1
+#define DVR_FWD_MIN_BLOCKS 4
 #endif
 #ifndef DVR_BWD_MIN_BLOCKS
 #define DVR_BWD_MIN_BLOCKS 1
+#endif
+// the volume-gradient adjoints of 16-bit volumes: 3 blocks of 4 warps (at
+// most 168 registers; the 64-row-TF variant takes 174 unbounded, 2 blocks)
+#ifndef DVR_BWD_MIN_BLOCKS_16
+#define DVR_BWD_MIN_BLOCKS_16 3
 #endif
 // the adjoint without a volume gradient (tile queue): 3 blocks of 4 warps
 // per SM, at most 168 registers a thread

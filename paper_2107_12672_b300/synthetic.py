@@ -178,6 +178,8 @@ class Workload:
     target: dict = field(default_factory=dict)  # what the loss compares to
     note: str = ""
     loss: str = "l2"                # "l2" against the target, or "entropy" (opacity entropy, maximised)
+    volume_dtype: str = "float32"   # storage of the volume on the device (torch dtype name)
+    tf_dtype: str = "float32"       # storage of the TF on the device
 
 
 def _orbit_params(rng, count, distance):
@@ -240,7 +242,8 @@ def workload(name: str, scale: float = 1.0) -> Workload:
         return Workload(name, "emission_absorption", [vol], tf, views, eye, None, 0.25,
                         ("volume", "tf", "camera"), target={"tf": random_tf(64, seed=105)},
                         note="512^3 BF16 value noise, 64-point FP16 TF, 16 views 1024^2, "
-                             "step 0.25 voxel")
+                             "step 0.25 voxel",
+                        volume_dtype="bfloat16", tf_dtype="float16")
     if name == "ea_fp16_1024":
         # volumes are left to the caller (device generation, see large_volume)
         n = sz(1024)
@@ -253,7 +256,7 @@ def workload(name: str, scale: float = 1.0) -> Workload:
                         note="1024^3 FP16 value noise plus 32 Gaussian blobs, 32-point TF, "
                              "32 views 2048^2, step 0.25 voxel (~4000 steps on axis-aligned rays), "
                              "opacity-entropy loss",
-                        loss="entropy")
+                        loss="entropy", volume_dtype="float16")
     raise KeyError(name)
 
 
