@@ -270,7 +270,7 @@ backward_kernel(const __grid_constant__ Params p)
 #pragma unroll (GVOL ? 1 : 3)
         for (int i = N - 1; i >= 0; --i, fi -= 1.f) {
             MCell cur = n1;
-            cell_resolve(cur, last_v);
+            cell_resolve<VT>(cur, last_v);
 #pragma unroll
             for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
             n1 = n2;

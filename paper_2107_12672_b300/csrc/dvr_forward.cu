@@ -81,7 +81,7 @@ forward_kernel(const __grid_constant__ Params p)
                 --ck_left;
             }
             MCell cur = n1;
-            cell_resolve(cur, last_v);
+            cell_resolve<VT>(cur, last_v);
 #pragma unroll
             for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
             n1 = n2;

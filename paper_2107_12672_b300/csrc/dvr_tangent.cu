@@ -145,7 +145,8 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
     Cell nxt;
     if (N > 0) fetch_sample<VT>(vol, G, m, 0, nxt);
     for (int i = 0; i < N; ++i) {
-        const Cell c = nxt;
+        Cell c = nxt;
+        cell_decode<VT>(c);
         fetch_sample<VT>(vol, G, m, i + 1, nxt);
         float dg[3];
         const float d = cell_value_grad(c, dg);
