@@ -24,8 +24,9 @@ constexpr int kMaxTF = 1024;         // transfer-function rows staged in shared 
 // Minimum resident blocks per SM the compiler must allow (register budget
 // of __launch_bounds__), chosen by measurement. The forward: 4 blocks of 4
 // warps, at most 128 registers a thread (the binary32 kernels need 122; the
-// 16-bit storage kernels took 138 unbounded, hence 3 blocks: bounded, the
-// BF16 forward of a 256^3 volume at 512^2 went 0.305 -> 0.295 ms).
+// FP16 kernels take 138 unbounded, and so did the BF16 ones before their
+// conversion moved to the consumer, hence 3 blocks: bounded, the BF16
+// forward of a 256^3 volume at 512^2 went 0.305 -> 0.295 ms).
 #ifndef DVR_FWD_MIN_BLOCKS
 #define DVR_FWD_MIN_BLOCKS 4
 #endif
@@ -33,7 +34,8 @@ constexpr int kMaxTF = 1024;         // transfer-function rows staged in shared 
 #define DVR_BWD_MIN_BLOCKS 1
 #endif
 // the volume-gradient adjoints of 16-bit volumes: 3 blocks of 4 warps (at
-// most 168 registers; the 64-row-TF variant takes 174 unbounded, 2 blocks)
+// most 168 registers; the FP16 64-row-TF variant takes 174 unbounded, 2
+// blocks, and the BF16 one did: 512^3 BF16 adjoint 241.3 -> 185.8 ms)
 #ifndef DVR_BWD_MIN_BLOCKS_16
 #define DVR_BWD_MIN_BLOCKS_16 3
 #endif
