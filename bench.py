@@ -13,8 +13,12 @@ adjoint) per second of step, in Gsamples/s.
 Timing: the tile widths are autotuned per pass (L2 flushed before each timed
 pass); W warm-up steps, then K steps each bracketed by CUDA events with a
 512 MiB write flushing L2 between steps, outside the brackets. `value` comes
-from the step captured once as a CUDA graph and replayed (--eager: launched
-step by step); forward_ms / adjoint_ms come from eager steps. NVML samples
+from the mean step of the step captured once as a CUDA graph and replayed
+(--eager: launched step by step; `ms_per_step_stats` gives the median,
+minimum and maximum of those K steps); forward_ms / adjoint_ms come from
+eager steps. The 512^3 and 1024^3 workloads run in their own BF16 / FP16
+storage (the arithmetic is binary32 throughout) and `storage_variants`
+times the other storage form of the same workload. NVML samples
 the SM clock and throttle reasons during the timed region. The roofline
 divides the adjoint's algorithmic bytes by its event time and compares them
 with the measured HBM copy bandwidth (MEASURED_PEAKS.json) and with the L2 /
@@ -581,11 +585,12 @@ def time_steps(wl, K, W, flush, clocks=None, world=1):
     return step_ms, fwd_ms, bwd_ms, wall, clk
 
 
-def time_steps_graph(wl, K, W, flush, clocks=None, world=1):
+def time_steps_graph(wl, K, W, flush, clocks=None, world=1, stats=None):
     """The same step captured once as a CUDA graph and replayed: K replays
     each bracketed by CUDA events (L2 flushed between replays, outside the
-    brackets), after W untimed replays. Returns per-step milliseconds and the
-    wall time of the timed region."""
+    brackets), after W untimed replays. Returns the mean milliseconds per
+    step and the wall time of the timed region; `stats`, if given, receives
+    the median, minimum and maximum of the K step times."""
     import torch
     import torch.distributed as dist
     side = torch.cuda.Stream()
@@ -619,7 +624,11 @@ def time_steps_graph(wl, K, W, flush, clocks=None, world=1):
     if world > 1:
         dist.barrier()
     clk = clocks.stop() if clocks is not None else None
-    return float(np.mean([s.elapsed_time(e) for s, e in zip(st, en)])), wall, clk
+    ms = [s.elapsed_time(e) for s, e in zip(st, en)]
+    if stats is not None:
+        stats.update(median=round(float(np.median(ms)), 4), min=round(float(np.min(ms)), 4),
+                     max=round(float(np.max(ms)), 4))
+    return float(np.mean(ms)), wall, clk
 
 
 def compare_camera_modes(wl, K, W, flush):
@@ -694,10 +703,11 @@ def run_ours(args):
     # per-kernel breakdown from eagerly launched steps; the headline step
     # time from the same step replayed as one CUDA graph
     eager_ms, fwd_ms, bwd_ms, _, _ = time_steps(wl, K, args.warmup, flush, None, world)
+    step_stats = {}                 # this rank's median / min / max step (graph replays)
     if args.eager:
         step_ms, _, _, wall, clk = time_steps(wl, K, args.warmup, flush, Clocks(local), world)
     else:
-        step_ms, wall, clk = time_steps_graph(wl, K, args.warmup, flush, Clocks(local), world)
+        step_ms, wall, clk = time_steps_graph(wl, K, args.warmup, flush, Clocks(local), world, step_stats)
     if world > 1:
         t = torch.tensor([step_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -762,10 +772,13 @@ def run_ours(args):
             "steps": K,
             "warmup": args.warmup,
             "ms_per_step": round(step_ms, 4),
+            "ms_per_step_stats": step_stats or None,
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32" if wl.vol[0].dtype == torch.float32 else str(wl.vol[0].dtype).replace("torch.", ""),
+            # the arithmetic is binary32 for every storage type (the storage
+            # is in config.volume / config.tf_dtype)
+            "dtype": "f32",
             "data": "synthetic (seeded generators; no dataset)",
             "config": cfg,
             "eager_ms_per_step": round(eager_ms, 4),
