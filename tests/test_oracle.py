@@ -377,6 +377,76 @@ def test_kink_ambiguity_bounds_one_sided_derivatives():
     assert g2["volume_ambiguity"].max() == 0
 
 
+def _kink_ray(D_shift):
+    """One perspective ray in the xz-plane-ish (pixel (5, 2) of a 7 x 6 view,
+    eye on the +z axis at distance D) through a 9^3 box whose vertex plane
+    x = 0.125 (vertex 5) holds a kink. D is chosen so that sample 3 lies
+    exactly on that plane (D_shift = 0) or shifted so that no sample lies
+    on any cell face or knot. Only that one sample sits on the kink, so a
+    small move of the eye along any axis takes it to one side."""
+    W, H, px, py = 7, 6, 5, 2
+    view = syn.View(W, H)
+    lens = view.tan_half_fov_y
+    su = ((2 * px + 1) / W - 1) * lens * W / H
+    sv = (1 - (2 * py + 1) / H) * lens
+    dl = math.sqrt(1 + su * su + sv * sv)
+    dt = 0.5 / 8
+    D = 0.5 + (0.125 - 3 * dt * su / dl) / su + D_shift
+    return view, np.array([py * W + px]), np.array([0.0, 0.0, D])
+
+
+@pytest.mark.parametrize("kind", ["cell_face", "tf_knot"])
+def test_eye_kink_ambiguity_bounds_one_sided_derivatives(kind):
+    """The eye-gradient kink bound (`eye_ambiguity`) against central
+    differences (Sec. 3.1: trilinear density, piecewise-linear TF; Alg. 2's
+    f_interpolate adjoint takes one-sided derivatives there). A sample on a
+    vertex plane across which the density's x-slope jumps (cell_face:
+    absorption model, d = 1/2 + |i - 5|/4), or whose density sits exactly on
+    a TF control point while the density varies along x (tf_knot: d = 3/16
+    + i/16, R = 5, d = 1/2 at vertex 5): the central difference w.r.t. each
+    eye coordinate averages the two one-sided derivatives, so it lies
+    exactly half the reported bound away from the adjoint's one-sided value
+    (the x and y coordinates also turn the ray, which the bound's chain
+    through the direction adjoint must carry); with the
+    ray moved off the plane the bound is exactly 0 and the central
+    difference equals the adjoint. All vertex values are dyadic, so slopes
+    away from the kink are exact and contribute nothing."""
+    n = 9
+    i = np.arange(n)
+    if kind == "cell_face":
+        model, tf = "absorption", None
+        prof = 0.5 + 0.25 * np.abs(i - 5)
+        G = np.array([[1.0]])
+    else:
+        model = "emission_absorption"
+        prof = 0.1875 + 0.0625 * i
+        tf = np.array([[0.1, 0.2, 0.3, 1.0], [0.4, 0.1, 0.9, 3.0], [0.2, 0.8, 0.5, 2.0],
+                       [0.9, 0.3, 0.1, 6.0], [0.5, 0.5, 0.5, 1.5]])
+        G = np.array([[0.3, -0.7, 0.5, 1.1]])
+    v = np.broadcast_to(prof[None, None, :], (n, n, n)).astype(np.float64).copy()
+    h = 1e-6
+    for shift in (0.0, 0.0123):
+        view, pix, eye = _kink_ray(shift)
+        g = oracle.backward(v, tf, model, view, eye, 0.5, G, fp32=False, pix=pix, want=("eye",), margin=1.0)
+        amb = g["eye_ambiguity"]
+        scale = np.abs(g["eye"]).max()
+        for k in range(3):
+            ep = eye.copy(); ep[k] += h
+            em = eye.copy(); em[k] -= h
+            ip, Np, _ = oracle.render(v, tf, model, view, ep, 0.5, fp32=False, pix=pix)
+            im, Nm, _ = oracle.render(v, tf, model, view, em, 0.5, fp32=False, pix=pix)
+            assert (Np == Nm).all() and Np[0] > 8
+            fd = (_loss(ip, G) - _loss(im, G)) / (2 * h)
+            dev = abs(fd - g["eye"][k])
+            if shift == 0.0:
+                assert abs(dev - 0.5 * amb[k]) <= 1e-6 * scale, (k, dev, amb[k])
+            else:
+                assert amb[k] == 0, amb
+                assert dev <= 1e-8 * scale, (k, fd, g["eye"][k])
+        if shift == 0.0:
+            assert amb[0] > 0.05 * scale and amb[2] > 0.05 * scale
+
+
 # ------------------------------------------------------- pre-shaded colour volume
 def test_color_volume_equals_ea_for_affine_tf():
     """Sec. 5.4 colour volume: per-vertex (r, g, b, tau), interpolated. An
