@@ -57,6 +57,10 @@ def _load():
         lib.ora_rays.argtypes = [I, I, I, I, I, I, D, P, D, I, P, P, P]
         lib.ora_interpolate.argtypes = [P, I, I, I, P, L, P]
         lib.ora_backward.argtypes = [P, I, I, I, I, P, I, I, I, I, I, D, P, D, I, P, L, P, I, P, P, P, P, D, P, P]
+        lib.ora_backward_sel.argtypes = lib.ora_backward.argtypes + [P, L]
+        lib.ora_backward_sel.restype = L
+        lib.ora_touched.argtypes = [I, I, I, I, I, I, D, P, D, I, P, L, P, L]
+        lib.ora_touched.restype = L
         lib.ora_render_dual.argtypes = [P, I, I, I, I, P, I, I, I, I, I, D, P, D, I, P, L, P, P]
         lib.ora_orbit_eye.argtypes = [P, L, P]
         lib.ora_orbit_eye_backward.argtypes = [P, L, P, P]
@@ -140,7 +144,7 @@ def render(volume, tf, model, view, eye, step, fp32=True, pix=None):
 
 
 def backward(volume, tf, model, view, eye, step, grad_image, fp32=True, pix=None,
-             invert=False, want=("volume", "tf", "eye", "step"), margin=0.0):
+             invert=False, want=("volume", "tf", "eye", "step"), margin=0.0, sel=None):
     """Alg. 2 for one view with the stored-state tape (invert=False) or the
     inversion of Eq. inv-blend-forward (invert=True). Returns a dict of
     binary64 gradients for the requested parameters.
@@ -151,20 +155,37 @@ def backward(volume, tf, model, view, eye, step, grad_image, fp32=True, pix=None
     far a correct gradient may move when samples closer to a kink of the
     piecewise-linear TF, or to a cell face, than binary32 rounding (times
     `margin`) take the other one-sided derivative.
+
+    With `sel` (ascending linear vertex indices, e.g. np.unique of
+    touched()), the volume gradient and its bound are returned compactly,
+    one entry (four for colour volumes) per selected vertex, for volumes
+    whose dense binary64 gradient would not fit in host memory; every
+    vertex the rays touch must be selected.
     """
     c = _Common(volume, tf, model, view, eye, step, fp32)
     p, n = _pix(pix)
     total = n if p is not None else c.W * c.H
     gi = _f64(grad_image).reshape(total, c.nc)
     out = {}
-    gv = np.zeros(c.vol.shape) if "volume" in want else None
+    if sel is not None:
+        sel = np.ascontiguousarray(np.asarray(sel, dtype=np.int64))
+        vshape = (sel.size,) + c.vol.shape[3:]
+    else:
+        vshape = c.vol.shape
+    gv = np.zeros(vshape) if "volume" in want else None
     gt = np.zeros((c.R, 4)) if ("tf" in want and c.model == EMISSION_ABSORPTION) else None
     ge = np.zeros(3) if "eye" in want else None
     gs = np.zeros(1) if "step" in want else None
-    amb = np.zeros(c.vol.shape) if (gv is not None and margin > 0) else None
+    amb = np.zeros(vshape[:1] if sel is not None else c.vol.shape) if (gv is not None and margin > 0) else None
     amb_e = np.zeros(3) if (ge is not None and margin > 0) else None
-    _load().ora_backward(*c.head(), c.fp32, _p(p), n, _p(gi), int(bool(invert)),
-                         _p(gv), _p(gt), _p(ge), _p(gs), float(margin), _p(amb), _p(amb_e))
+    args = (*c.head(), c.fp32, _p(p), n, _p(gi), int(bool(invert)),
+            _p(gv), _p(gt), _p(ge), _p(gs), float(margin), _p(amb), _p(amb_e))
+    if sel is not None:
+        miss = _load().ora_backward_sel(*args, _p(sel), sel.size)
+        if miss:
+            raise ValueError(f"{miss} vertex contributions fell outside `sel`")
+    else:
+        _load().ora_backward(*args)
     if amb is not None:
         out["volume_ambiguity"] = amb
     if amb_e is not None:
@@ -178,6 +199,24 @@ def backward(volume, tf, model, view, eye, step, grad_image, fp32=True, pix=None
     if gs is not None:
         out["step"] = gs[0]
     return out
+
+
+def touched(shape, view, eye, step, pix=None, fp32=True):
+    """Ascending unique linear indices of the vertices whose values the
+    listed rays read (the 8 corners of every sample, Alg. 1's
+    f_interpolate), for backward(..., sel=...)."""
+    nz, ny, nx = shape[:3]
+    W, H = int(view.width), int(view.height)
+    cv = _f32val if fp32 else float
+    lens = cv(view.ortho_height if view.ortho else view.tan_half_fov_y)
+    e = np.array([cv(v) for v in np.asarray(eye).reshape(3)], dtype=np.float64)
+    p, n = _pix(pix)
+    lib = _load()
+    head = (nx, ny, nz, W, H, int(bool(view.ortho)), lens, _p(e), cv(step), int(bool(fp32)), _p(p), n)
+    count = lib.ora_touched(*head, None, 0)
+    out = np.empty(count, dtype=np.int64)
+    lib.ora_touched(*head, _p(out), count)
+    return np.unique(out)
 
 
 def render_dual(volume, tf, model, view, eye, step, pix=None, n_fp32=False):

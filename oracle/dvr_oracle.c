@@ -500,6 +500,12 @@ static inline void atomic_add(double* p, double v)
     *p += v;
 }
 
+static inline void atomic_miss(int64_t* n)
+{
+#pragma omp atomic
+    *n += 1;
+}
+
 /*
  * Adjoint of f_camera: chain the adjoints of the entry point x_o and the
  * direction w back to the eye position (last line of Alg. 2's loop body
@@ -580,12 +586,117 @@ static void camera_adjoint(const cam_t* c, const ray_t* r, const double xo_hat[3
  *   amb_eye: the change of x^_i from either kind of kink, chained through
  *            the camera adjoint, summed in absolute value.
  */
+/*
+ * Where the volume gradient of vertex `idx` is stored: at idx itself
+ * (dense output), or, with a selection `sel` (ascending vertex indices),
+ * at its position in `sel` (compact output for volumes whose dense
+ * binary64 gradient would not fit in host memory); -1 if the vertex is not
+ * selected (counted by the caller as a miss).
+ */
+typedef struct {
+    const int64_t* sel;
+    int64_t n;
+} vsel_t;
+
+static inline int64_t vslot(const vsel_t* vs, long idx)
+{
+    if (!vs->sel) return idx;
+    int64_t lo = 0, hi = vs->n - 1;
+    while (lo <= hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (vs->sel[mid] == idx) return mid;
+        if (vs->sel[mid] < idx) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+static int64_t backward_impl(const void* V, int vf32, int nx, int ny, int nz, const double* tf, int R, int model,
+                         int W, int H, int ortho, double lens, const double* eye, double step, int fp32,
+                         const int64_t* pix, int64_t npix, const double* grad_image, int invert,
+                         double* grad_vol, double* grad_tf, double* grad_eye, double* grad_step,
+                         double margin, double* amb_vol, double* amb_eye, const vsel_t* vs);
+
 int ora_backward(const void* V, int vf32, int nx, int ny, int nz, const double* tf, int R, int model,
                  int W, int H, int ortho, double lens, const double* eye, double step, int fp32,
                  const int64_t* pix, int64_t npix, const double* grad_image, int invert,
                  double* grad_vol, double* grad_tf, double* grad_eye, double* grad_step,
                  double margin, double* amb_vol, double* amb_eye)
 {
+    vsel_t vs = {NULL, 0};
+    return (int)backward_impl(V, vf32, nx, ny, nz, tf, R, model, W, H, ortho, lens, eye, step, fp32, pix, npix,
+                         grad_image, invert, grad_vol, grad_tf, grad_eye, grad_step, margin, amb_vol, amb_eye,
+                         &vs);
+}
+
+/*
+ * ora_backward with the volume gradient (and its kink bound) stored
+ * compactly: grad_vol[k] (grad_vol[4k + ch] for colour volumes) and
+ * amb_vol[k] belong to vertex sel[k], sel ascending. Returns the number of
+ * vertex contributions that found no slot (0 when sel lists every vertex
+ * the rays touch, as ora_touched gives).
+ */
+int64_t ora_backward_sel(const void* V, int vf32, int nx, int ny, int nz, const double* tf, int R, int model,
+                         int W, int H, int ortho, double lens, const double* eye, double step, int fp32,
+                         const int64_t* pix, int64_t npix, const double* grad_image, int invert,
+                         double* grad_vol, double* grad_tf, double* grad_eye, double* grad_step,
+                         double margin, double* amb_vol, double* amb_eye, const int64_t* sel, int64_t nsel)
+{
+    vsel_t vs = {sel, nsel};
+    return backward_impl(V, vf32, nx, ny, nz, tf, R, model, W, H, ortho, lens, eye, step, fp32, pix, npix,
+                         grad_image, invert, grad_vol, grad_tf, grad_eye, grad_step, margin, amb_vol, amb_eye,
+                         &vs);
+}
+
+/*
+ * The 8 corner vertices of every sample of the listed rays (Alg. 1's
+ * f_interpolate footprint), in march order, duplicates included. With
+ * out == NULL only counts them. Returns the count (or, with out given, the
+ * number written, at most cap).
+ */
+int64_t ora_touched(int nx, int ny, int nz, int W, int H, int ortho, double lens, const double* eye,
+                    double step, int fp32, const int64_t* pix, int64_t npix, int64_t* out, int64_t cap)
+{
+    scene_t s;
+    setup_scene(&s, NULL, 0, nx, ny, nz, NULL, 2, ORA_ABSORPTION, W, H, ortho, lens, eye, step, fp32);
+    int64_t total = pix ? npix : (int64_t)W * H;
+    int64_t k = 0;
+    for (int64_t t = 0; t < total; ++t) {
+        int64_t p = pix ? pix[t] : t;
+        ray_t ry;
+        camera_ray(&s.cam, &s.G, (int)(p % W), (int)(p / W), fp32, &ry);
+        for (int i = 0; i < ry.N; ++i) {
+            double x[3];
+            double ti = (double)i * s.G.dt;
+            for (int a = 0; a < 3; ++a) x[a] = ry.xo[a] + ti * ry.w[a];
+            /* the corner indices of f_interpolate at x (values not read) */
+            int j[3];
+            for (int a = 0; a < 3; ++a) {
+                double g = (x[a] + s.G.half[a]) * s.G.inv_h;
+                if (g < 0.0) g = 0.0;
+                if (g > (double)(s.G.n[a] - 1)) g = (double)(s.G.n[a] - 1);
+                int jj = (int)floor(g);
+                if (jj > s.G.n[a] - 2) jj = s.G.n[a] - 2;
+                j[a] = jj;
+            }
+            for (int c = 0; c < 8; ++c) {
+                if (out && k >= cap) return k;
+                if (out)
+                    out[k] = ((long)(j[2] + ((c >> 2) & 1)) * s.G.n[1] + (j[1] + ((c >> 1) & 1))) * (long)s.G.n[0]
+                             + (j[0] + (c & 1));
+                ++k;
+            }
+        }
+    }
+    return k;
+}
+
+static int64_t backward_impl(const void* V, int vf32, int nx, int ny, int nz, const double* tf, int R, int model,
+                         int W, int H, int ortho, double lens, const double* eye, double step, int fp32,
+                         const int64_t* pix, int64_t npix, const double* grad_image, int invert,
+                         double* grad_vol, double* grad_tf, double* grad_eye, double* grad_step,
+                         double margin, double* amb_vol, double* amb_eye, const vsel_t* vs)
+{
+    int64_t misses = 0;
     scene_t s;
     setup_scene(&s, V, vf32, nx, ny, nz, tf, R, model, W, H, ortho, lens, eye, step, fp32);
     int64_t total = pix ? npix : (int64_t)W * H;
@@ -685,7 +796,11 @@ int ora_backward(const void* V, int vf32, int nx, int ny, int nz, const double* 
                             double jump = fabs(side[1] - side[0]);
                             d_jump = jump;
                             if (amb_vol)
-                                for (int c = 0; c < 8; ++c) atomic_add(&amb_vol[sm.idx[c]], sm.wt[c] * jump);
+                                for (int c = 0; c < 8; ++c) {
+                                    int64_t q = vslot(vs, sm.idx[c]);
+                                    if (q < 0) { atomic_miss(&misses); continue; }
+                                    atomic_add(&amb_vol[q], sm.wt[c] * jump);
+                                }
                         }
                     }
                 } else {
@@ -695,16 +810,23 @@ int ora_backward(const void* V, int vf32, int nx, int ny, int nz, const double* 
                 double gd[3];
                 if (model == ORA_COLOR_VOLUME) {
                     if (grad_vol)
-                        for (int c = 0; c < 8; ++c)
+                        for (int c = 0; c < 8; ++c) {
+                            int64_t q = vslot(vs, sm.idx[c]);
+                            if (q < 0) { atomic_miss(&misses); continue; }
                             for (int ch = 0; ch < 4; ++ch)
-                                atomic_add(&grad_vol[sm.idx[c] * 4 + ch], sm.wt[c] * c_hat[ch]);
+                                atomic_add(&grad_vol[q * 4 + ch], sm.wt[c] * c_hat[ch]);
+                        }
                     for (int a = 0; a < 3; ++a) {
                         gd[a] = 0.0;
                         for (int ch = 0; ch < 4; ++ch) gd[a] += sm.dg4[ch][a] * c_hat[ch];
                     }
                 } else {
                     if (grad_vol)
-                        for (int c = 0; c < 8; ++c) atomic_add(&grad_vol[sm.idx[c]], sm.wt[c] * d_hat);
+                        for (int c = 0; c < 8; ++c) {
+                            int64_t q = vslot(vs, sm.idx[c]);
+                            if (q < 0) { atomic_miss(&misses); continue; }
+                            atomic_add(&grad_vol[q], sm.wt[c] * d_hat);
+                        }
                     for (int a = 0; a < 3; ++a) gd[a] = sm.dg[a] * d_hat;
                 }
                 double ti = (double)i * dt;
@@ -771,7 +893,7 @@ int ora_backward(const void* V, int vf32, int nx, int ny, int nz, const double* 
         free(tapeA);
         free(tapeC);
     }
-    return 0;
+    return misses;
 }
 
 /* ---------------------------------------------------------------------- */
