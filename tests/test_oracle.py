@@ -586,3 +586,40 @@ def test_opacity_entropy_gradient():
     a[5] = 0.0
     _, g = oracle.opacity_entropy(a)
     assert g[5] > 0 and np.isfinite(g[5])
+
+
+@pytest.mark.parametrize("model", ["absorption", "emission_absorption", "color"])
+def test_compact_volume_gradient_equals_dense(model):
+    """The compact volume-gradient output (one entry per vertex the listed
+    rays read, for volumes whose dense binary64 gradient does not fit in
+    host memory) holds exactly the dense gradient's values at those
+    vertices, and the dense gradient is zero everywhere else."""
+    rng = np.random.default_rng(8)
+    n = 10
+    if model == "color":
+        v = rng.uniform(0.1, 1.0, (n, n, n, 4))
+        tf = None
+    else:
+        v = rng.uniform(0.0, 1.0, (n, n, n))
+        tf = rng.uniform(0.1, 1.0, (6, 4)) if model == "emission_absorption" else None
+    view = syn.View(11, 9)
+    eye = np.array([0.9, -0.5, 1.6])
+    pix = np.array([3, 17, 40, 41, 77, 98])
+    nc = 1 if model == "absorption" else 4
+    G = rng.normal(size=(pix.size, nc))
+    sel = oracle.touched(v.shape, view, eye, 0.5, pix=pix)
+    assert sel.size > 8 and (np.diff(sel) > 0).all()
+    dense = oracle.backward(v, tf, model, view, eye, 0.5, G, pix=pix, want=("volume", "eye"), margin=2.0)
+    comp = oracle.backward(v, tf, model, view, eye, 0.5, G, pix=pix, want=("volume", "eye"), margin=2.0, sel=sel)
+    flat = dense["volume"].reshape((n ** 3,) + v.shape[3:])
+    np.testing.assert_allclose(comp["volume"], flat[sel], rtol=1e-13, atol=1e-15)
+    rest = np.ones(n ** 3, bool)
+    rest[sel] = False
+    assert not flat[rest].any()
+    assert np.abs(flat[sel]).max() > 0
+    np.testing.assert_allclose(comp["eye"], dense["eye"], rtol=1e-13)
+    if model == "emission_absorption":
+        np.testing.assert_allclose(comp["volume_ambiguity"], dense["volume_ambiguity"].reshape(-1)[sel],
+                                   rtol=1e-13, atol=1e-15)
+    with pytest.raises(ValueError):
+        oracle.backward(v, tf, model, view, eye, 0.5, G, pix=pix, want=("volume",), sel=sel[1:])
