@@ -262,9 +262,13 @@ backward_kernel(const __grid_constant__ Params p)
         tf_cache_init(tfc);
         MCell n1, n2;
         float2 last_v[4];
+        long long q[3];                // position of the next fetch (fixed point)
+        march_pos(m, N - 1, q);
         if (N > 0) {
-            fetch_sample_reuse<VT>(vol, G, m, (float)(N - 1), 0xffffffffu, n1);
-            fetch_sample_reuse<VT>(vol, G, m, (float)(N - 2), n1.c.base, n2);
+            fetch_sample_reuse<VT>(vol, G, q, 0xffffffffu, n1);
+            march_prev(m, q);
+            fetch_sample_reuse<VT>(vol, G, q, n1.c.base, n2);
+            march_prev(m, q);
         }
         float fi = (float)(N - 1);     // sample index i as a float (exact below 2^24)
 #pragma unroll (GVOL ? 1 : 3)
@@ -274,10 +278,11 @@ backward_kernel(const __grid_constant__ Params p)
 #pragma unroll
             for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
             n1 = n2;
-            fetch_sample_reuse<VT>(vol, G, m, fi - 2.f, n1.c.base, n2);
+            fetch_sample_reuse<VT>(vol, G, q, n1.c.base, n2);      // sample i - 2
+            march_prev(m, q);
             const Cell& c = cur.c;
             float dg[3];
-            const float d = POS ? cell_value_grad(c, dg) : cell_value(c);
+            const Density d = POS ? cell_density_grad(c, dg) : cell_density(c);
             float d_hat;
             if (EA) {
                 TFSample s;
@@ -376,7 +381,7 @@ backward_kernel(const __grid_constant__ Params p)
                                 : 0.f;
             } else {
                 d_hat = dconst;
-                if (POS) dt_hat = fmaf(Ah, d, dt_hat);   // times T_N below
+                if (POS) dt_hat = fmaf(Ah, density_value(d), dt_hat);   // times T_N below
             }
             if (GVOL) {
                 if (c.base != cr.base) {

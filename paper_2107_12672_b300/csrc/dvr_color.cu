@@ -49,21 +49,14 @@ template <typename VT>
 __device__ __forceinline__ void fetch4(const VT* __restrict__ vol, const Grid& G, const March& m, int i,
                                        Cell4& c)
 {
-    const float fi = (float)i;
-    const float gc[3] = {march_coord(m, 0, fi), march_coord(m, 1, fi), march_coord(m, 2, fi)};
-    int j[3];
-    float fr[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float hi = (float)(G.n[a] - 1);
-        c.in[a] = (gc[a] >= 0.f) && (gc[a] <= hi);
-        const float gg = fminf(fmaxf(gc[a], 0.f), hi);
-        j[a] = min((int)gg, G.n[a] - 2);
-        fr[a] = gg - (float)j[a];
-    }
-    c.fx = fr[0]; c.fy = fr[1]; c.fz = fr[2];
+    long long q[3];
+    march_pos(m, i, q);
+    Cell cl;                                   // the cell of sample i (no corner loads)
+    cell_locate(G, q, cl);
+    c.fx = cl.fx; c.fy = cl.fy; c.fz = cl.fz;
+    c.in[0] = cl.in[0]; c.in[1] = cl.in[1]; c.in[2] = cl.in[2];
+    c.base = cl.base;
     const uint32_t sy = (uint32_t)G.n[0], sz = (uint32_t)G.n[0] * (uint32_t)G.n[1];
-    c.base = (uint32_t)j[0] + sy * (uint32_t)j[1] + sz * (uint32_t)j[2];
     const VT* p = vol + 4 * (size_t)c.base;
     const size_t y4 = 4 * (size_t)sy, z4 = 4 * (size_t)sz;
     c.v[0] = Load4<VT>::get(p);
@@ -131,20 +124,26 @@ forward_color_kernel(const __grid_constant__ Params p)
         March m;
         make_march(R, G, m);
         float sh = 0.f, sl = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+        float P0 = 0.f, P1 = 0.f, P2 = 0.f;          // colour of the current block of samples
         Cell4 nxt;
         if (N > 0) fetch4<VT>(vol, G, m, 0, nxt);
         for (int i = 0; i < N; ++i) {
             const Cell4 c = nxt;
             fetch4<VT>(vol, G, m, i + 1, nxt);
             const float4 s = cell4_value(c);
+            const float alpha = sample_alpha(G.dt, s.w);
             depth_add(sh, sl, G.dt, s.w);
-            const float Tn = transmittance(sh, sl);
-            const float wgt = T - Tn;                  // (1 - A_i) alpha_i
-            C0 = fmaf(wgt, s.x, C0);
-            C1 = fmaf(wgt, s.y, C1);
-            C2 = fmaf(wgt, s.z, C2);
-            T = Tn;
+            const float wgt = T * alpha;               // (1 - A_i) alpha_i
+            P0 = fmaf(wgt, s.x, P0);
+            P1 = fmaf(wgt, s.y, P1);
+            P2 = fmaf(wgt, s.z, P2);
+            if ((i & (kColourBlock - 1)) == kColourBlock - 1) {
+                C0 += P0; C1 += P1; C2 += P2;
+                P0 = 0.f; P1 = 0.f; P2 = 0.f;
+            }
+            T = transmittance(sh, sl);
         }
+        C0 += P0; C1 += P1; C2 += P2;
         if (valid) {
             const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
             reinterpret_cast<float4*>(p.image)[pix] = make_float4(C0, C1, C2, -expm1f(-(sh + sl)));

@@ -20,6 +20,7 @@ constexpr int kWarps = 4;            // warps per block
 constexpr int kTileW = 8;            // default warp tile: 8 x 4 pixels (tile_w x tile_h = 32,
 constexpr int kTileH = 4;            // set per launch)
 constexpr int kMaxTF = 1024;         // transfer-function rows staged in shared memory
+constexpr int kFixBits = 40;         // fraction bits of a fixed-point sample position
 
 // Minimum resident blocks per SM the compiler must allow (register budget
 // of __launch_bounds__), chosen by measurement. The forward: 4 blocks of 4
@@ -133,16 +134,14 @@ __device__ __forceinline__ float2 p2sub(float2 a, float2 b)
 __device__ __forceinline__ float2 p2dup(float a) { return make_float2(a, a); }
 
 // expm1(-x), the negated opacity -alpha of a segment with optical depth x
-// (Sec. 3.1, alpha = 1 - exp(-dt tau)), for the adjoint's alpha-form
-// inversion ablations (the other passes blend with differences of
-// transmittances and need no alpha). For |x| <= 1/8 the Taylor series of
-// e^y - 1 at y = -x to degree 7 in Horner form (truncation below 2^-33
-// relative, far under one binary32 ulp); beyond, exp(-x) - 1 with CUDA's
-// expf (exact subtraction there, within ~1e-6 relative).
+// (Sec. 3.1, alpha = 1 - exp(-dt tau)). For |x| <= 1/8 the Taylor series of
+// e^y - 1 at y = -x to degree 6 in Horner form (truncation below
+// (1/8)^6 / 7! = 7.6e-10 relative, under one binary32 ulp); beyond,
+// exp(-x) - 1 with CUDA's expf (exact subtraction there, within ~1e-6
+// relative).
 __device__ __forceinline__ float expm1_taylor(float y)
 {
-    float q = fmaf(y, 1.f / 5040.f, 1.f / 720.f);
-    q = fmaf(y, q, 1.f / 120.f);
+    float q = fmaf(y, 1.f / 720.f, 1.f / 120.f);
     q = fmaf(y, q, 1.f / 24.f);
     q = fmaf(y, q, 1.f / 6.f);
     q = fmaf(y, q, 0.5f);
@@ -158,6 +157,39 @@ __device__ __forceinline__ float neg_expm1_br(float x)
     return neg_expm1_wide(x);
 }
 
+// Opacity alpha_i = 1 - exp(-dt tau_i) of a sample (Sec. 3.1) for the
+// forward passes, accurate relative to its own size however thin the
+// sample: for |x| <= 1/8 (x = dt tau) the Taylor series x - x^2/2 + ... +
+// x^5/120 (truncation below x^5/720 <= 4.2e-8 relative), beyond it
+// 1 - exp(-x) with CUDA's expf (within ~1e-6 relative there). The blend
+// weight (1 - A_i) alpha_i is formed as T_i alpha_i with T_i = exp(-S_i):
+// each factor keeps its relative precision, so every image element does,
+// faint ones included. The difference of consecutive transmittances
+// T_i - T_{i+1} (the same value) carries an absolute error of one rounding
+// of T_i: 1.4e-5 relative was measured that way on a faint element. (The
+// adjoint, whose bar is 1e-3, keeps the difference: it needs T_{i+1} and
+// T_i anyway.) The product dt tau is one explicit rounding, the same in
+// every kernel.
+__device__ __forceinline__ float sample_alpha(float dt, float tau)
+{
+    const float x = __fmul_rn(dt, tau);
+    if (fabsf(x) <= 0.125f) {
+        float q = fmaf(x, -1.f / 120.f, 1.f / 24.f);
+        q = fmaf(x, q, -1.f / 6.f);
+        q = fmaf(x, q, 0.5f);
+        q = fmaf(x, q, -1.f);
+        return -x * q;
+    }
+    return -neg_expm1_wide(x);           // a call, so the common path stays short
+}
+
+// Colour sums of long rays: the blend adds thousands of small terms to a
+// growing sum, whose roundings (half an ulp of the sum each) added up to
+// 2.2e-5 relative on a 4000-sample ray. The forward passes add each block
+// of kColourBlock samples into a partial sum first and the partial sum
+// into the total, so the total takes one rounding per block.
+constexpr int kColourBlock = 64;
+
 // --------------------------------------------------------------- the ray
 struct Ray {
     float o[3], w[3], xo[3];
@@ -172,6 +204,7 @@ struct Grid {
     float dt;
     float inv_h;                     // max(n) - 1
     int n[3];
+    int top[3];                      // (n - 1) in the high word of a fixed-point position
 };
 
 __device__ __forceinline__ void make_grid(const VolumeDesc& v, float step, Grid& g)
@@ -182,6 +215,7 @@ __device__ __forceinline__ void make_grid(const VolumeDesc& v, float step, Grid&
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         g.n[a] = v.n[a];
+        g.top[a] = (v.n[a] - 1) << (kFixBits - 32);
         g.half[a] = __fmul_rn(__fdiv_rn((float)(v.n[a] - 1), den), 0.5f);
     }
 }
@@ -270,11 +304,21 @@ __device__ __forceinline__ void ray_setup(const float e[3], int px, int py, cons
     for (int a = 0; a < 3; ++a) R.xo[a] = __fadd_rn(R.o[a], __fmul_rn(tn, R.w[a]));
 }
 
-// Sample positions in grid coordinates, g_i = G0 + i*Gd, each term carried
-// as an unevaluated float pair so that g_i is within one rounding of the
-// exact (x_o + i dt w + half) * inv_h, however long the ray.
+// Sample positions in grid coordinates as 64-bit fixed point with kFixBits
+// fraction bits. The entry point G0 and the step Gd (each first formed as
+// an unevaluated float pair, within ~2^-48 relative of the exact values)
+// are rounded to that grid once per ray; sample i is then G0 + i Gd, an
+// exact integer sum however a kernel gets there (by index, or by adding or
+// subtracting Gd sample after sample), so the forward, the forward-mode and
+// the adjoint kernels take the same position for sample i, within
+// 2^-41 (1 + i) grid units of the exact one (~5e-9 after 10^4 samples). The
+// trilinear weights then carry the rounding of a fraction in [0, 1]
+// (2^-25) rather than that of a binary32 coordinate as large as the grid
+// (2^-25 (n - 1): 1.5e-5 at n = 256, 3e-5 at n = 1024), which decided the
+// error of voxel gradients formed from small weights.
+
 struct March {
-    float g0h[3], g0l[3], gdh[3], gdl[3];
+    long long g0[3], gd[3];
 };
 
 // Knuth's two-sum, s + e = a + b exactly. Every operation is a rounded
@@ -307,24 +351,47 @@ __device__ __forceinline__ void depth_add(float& sh, float& sl, float dt, float 
 // Transmittance 1 - A = exp(-S) of the optical depth (sh, sl).
 __device__ __forceinline__ float transmittance(float sh, float sl) { return expf(-(sh + sl)); }
 
+// The float pair (h, l) in fixed point (h 2^40 is exact in binary32; the
+// conversions round to the nearest integer).
+__device__ __forceinline__ long long to_fixed(float h, float l)
+{
+    return __float2ll_rn(h * 0x1p40f) + __float2ll_rn(l * 0x1p40f);
+}
+
 __device__ __forceinline__ void make_march(const Ray& R, const Grid& g, March& m)
 {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         float sh, sl;
         two_sum(R.xo[a], g.half[a], sh, sl);
-        m.g0h[a] = __fmul_rn(sh, g.inv_h);
-        m.g0l[a] = __fadd_rn(__fmaf_rn(sh, g.inv_h, -m.g0h[a]), __fmul_rn(sl, g.inv_h));
+        const float g0h = __fmul_rn(sh, g.inv_h);
+        const float g0l = __fadd_rn(__fmaf_rn(sh, g.inv_h, -g0h), __fmul_rn(sl, g.inv_h));
         const float ph = __fmul_rn(R.w[a], g.dt);
         const float pl = __fmaf_rn(R.w[a], g.dt, -ph);
-        m.gdh[a] = __fmul_rn(ph, g.inv_h);
-        m.gdl[a] = __fadd_rn(__fmaf_rn(ph, g.inv_h, -m.gdh[a]), __fmul_rn(pl, g.inv_h));
+        const float gdh = __fmul_rn(ph, g.inv_h);
+        const float gdl = __fadd_rn(__fmaf_rn(ph, g.inv_h, -gdh), __fmul_rn(pl, g.inv_h));
+        m.g0[a] = to_fixed(g0h, g0l);
+        m.gd[a] = to_fixed(gdh, gdl);
     }
 }
 
-__device__ __forceinline__ float march_coord(const March& m, int a, float fi)
+// Position of sample i.
+__device__ __forceinline__ void march_pos(const March& m, int i, long long q[3])
 {
-    return __fmaf_rn(fi, m.gdh[a], m.g0h[a]) + __fmaf_rn(fi, m.gdl[a], m.g0l[a]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q[a] = m.g0[a] + (long long)i * m.gd[a];
+}
+
+// One sample further (+1) or back (-1).
+__device__ __forceinline__ void march_next(const March& m, long long q[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q[a] += m.gd[a];
+}
+__device__ __forceinline__ void march_prev(const March& m, long long q[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q[a] -= m.gd[a];
 }
 
 // Trilinear interpolation at grid coordinate g (clamped to the box), split
@@ -340,18 +407,62 @@ struct Cell {
     float2 vz[4];
 };
 
-// Cell of grid coordinate gc: corner index, fractions, clamp flags.
-__device__ __forceinline__ void cell_locate(const Grid& G, const float gc[3], Cell& c)
+// Cell of the fixed-point position q: corner index, fractions, clamp
+// flags. Only the two 32-bit halves of q are used: hi holds the integer
+// part and the top 8 fraction bits. A coordinate outside [0, n - 1] is
+// clamped (zero derivative along that axis), and n - 1 itself lies in the
+// last cell at fraction 1. Both happen only at the ends of a ray, so they
+// are handled apart from the common case (every coordinate in [0, n - 1)),
+// which takes one comparison per axis.
+// One axis of a position at or beyond the box (the rare case of
+// cell_locate): the clamped cell, fraction and inside flag, packed as
+// cell | inside << 31 and the fraction.
+struct AxisClamp {
+    unsigned cell_in;
+    float fr;
+};
+
+static __device__ __noinline__ AxisClamp clamp_axis(long long q, int n)
+{
+    AxisClamp r;
+    const bool in = (unsigned long long)q <= ((unsigned long long)(n - 1) << kFixBits);
+    const int ji = (int)(q >> kFixBits);
+    int j;
+    if (q < 0) {
+        j = 0;
+        r.fr = 0.f;
+    } else if (ji > n - 2) {
+        j = n - 2;
+        r.fr = 1.f;
+    } else {
+        j = ji;
+        r.fr = __uint2float_rn((unsigned)(q >> (kFixBits - 32))) * 0x1p-32f;
+    }
+    r.cell_in = (unsigned)j | (in ? 0x80000000u : 0u);
+    return r;
+}
+
+__device__ __forceinline__ void cell_locate(const Grid& G, const long long q[3], Cell& c)
 {
     int j[3];
     float fr[3];
+    bool edge = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float hi = (float)(G.n[a] - 1);
-        const float gg = fminf(fmaxf(gc[a], 0.f), hi);
-        c.in[a] = gg == gc[a];        // 0 <= gc <= hi (false for NaN, as the comparisons)
-        j[a] = min((int)gg, G.n[a] - 2);
-        fr[a] = gg - (float)j[a];
+        const int hi = (int)(q[a] >> 32);
+        j[a] = hi >> (kFixBits - 32);
+        fr[a] = __uint2float_rn((unsigned)(q[a] >> (kFixBits - 32))) * 0x1p-32f;
+        c.in[a] = true;
+        edge |= (unsigned)hi >= (unsigned)G.top[a];   // below 0, or at or past n - 1
+    }
+    if (edge) {                                       // a call, so the common path stays short
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const AxisClamp r = clamp_axis(q[a], G.n[a]);
+            j[a] = (int)(r.cell_in & 0x7fffffffu);
+            c.in[a] = (r.cell_in >> 31) != 0u;
+            fr[a] = r.fr;
+        }
     }
     c.fx = fr[0]; c.fy = fr[1]; c.fz = fr[2];
     c.base = (uint32_t)j[0] + (uint32_t)G.n[0] * ((uint32_t)j[1] + (uint32_t)G.n[1] * (uint32_t)j[2]);
@@ -373,10 +484,10 @@ __device__ __forceinline__ void cell_load(const VT* __restrict__ vol, const Grid
 }
 
 template <typename VT>
-__device__ __forceinline__ void cell_fetch(const VT* __restrict__ vol, const Grid& G, const float gc[3],
+__device__ __forceinline__ void cell_fetch(const VT* __restrict__ vol, const Grid& G, const long long q[3],
                                            Cell& c)
 {
-    cell_locate(G, gc, c);
+    cell_locate(G, q, c);
     cell_load<VT>(vol, G, c);
 }
 
@@ -426,17 +537,64 @@ __device__ __forceinline__ float cell_value_grad(const Cell& c, float dg[3])
     return fmaf(c.fz, dz, f.x);
 }
 
+// The density of a sample as the unevaluated pair v0 + dd: v0 the stored
+// value of corner (0, 0, 0) and dd the trilinear interpolation (the same
+// lerps as cell_value) of the corners' differences from it. Neighbouring
+// values differ little, so dd carries rounding errors of the size of those
+// differences rather than of the density: within ~1e-9 of the exact
+// trilinear value of a smooth field, where one binary32 result is within
+// ~1e-7. The transfer function amplifies the density's error by the slope
+// of its rows (tau changes by up to 750 per unit density on a 16-row TF of
+// tau in [0, 50]): images from the rounded density were off by up to 4e-5
+// relative per element, from the pair by ~1e-6.
+struct Density {
+    float v0, dd;
+};
+
+__device__ __forceinline__ float density_value(const Density& d) { return d.v0 + d.dd; }
+
+__device__ __forceinline__ Cell cell_relative(const Cell& c, float v0)
+{
+    Cell r = c;
+    const float2 b = p2dup(v0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.vz[k] = p2sub(c.vz[k], b);
+    return r;
+}
+
+__device__ __forceinline__ Density cell_density(const Cell& c)
+{
+    const float v0 = c.vz[0].x;
+    return {v0, cell_value(cell_relative(c, v0))};
+}
+
+// The same with the derivative w.r.t. the grid coordinate (the differences
+// have the derivative of the values).
+__device__ __forceinline__ Density cell_density_grad(const Cell& c, float dg[3])
+{
+    const float v0 = c.vz[0].x;
+    return {v0, cell_value_grad(cell_relative(c, v0), dg)};
+}
+
+// S += dt d for the absorption model (tau = d), the density as its pair:
+// the exact product dt v0 through depth_add, dt dd into the low part.
+__device__ __forceinline__ void depth_add_density(float& sh, float& sl, float dt, const Density& d)
+{
+    depth_add(sh, sl, dt, d.v0);
+    sl = __fmaf_rn(dt, d.dd, sl);
+}
+
 template <typename VT>
 __device__ __forceinline__ void fetch_sample(const VT* __restrict__ vol, const Grid& G, const March& m,
                                              int i, Cell& c)
 {
-    const float fi = (float)i;
-    const float gc[3] = {march_coord(m, 0, fi), march_coord(m, 1, fi), march_coord(m, 2, fi)};
-    cell_fetch<VT>(vol, G, gc, c);
+    long long q[3];
+    march_pos(m, i, q);
+    cell_fetch<VT>(vol, G, q, c);
 }
 
-// The march's fetch of sample i when the previous sample (in march order)
-// lies in cell `prev_base`: if sample i is in the same cell, no corner is
+// The march's fetch of the sample at q when the previous sample (in march
+// order) lies in cell `prev_base`: if it is in the same cell, no corner is
 // loaded (the lane sits out the warp's load instructions, which then touch
 // fewer cache sectors) and c.reuse is set; cell_resolve later copies the
 // corners from the previous sample once those have arrived.
@@ -446,11 +604,10 @@ struct MCell {
 };
 
 template <typename VT>
-__device__ __forceinline__ void fetch_sample_reuse(const VT* __restrict__ vol, const Grid& G, const March& m,
-                                                   float fi, uint32_t prev_base, MCell& mc)
+__device__ __forceinline__ void fetch_sample_reuse(const VT* __restrict__ vol, const Grid& G, const long long q[3],
+                                                   uint32_t prev_base, MCell& mc)
 {
-    const float gc[3] = {march_coord(m, 0, fi), march_coord(m, 1, fi), march_coord(m, 2, fi)};
-    cell_locate(G, gc, mc.c);
+    cell_locate(G, q, mc.c);
     mc.reuse = mc.c.base == prev_base;
     if (!mc.reuse) cell_load<VT>(vol, G, mc.c);
 }
@@ -491,14 +648,18 @@ struct TFCache {
 
 __device__ __forceinline__ void tf_cache_init(TFCache& t) { t.k = -1; }
 
-__device__ __forceinline__ void tf_lookup(const float4* __restrict__ tf, int R, float d, TFCache& t,
+__device__ __forceinline__ void tf_lookup(const float4* __restrict__ tf, int R, const Density& d, TFCache& t,
                                           TFSample& s)
 {
-    const float dc = fminf(fmaxf(d, 0.f), 1.f);
-    s.slope = dc == d;                // 0 <= d <= 1
-    const float u = __fmul_rn(dc, (float)(R - 1));   // rounded, then the exact difference
+    const float dv = density_value(d);
+    const float dc = fminf(fmaxf(dv, 0.f), 1.f);
+    s.slope = dc == dv;               // 0 <= d <= 1
+    const float Rm1 = (float)(R - 1);
+    // segment from the rounded position, fraction from the pair: (v0 (R-1)
+    // - k) is one rounding of a number below 2, to which dd (R-1) adds
+    const float u = s.slope ? __fmaf_rn(d.dd, Rm1, __fmul_rn(d.v0, Rm1)) : __fmul_rn(dc, Rm1);
     s.k = min((int)u, R - 2);
-    s.fr = __fsub_rn(u, (float)s.k);
+    s.fr = s.slope ? __fmaf_rn(d.dd, Rm1, __fmaf_rn(d.v0, Rm1, -(float)s.k)) : __fsub_rn(u, (float)s.k);
     if (s.k != t.k) {
         t.a = tf[2 * s.k];
         t.dc = tf[2 * s.k + 1];

@@ -4,10 +4,10 @@
 // front-to-back blending (Eq. blend-forward) in registers. The ray's optical
 // depth S = sum dt tau_i is accumulated as an unevaluated float pair and
 // stored, so the adjoint can recover every transmittance exp(-S_i) without
-// a per-step record (Sec. 4.4). The blend weight (1 - A_i) alpha_i is taken
-// as the difference of consecutive transmittances exp(-S_i) - exp(-S_{i+1}),
-// the same value as the product form, with one exponential per sample; its
-// rounding errors telescope in the colour sum.
+// a per-step record (Sec. 4.4). The blend weight (1 - A_i) alpha_i is the
+// product of the transmittance before the sample, exp(-S_i), and the
+// sample's opacity; the colour is summed in blocks of 64 samples
+// (sample_alpha and kColourBlock in the device header).
 #include "dvr_device.cuh"
 #include "dvr_launch.h"
 
@@ -52,7 +52,8 @@ forward_kernel(const __grid_constant__ Params p)
         make_march(R, G, m);
 
         float sh = 0.f, sl = 0.f;    // optical depth, hi + lo
-        float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+        float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;   // colour of the finished blocks
+        float P0 = 0.f, P1 = 0.f, P2 = 0.f;            // colour of the current block
         // checkpoints of this ray: slot m holds 1 - A before sample m K
         float* ck = CKPT && valid ? p.ckpt + (vw.pixel_offset + (long long)py * vw.width + px) * p.ckpt_slots
                                   : nullptr;
@@ -60,18 +61,21 @@ forward_kernel(const __grid_constant__ Params p)
         // software pipeline: the corners of samples i+1 and i+2 are in
         // flight while sample i is composited (positions past the ray end are
         // clamped to the box, so the extra fetches stay in bounds); a sample
-        // in the same cell as its predecessor loads nothing
+        // in the same cell as its predecessor loads nothing. Positions are
+        // fixed point, stepped by exact integer additions.
         TFCache tfc;
         tf_cache_init(tfc);
         MCell n1, n2;
         float2 last_v[4];
+        long long q[3] = {m.g0[0], m.g0[1], m.g0[2]};   // position of the next fetch
         if (N > 0) {
-            fetch_sample_reuse<VT>(vol, G, m, 0.f, 0xffffffffu, n1);
-            fetch_sample_reuse<VT>(vol, G, m, 1.f, n1.c.base, n2);
+            fetch_sample_reuse<VT>(vol, G, q, 0xffffffffu, n1);
+            march_next(m, q);
+            fetch_sample_reuse<VT>(vol, G, q, n1.c.base, n2);
+            march_next(m, q);
         }
-        float f2 = 2.f;                // sample index i + 2 (exact below 2^24)
 #pragma unroll 3
-        for (int i = 0; i < N; ++i, f2 += 1.f) {
+        for (int i = 0; i < N; ++i) {
             if (CKPT) {
                 if (ck_left == 0) {
                     if (ck && ck_m < p.ckpt_slots) ck[ck_m] = T;
@@ -85,23 +89,29 @@ forward_kernel(const __grid_constant__ Params p)
 #pragma unroll
             for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
             n1 = n2;
-            fetch_sample_reuse<VT>(vol, G, m, f2, n1.c.base, n2);
+            fetch_sample_reuse<VT>(vol, G, q, n1.c.base, n2);      // sample i + 2
+            march_next(m, q);
             const Cell& c = cur.c;
-            const float d = cell_value(c);
+            const Density d = cell_density(c);
             if (MODEL == DVR_EMISSION_ABSORPTION) {
                 TFSample s;
                 tf_lookup(tf_s, p.R, d, tfc, s);
+                const float alpha = sample_alpha(G.dt, s.c.w);
                 depth_add(sh, sl, G.dt, s.c.w);      // S_{i+1} = S_i + dt tau_i
-                const float Tn = transmittance(sh, sl);   // 1 - A_{i+1}
-                const float wgt = T - Tn;             // (1 - A_i) alpha_i
-                C0 = fmaf(wgt, s.c.x, C0);
-                C1 = fmaf(wgt, s.c.y, C1);
-                C2 = fmaf(wgt, s.c.z, C2);
-                T = Tn;
+                const float wgt = T * alpha;          // (1 - A_i) alpha_i
+                P0 = fmaf(wgt, s.c.x, P0);
+                P1 = fmaf(wgt, s.c.y, P1);
+                P2 = fmaf(wgt, s.c.z, P2);
+                if ((i & (kColourBlock - 1)) == kColourBlock - 1) {
+                    C0 += P0; C1 += P1; C2 += P2;
+                    P0 = 0.f; P1 = 0.f; P2 = 0.f;
+                }
+                T = transmittance(sh, sl);            // 1 - A_{i+1}
             } else {
-                depth_add(sh, sl, G.dt, d);
+                depth_add_density(sh, sl, G.dt, d);
             }
         }
+        C0 += P0; C1 += P1; C2 += P2;
         if (valid) {
             const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
             const float A = -expm1f(-(sh + sl));

@@ -139,6 +139,7 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
     const float Rm1 = (float)(p.R - 1);
 
     float sh = 0.f, sl = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+    float P0 = 0.f, P1 = 0.f, P2 = 0.f;          // the forward kernel's block sums
     float dC[3][3] = {}, dT[3] = {0.f, 0.f, 0.f}, dS[3] = {0.f, 0.f, 0.f};
     TFCache tfc;
     tf_cache_init(tfc);
@@ -149,7 +150,7 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
         cell_decode<VT>(c);
         fetch_sample<VT>(vol, G, m, i + 1, nxt);
         float dg[3];
-        const float d = cell_value_grad(c, dg);
+        const Density d = cell_density_grad(c, dg);
         const float ti = (float)i * G.dt;
         float dd[3];                              // d(density)/d(eye)
 #pragma unroll
@@ -162,9 +163,11 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
         if (EA) {
             TFSample s;
             tf_lookup(tf_s, p.R, d, tfc, s);
+            const float alpha = sample_alpha(G.dt, s.c.w);
             depth_add(sh, sl, G.dt, s.c.w);         // S_{i+1}
             const float Tn = transmittance(sh, sl);  // the forward kernel's roundings
-            const float wgt = T - Tn;
+            const float wgt = T * alpha;
+            const bool block_end = (i & (kColourBlock - 1)) == kColourBlock - 1;
             const float sl_ = s.slope ? Rm1 : 0.f;
             const float dtau = G.dt * s.dc.w;
 #pragma unroll
@@ -172,22 +175,29 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
                 const float dk = sl_ * dd[k];        // d(segment position)/d(eye)
                 dS[k] = fmaf(dtau, dk, dS[k]);       // d S_{i+1} / d(eye)
                 const float dTn = -Tn * dS[k];
-                const float dwgt = dT[k] - dTn;
+                // d(T_i alpha_i) = dT_i alpha_i + T_i (1 - alpha_i) d(dt tau_i),
+                // T_i (1 - alpha_i) = T_{i+1}
+                const float dwgt = fmaf(dT[k], alpha, Tn * (dtau * dk));
                 dC[0][k] = fmaf(dwgt, s.c.x, fmaf(wgt * s.dc.x, dk, dC[0][k]));
                 dC[1][k] = fmaf(dwgt, s.c.y, fmaf(wgt * s.dc.y, dk, dC[1][k]));
                 dC[2][k] = fmaf(dwgt, s.c.z, fmaf(wgt * s.dc.z, dk, dC[2][k]));
                 dT[k] = dTn;
             }
-            C0 = fmaf(wgt, s.c.x, C0);
-            C1 = fmaf(wgt, s.c.y, C1);
-            C2 = fmaf(wgt, s.c.z, C2);
+            P0 = fmaf(wgt, s.c.x, P0);
+            P1 = fmaf(wgt, s.c.y, P1);
+            P2 = fmaf(wgt, s.c.z, P2);
+            if (block_end) {
+                C0 += P0; C1 += P1; C2 += P2;
+                P0 = 0.f; P1 = 0.f; P2 = 0.f;
+            }
             T = Tn;
         } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k) dS[k] = fmaf(G.dt, dd[k], dS[k]);
-            depth_add(sh, sl, G.dt, d);
+            depth_add_density(sh, sl, G.dt, d);
         }
     }
+    C0 += P0; C1 += P1; C2 += P2;
     const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
     const float S = sh + sl;
     if (EA) {

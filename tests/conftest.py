@@ -28,3 +28,18 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """With DVR_PARITY_REPORT=<path>, write every comparison the GPU parity
+    tests made (per-element error with and without the kink slack, and the
+    max-norm error) as JSON lines."""
+    path = os.environ.get("DVR_PARITY_REPORT")
+    helpers = sys.modules.get("tests.gpu_helpers")
+    if not path or helpers is None:
+        return
+    import json
+    with open(path, "w") as f:
+        for what, e, raw, mx in helpers.RECORD:
+            f.write(json.dumps({"what": what, "per_element": e, "per_element_no_slack": raw,
+                                "max_norm": mx}) + "\n")
