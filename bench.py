@@ -1,33 +1,41 @@
 #!/usr/bin/env python
 """Forward + adjoint throughput of the differentiable volume renderer.
 
-One step = one pass of the whole hot path over the 256^3 emission-absorption
-workload: orbit camera -> forward march (Alg. 1) -> L2 loss seed ->
-constant-memory adjoint (Alg. 2) with TF and camera gradients -> orbit
-camera adjoint. Metric: ray samples (each visited by the forward and by the
-adjoint) per second of step, in Gsamples/s.
+One step = one pass of the whole hot path over the largest workload that
+one GPU holds: a 1024^3 FP16 volume (value noise + 32 Gaussian blobs), a
+32-point TF, 32 views of 2048^2 at step 0.25 voxel (135 G ray samples per
+pass): forward march (Alg. 1) -> opacity-entropy loss and its seed
+(Sec. 5.1) -> constant-memory adjoint (Alg. 2) with the volume, TF and
+camera gradients. Metric: ray samples (each visited by the forward and by
+the adjoint) per second of step, in Gsamples/s.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload ea_256|absorption_64|tomo_256x64|ea_bf16_512|ea_fp16_1024]
+                    [--workload ea_fp16_1024|ea_256|absorption_64|tomo_256x64|ea_bf16_512]
 
 Timing: the tile widths are autotuned per pass (L2 flushed before each timed
-pass); W warm-up steps, then K steps each bracketed by CUDA events with a
-512 MiB write flushing L2 between steps, outside the brackets. `value` comes
-from the mean step of the step captured once as a CUDA graph and replayed
-(--eager: launched step by step; `ms_per_step_stats` gives the median,
-minimum and maximum of those K steps); forward_ms / adjoint_ms come from
-eager steps. The 512^3 and 1024^3 workloads run in their own BF16 / FP16
-storage (the arithmetic is binary32 throughout) and `storage_variants`
-times the other storage form of the same workload. NVML samples
-the SM clock and throttle reasons during the timed region. The roofline
-divides the adjoint's algorithmic bytes by its event time and compares them
-with the measured HBM copy bandwidth (MEASURED_PEAKS.json) and with the L2 /
-L1 / reduction ceilings measured in the same run (dvr_probe); `traffic` is
-the DRAM bytes of the committed ncu summary of that kernel, when it was
-taken on the kernel's current sources. `e2e` copies the step's inputs from
-pinned host memory and reads the results back every step, through the
-public binding. `cpu_baseline` times the FP64 oracle on a strided sample of
-the same rays on the host cores.
+pass; views beyond the first four are left out of the tuning runs of
+workloads whose step takes longer than a second); W warm-up steps, then K
+steps each bracketed by CUDA events with a 512 MiB write flushing L2 between
+steps, outside the brackets. `value` comes from the mean step of the step
+captured once as a CUDA graph and replayed (--eager: launched step by
+step; `ms_per_step_stats` gives the median, minimum and maximum of those K
+steps). The secondary legs (forward / adjoint breakdown from eager steps,
+e2e, the other storage form, the camera-gradient modes) run
+`secondary_steps` steps each, enough for ~10 s of work, so that the whole
+run ends within a few minutes. The 512^3 and 1024^3 workloads run in their
+own BF16 / FP16 storage (the arithmetic is binary32 throughout) and
+`storage_variants` times the other storage form of the same workload
+(binary32 beside 16-bit). NVML samples the SM clock and throttle reasons
+during the timed region. The roofline divides the adjoint's algorithmic
+bytes by its event time and compares them with the measured HBM copy
+bandwidth (MEASURED_PEAKS.json) and with the L2 / L1 / reduction ceilings
+measured in the same run (dvr_probe); `traffic` is the DRAM bytes of the
+committed ncu summary of that kernel, when it was taken on the kernel's
+current sources. `e2e` copies the step's inputs from pinned host memory and
+reads the results back every step, through the public binding.
+`cpu_baseline` times the FP64 oracle on a strided sample of the same rays
+on the host cores. `accuracy` compares seeded pixels and the gradients of a
+seed supported on them with the FP64 oracle, element by element.
 
 Under torchrun each rank renders its own replica of the workload (the rays
 of different problems are independent; no collective on the data path) and
@@ -60,10 +68,10 @@ METRIC = "forward+adjoint Gsamples/s and % gather roofline vs plain FP32 at stat
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="ea_256")
+    ap.add_argument("--workload", default="ea_fp16_1024")
     ap.add_argument("--tf-immediate", action="store_true", help="adjoint-immediate TF accumulation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -72,6 +80,9 @@ def parse():
     ap.add_argument("--tile-width", type=int, default=0, help="fix the warp tile width (1..32)")
     ap.add_argument("--no-variants", action="store_true", help="skip the BF16/FP16 storage comparison")
     ap.add_argument("--eager", action="store_true", help="time eagerly launched steps instead of a CUDA graph")
+    ap.add_argument("--views", type=int, default=0,
+                    help="keep only the first N views (a smaller case of the workload, e.g. for ncu)")
+    ap.add_argument("--image", type=int, default=0, help="render every view at S x S pixels (smaller case)")
     return ap.parse_args()
 
 
@@ -219,7 +230,9 @@ class Workload:
     workload's own dtypes (BF16 / FP16 for the 512^3 and 1024^3 workloads)
     unless others are given (the FP32 form is the plain one)."""
 
-    def __init__(self, name, device, tf_immediate=False, vol_dtype=None, tf_dtype=None):
+    def __init__(self, name, device, tf_immediate=False, vol_dtype=None, tf_dtype=None, views=0, image=0):
+        import dataclasses
+
         import torch
 
         import paper_2107_12672_b300 as dvr
@@ -227,6 +240,15 @@ class Workload:
         self.dvr = dvr
         self.torch = torch
         w = syn.workload(name)
+        # a smaller case of the same workload (profiling stand-ins): its
+        # first `views` views, each `image` pixels square
+        if views:
+            w.views, w.eye = w.views[:views], w.eye[:views]
+            if w.orbit is not None:
+                w.orbit = w.orbit[:views]
+        if image:
+            w.views = [dataclasses.replace(v, width=image, height=image) for v in w.views]
+        self.reduced = {"views": views or None, "image": image or None} if (views or image) else None
         self.w = w
         self.name = name
         self.device = device
@@ -345,6 +367,7 @@ class Workload:
             "samples_per_pass": self.samples_per_pass,
             "loss": {"l2": "L2 against the target image", "entropy": "opacity entropy (Sec. 5.1), maximised"}[w.loss],
             "note": w.note,
+            "reduced_case": self.reduced,
         }
 
 
@@ -394,15 +417,33 @@ def probe_ceilings(dev):
     return out
 
 
+def _errs(a, b, slack=None):
+    """The parity tests' two error forms: per element, (|a - b| - slack)+ /
+    max(|b|, 1e-3 max|b|) (the bar: 1e-5 for images, 1e-3 for gradients),
+    and the max-norm form |a - b| / (|b| + max|b|)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    d = np.abs(a - b)
+    s = np.abs(b).max() if b.size else 0.0
+    if s == 0:
+        return {"per_element": float(d.max()) if d.size else 0.0, "max_norm": float(d.max()) if d.size else 0.0}
+    out = {"max_norm": float((d / (np.abs(b) + s)).max()),
+           "per_element": float((d / np.maximum(np.abs(b), 1e-3 * s)).max())}
+    if slack is not None:
+        out["per_element_beyond_kink_bound"] = float((np.maximum(d - slack, 0.0) / np.maximum(np.abs(b), 1e-3 * s)).max())
+    return out
+
+
 def sampled_accuracy(wl, per_view=64, n_views=4, seed=21):
     """accuracy() for workloads whose views are too large for the oracle to
     render whole: seeded pixel samples of the first views, with dL/d(image)
     non-zero only on them, so the oracle computes the exact gradients of the
-    same seed; every voxel of the volume gradient is compared (the oracle
-    reads the stored BF16 / FP16 values exactly). `*_beyond_kink_bound`
-    subtracts, per element, the oracle's bound on what binary32 rounding may
-    change where a sample lies on a cell face or TF control point (the
-    parity tests' slack)."""
+    same seed. The volume gradient is compared on every vertex those rays
+    read (the oracle returns it compactly there; a 1024^3 volume needs no
+    dense binary64 array) and must be exactly zero on every other vertex.
+    `per_element_beyond_kink_bound` subtracts, per element, the oracle's
+    bound on what binary32 rounding may change where a sample lies on a cell
+    face or TF control point (the parity tests' slack)."""
     import torch
 
     import oracle
@@ -422,58 +463,50 @@ def sampled_accuracy(wl, per_view=64, n_views=4, seed=21):
         Gs.append(gk)
         G[torch.as_tensor(offs[k] + pk, device=wl.device)] = torch.as_tensor(gk, device=wl.device)
     want = tuple(wl.want)
-    # the oracle's dense binary64 volume gradient (and its kink bound) of a
-    # 1024^3 volume would take 16 GB of host memory: compared up to 512^3
-    dense = wl.vol[0].numel() <= 512 ** 3
-    if not dense:
-        want = tuple(x for x in want if x != "volume")
     g = dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=wl.scene, want=want)
     torch.cuda.synchronize()
+    imgh = np.concatenate([img[offs[k] + torch.as_tensor(picks[k], device=wl.device)].cpu().numpy()
+                           for k in range(len(views))])
+    del img, aux, G
     vol = wl.vol[0].float().cpu().numpy()
     tf = wl.tf.float().cpu().numpy().astype(np.float64) if wl.tf is not None else None
-    imgh = img.cpu().numpy()
-
-    def rel(a, b, slack=None):
-        a = np.asarray(a, np.float64)
-        d = np.abs(a - b)
-        if slack is not None:
-            d = np.maximum(d - slack, 0.0)
-        return float((d / (np.abs(b) + np.abs(b).max())).max())
-
-    ref_vol = np.zeros(vol.shape) if "volume" in want else None
-    amb_vol = np.zeros(vol.shape) if "volume" in want else None
+    sel = None
+    if "volume" in want:
+        sel = np.unique(np.concatenate([oracle.touched(vol.shape, view, w.eye[k], w.step_voxels, pix=picks[k])
+                                        for k, view in enumerate(views)]))
+        ref_vol = np.zeros(sel.size)
+        amb_vol = np.zeros(sel.size)
     ref_tf = np.zeros((tf.shape[0], 4)) if (tf is not None and "tf" in want) else None
-    e_img, e_eye, e_eye_k = [], [], []
+    ref_img, e_eye = [], []
     for k, view in enumerate(views):
         ri, _, _ = oracle.render(vol, tf, w.model, view, w.eye[k], w.step_voxels, pix=picks[k])
-        e_img.append(rel(imgh[offs[k] + picks[k]], ri))
+        ref_img.append(ri)
         rg = oracle.backward(vol, tf, w.model, view, w.eye[k], w.step_voxels, Gs[k], pix=picks[k],
-                             want=want, margin=2.0)
-        if ref_vol is not None:
+                             want=want, margin=2.0, sel=sel)
+        if sel is not None:
             ref_vol += rg["volume"]
             amb_vol += rg["volume_ambiguity"]
         if ref_tf is not None:
             ref_tf += rg["tf"]
         if "eye" in rg:
-            ge = g["eye"][k].cpu().numpy()
-            e_eye.append(rel(ge, rg["eye"]))
-            e_eye_k.append(rel(ge, rg["eye"], rg["eye_ambiguity"]))
+            e_eye.append((g["eye"][k].cpu().numpy(), rg["eye"], rg["eye_ambiguity"]))
     out = {"reference": f"FP64 oracle, same stored inputs, {len(views)} views x {per_view} seeded pixels "
                         "(dL/d(image) non-zero only there)",
-           "definition": "max_i |gpu - ref| / (|ref| + max|ref|)",
-           "image": max(e_img)}
-    if ref_vol is not None:
-        gv = g["volume"][0].cpu().numpy()
-        out["grad_volume_per_voxel"] = rel(gv, ref_vol)
-        out["grad_volume_beyond_kink_bound"] = rel(gv, ref_vol, amb_vol)
+           "definition": "per_element: max_i |gpu - ref| / max(|ref_i|, 1e-3 max|ref|) (bar: 1e-5 image, "
+                         "1e-3 gradients); max_norm: max_i |gpu - ref| / (|ref_i| + max|ref|)",
+           "image": _errs(imgh, np.concatenate(ref_img))}
+    if sel is not None:
+        flat = g["volume"][0].view(-1)
+        idx = torch.as_tensor(sel, device=flat.device)
+        out["grad_volume"] = _errs(flat[idx].cpu().numpy(), ref_vol, amb_vol)
+        out["grad_volume"]["vertices_compared"] = int(sel.size)
+        flat[idx] = 0.0
+        out["grad_volume"]["nonzero_outside_the_rays"] = int(torch.count_nonzero(flat))
     if ref_tf is not None:
-        out["grad_tf"] = rel(g["tf"].cpu().numpy(), ref_tf)
+        out["grad_tf"] = _errs(g["tf"].cpu().numpy(), ref_tf)
     if e_eye:
-        out["grad_eye"] = max(e_eye)
-        out["grad_eye_beyond_kink_bound"] = max(e_eye_k)
-    if not dense and "volume" in wl.want:
-        out["grad_volume_per_voxel"] = None
-        out["grad_volume_note"] = "not compared above 512^3 voxels (host memory of the dense oracle gradient)"
+        out["grad_eye"] = _errs(np.stack([a for a, _, _ in e_eye]), np.stack([b for _, b, _ in e_eye]),
+                                np.stack([c for _, _, c in e_eye]))
     out["views_checked"] = len(views)
     return out
 
@@ -481,9 +514,9 @@ def sampled_accuracy(wl, per_view=64, n_views=4, seed=21):
 def accuracy(wl):
     """Errors of one forward + adjoint against the FP64 oracle on identical
     inputs (the workload's seeded eye positions; volume and TF as stored on
-    the device). Relative per element to (|ref| + max|ref|), as in the
-    parity tests; untimed. Views of more than 300,000 pixels in all are
-    checked on pixel samples (sampled_accuracy)."""
+    the device), in the parity tests' two forms (_errs); untimed. Views of
+    more than 300,000 pixels in all are checked on pixel samples
+    (sampled_accuracy)."""
     import torch
 
     import oracle
@@ -502,16 +535,18 @@ def accuracy(wl):
     imgh = img.cpu().numpy()
 
     def rel(a, b):
-        a = np.asarray(a, np.float64)
-        return float((np.abs(a - b) / (np.abs(b) + np.abs(b).max())).max())
+        return _errs(a, b)["per_element"]
 
     out = {"reference": "FP64 oracle, same stored inputs, fixed eye positions",
-           "definition": "max_i |gpu - ref| / (|ref| + max|ref|)"}
+           "definition": "per_element: max_i |gpu - ref| / max(|ref_i|, 1e-3 max|ref|) (bar: 1e-5 image, "
+                         "1e-3 gradients); max_norm: max_i |gpu - ref| / (|ref_i| + max|ref|)"}
     off = 0
     errs_img, ref_tf, ref_eye = [], None, []
+    ref_imgs = []
     for k, view in enumerate(w.views[:4]):
         n = view.width * view.height
         ri, _, _ = oracle.render(vol64, tf64, w.model, view, w.eye[k], w.step_voxels)
+        ref_imgs.append(ri)
         errs_img.append(rel(imgh[off:off + n], ri))
         ow = tuple(x for x in want if x != "volume")
         rg = oracle.backward(vol64, tf64, w.model, view, w.eye[k], w.step_voxels, Gh[off:off + n], want=ow)
@@ -520,13 +555,14 @@ def accuracy(wl):
         if "eye" in rg:
             ref_eye.append((k, rg["eye"]))
         off += n
-    out["image"] = max(errs_img)
+    nimg = sum(v.width * v.height for v in w.views[:4])
+    out["image"] = _errs(imgh[:nimg], np.concatenate(ref_imgs))
     if len(w.views) <= 4:
         if ref_tf is not None:
-            out["grad_tf"] = rel(g["tf"].cpu().numpy(), ref_tf)
+            out["grad_tf"] = _errs(g["tf"].cpu().numpy(), ref_tf)
             if wl.vol[0].dtype == torch.float32 and len(w.views) == 1:
                 # how the opacity before each sample is recovered (Sec. 4.4)
-                inv = {"optical_depth (default)": out["grad_tf"]}
+                inv = {"optical_depth (default)": out["grad_tf"]["per_element"]}
                 for mode in ("alpha64", "alpha32"):
                     gm = dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=wl.scene,
                                       want=("tf",), inversion=mode)
@@ -544,7 +580,8 @@ def accuracy(wl):
                     del ck
                 out["grad_tf_by_inversion"] = inv
     if ref_eye:
-        out["grad_eye"] = max(rel(g["eye"].cpu().numpy()[k], r) for k, r in ref_eye)
+        ge = g["eye"].cpu().numpy()
+        out["grad_eye"] = _errs(np.stack([ge[k] for k, _ in ref_eye]), np.stack([r for _, r in ref_eye]))
     out["views_checked"] = min(4, len(w.views))
     return out
 
@@ -585,7 +622,7 @@ def time_steps(wl, K, W, flush, clocks=None, world=1):
     return step_ms, fwd_ms, bwd_ms, wall, clk
 
 
-def time_steps_graph(wl, K, W, flush, clocks=None, world=1, stats=None):
+def time_steps_graph(wl, K, W, flush, clocks=None, world=1, stats=None, side_steps=3):
     """The same step captured once as a CUDA graph and replayed: K replays
     each bracketed by CUDA events (L2 flushed between replays, outside the
     brackets), after W untimed replays. Returns the mean milliseconds per
@@ -596,7 +633,7 @@ def time_steps_graph(wl, K, W, flush, clocks=None, world=1, stats=None):
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):
-        for _ in range(3):
+        for _ in range(side_steps):
             wl.step()
     torch.cuda.current_stream().wait_stream(side)
     graph = torch.cuda.CUDAGraph()
@@ -689,9 +726,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    wl = Workload(args.workload, dev, args.tf_immediate)
+    wl = Workload(args.workload, dev, args.tf_immediate, views=args.views, image=args.image)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     K = args.steps
+    # one untimed step to size the secondary legs (~10 s of work each)
+    probe_ms, _, _, _, _ = time_steps(wl, 1, 1, flush, None, world)
+    K2 = max(2, min(K, int(math.ceil(10_000.0 / max(probe_ms, 1e-3)))))
+    W2 = min(args.warmup, 2) if probe_ms > 1000.0 else args.warmup
     tuning = None
     if args.tile_width:
         from paper_2107_12672_b300 import autotune
@@ -699,15 +740,24 @@ def run_ours(args):
         tuning = {"width": args.tile_width, "adjoint_width": args.tile_width, "fixed": True}
     elif not args.no_autotune:
         from paper_2107_12672_b300 import autotune
-        tuning = autotune.autotune(wl.scene, wl.eye, wl.w.step_voxels, want=wl.want, l2_flush=flush)
+        tscene, teye, tnote = wl.scene, wl.eye, "all views"
+        if probe_ms > 1000.0 and len(wl.w.views) > 4:
+            # steps of seconds: tune on the first four views (same volume,
+            # TF and view sizes), one timed pass per width and round
+            tscene = wl.dvr.Scene.make(wl.vol, wl.tf, wl.w.model, wl.w.views[:4])
+            teye, tnote = wl.eye[:4].contiguous(), "first 4 views"
+        tuning = autotune.autotune(tscene, teye, wl.w.step_voxels, want=wl.want, l2_flush=flush,
+                                   reps=1 if probe_ms > 1000.0 else 5)
+        tuning["tuned_on"] = tnote
     # per-kernel breakdown from eagerly launched steps; the headline step
     # time from the same step replayed as one CUDA graph
-    eager_ms, fwd_ms, bwd_ms, _, _ = time_steps(wl, K, args.warmup, flush, None, world)
+    eager_ms, fwd_ms, bwd_ms, _, _ = time_steps(wl, K2, W2, flush, None, world)
     step_stats = {}                 # this rank's median / min / max step (graph replays)
     if args.eager:
         step_ms, _, _, wall, clk = time_steps(wl, K, args.warmup, flush, Clocks(local), world)
     else:
-        step_ms, wall, clk = time_steps_graph(wl, K, args.warmup, flush, Clocks(local), world, step_stats)
+        step_ms, wall, clk = time_steps_graph(wl, K, args.warmup, flush, Clocks(local), world, step_stats,
+                                              side_steps=1 if probe_ms > 1000.0 else 3)
     if world > 1:
         t = torch.tensor([step_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -718,26 +768,28 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(wl, args, world)
+        e2e = run_e2e(wl, args, world, K2, W2)
     cpu = acc = variants = camera_modes = None
     if rank == 0 and world == 1:
         if not args.no_accuracy:
             acc = accuracy(wl)
-        if not args.no_cpu_baseline and wl.w.volumes[0] is not None:
-            cpu = cpu_baseline(wl.w, budget_s=12.0)
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(wl, budget_s=12.0)
         if not args.no_variants and "eye" in wl.want:
-            camera_modes = compare_camera_modes(wl, K, args.warmup, flush)
+            camera_modes = compare_camera_modes(wl, K2, W2, flush)
         if not args.no_variants and wl.ea:
             variants = {}
             # the other storage form of the same workload: 16-bit beside a
             # binary32 workload, the plain binary32 form beside a 16-bit one
             plain = wl.w.volume_dtype == "float32" and wl.w.tf_dtype == "float32"
             for vd, td in ((("bfloat16", "float16"),) if plain else (("float32", "float32"),)):
-                wv = Workload(args.workload, dev, args.tf_immediate, vol_dtype=vd, tf_dtype=td)
-                sm, fm, bm, _, _ = time_steps(wv, K, args.warmup, flush)
+                wv = Workload(args.workload, dev, args.tf_immediate, vol_dtype=vd, tf_dtype=td, views=args.views,
+                              image=args.image)
+                sm, fm, bm, _, _ = time_steps(wv, K2, W2, flush)
                 variants[f"volume_{vd}_tf_{td}"] = {
                     "value": round(wv.samples_per_pass / (sm * 1e-3) / 1e9, 4), "unit": "Gsamples/s",
                     "ms_per_step": round(sm, 4), "forward_ms": round(fm, 4), "adjoint_ms": round(bm, 4),
+                    "steps": K2, "launch": "eager launches",
                     "accuracy": None if args.no_accuracy else accuracy(wv),
                     "note": "errors include the rounding of the stored volume and TF"}
                 del wv
@@ -781,6 +833,9 @@ def run_ours(args):
             "dtype": "f32",
             "data": "synthetic (seeded generators; no dataset)",
             "config": cfg,
+            "secondary_steps": {"steps": K2, "warmup": W2,
+                                "legs": "eager breakdown (forward_ms, adjoint_ms), e2e, storage_variants, "
+                                        "camera_gradient_modes"},
             "eager_ms_per_step": round(eager_ms, 4),
             "forward_ms": round(fwd_ms, 4),
             "adjoint_ms": round(bwd_ms, 4),
@@ -812,7 +867,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(wl, args, world):
+def run_e2e(wl, args, world, K, W):
     """Same metric through the public API with host buffers: every step
     copies its inputs (volume, TF, camera parameters) from pinned host memory
     and reads back the loss and the gradients, and the host waits for them.
@@ -845,7 +900,7 @@ def run_e2e(wl, args, world):
         side = torch.cuda.Stream()
         side.wait_stream(compute)
         with torch.cuda.stream(side):
-            for _ in range(3):
+            for _ in range(1 if W < 3 else 3):
                 wl.step(scene=sc)
         compute.wait_stream(side)
         g = torch.cuda.CUDAGraph()
@@ -877,26 +932,28 @@ def run_e2e(wl, args, world):
             done.synchronize()        # the host has the step's loss and gradients
         torch.cuda.synchronize()
 
-    run(max(3, args.warmup))
+    run(max(1, W))
     t0 = time.perf_counter()
-    run(args.steps)
-    dt = (time.perf_counter() - t0) / args.steps
+    run(K)
+    dt = (time.perf_counter() - t0) / K
     h2d = vol_h.numel() * vol_h.element_size() + sum(h.numel() * h.element_size() for _, h in small_in)
     d2h = sum(h.numel() * h.element_size() for h in h_out)
     return {"value": round(world * wl.samples_per_pass / dt / 1e9, 4), "unit": "Gsamples/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 4),
+            "steps": K,
             "how": "step as a replayed CUDA graph; next step's volume copied on a second stream "
                    "during the current step; host waits for each step's loss and gradients"}
 
 
 # ------------------------------------------------------ the CPU oracle arm
 class OraclePass:
-    """The oracle's forward + stored-state adjoint (with the L2 seed, and the
-    orbit chain when the camera is orbit-parameterised) on a strided subset
-    of the rows of the workload's first view; the target image is rendered
-    once, untimed, as on the GPU side."""
+    """The oracle's forward + stored-state adjoint (with the workload's loss
+    seed, and the orbit chain when the camera is orbit-parameterised) on a
+    strided subset of the rows of the workload's first view. The L2 loss's
+    target image is rendered once, untimed, as on the GPU side; the
+    opacity-entropy loss (Sec. 5.1) is taken over the sampled pixels."""
 
-    def __init__(self, w, stride):
+    def __init__(self, w, stride, volume=None):
         import oracle
         oracle.build()
         self.oracle = oracle
@@ -907,12 +964,14 @@ class OraclePass:
             self.eye = oracle.orbit_eye(w.orbit.astype(np.float32).astype(np.float64))[0]
         else:
             self.eye = w.eye[0].astype(np.float64)
-        self.vol = w.volumes[0] if w.volumes and w.volumes[0] is not None else None
+        self.vol = volume if volume is not None else (w.volumes[0] if w.volumes else None)
         if self.vol is None:
             raise ValueError("the oracle baseline needs the volume on the host")
-        tf_t = w.target.get("tf", w.tf)
-        vol_t = w.target.get("volume", self.vol)
-        self.target, _, _ = oracle.render(vol_t, tf_t, w.model, self.view, self.eye, w.step_voxels)
+        self.target = None
+        if w.loss == "l2":
+            tf_t = w.target.get("tf", w.tf)
+            vol_t = w.target.get("volume", self.vol)
+            self.target, _, _ = oracle.render(vol_t, tf_t, w.model, self.view, self.eye, w.step_voxels)
         self.want = tuple({"volume": "volume", "tf": "tf", "camera": "eye"}[g] for g in w.grads)
         self.phase = 0
 
@@ -922,15 +981,47 @@ class OraclePass:
         self.phase = (self.phase + 1) % self.stride
         pix = (rows[:, None] * view.width + np.arange(view.width)[None, :]).reshape(-1).astype(np.int64)
         img, N, _ = o.render(self.vol, w.tf, w.model, view, self.eye, w.step_voxels, pix=pix)
-        G = 2.0 * (img - self.target[pix]) / self.target.size
+        if self.target is not None:
+            G = 2.0 * (img - self.target[pix]) / self.target.size
+        else:
+            _, dH = o.opacity_entropy(img[:, -1])
+            G = np.zeros_like(img)
+            G[:, -1] = -dH          # the loss is -H (maximised)
+        # the dense binary64 volume gradient (8 GB virtual at 1024^3) is
+        # zero-filled lazily by the host OS: only the pages these rays touch
+        # are ever backed
         g = o.backward(self.vol, w.tf, w.model, view, self.eye, w.step_voxels, G, pix=pix, want=self.want)
         if w.orbit is not None and "eye" in g:
             o.orbit_eye_backward(w.orbit, g["eye"][None])
         return int(N.sum()), pix.size
 
 
-def cpu_baseline(w, budget_s=12.0):
-    op = OraclePass(w, stride=8)
+def _host_volume(wl_or_w, name):
+    """The workload's volume on the host as float32 (the values the device
+    holds: binary16 / bfloat16 widen exactly)."""
+    if hasattr(wl_or_w, "vol"):
+        return wl_or_w.vol[0].float().cpu().numpy()
+    w = wl_or_w
+    if w.volumes and w.volumes[0] is not None:
+        return w.volumes[0]
+    import torch
+
+    from paper_2107_12672_b300 import synthetic as syn
+    torch.set_num_threads(os.cpu_count() or 1)
+    v = syn.large_volume(w.target["n"], device="cpu")
+    return v.to(getattr(torch, w.volume_dtype)).float().numpy()
+
+
+def _stride(w):
+    """Rows between sampled rows: about 64 sampled rows of the first view,
+    so that one oracle pass takes seconds at every size."""
+    return max(8, w.views[0].height // 64)
+
+
+def cpu_baseline(wl, budget_s=12.0):
+    w = wl.w
+    stride = _stride(w)
+    op = OraclePass(w, stride=stride, volume=_host_volume(wl, wl.name))
     done, passes, rays = 0, 0, 0
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
@@ -941,20 +1032,22 @@ def cpu_baseline(w, budget_s=12.0):
     dt = time.perf_counter() - t0
     return {"value": round(done / dt / 1e9, 6), "unit": "Gsamples/s", "cores": op.oracle.threads(),
             "kind": "oracle",
-            "sample": f"{passes} passes over every 8th row of the {w.views[0].width}x{w.views[0].height} "
-                      f"image ({rays} rays, {done} samples; forward + L2 seed + stored-state adjoint, "
-                      f"FP64, OpenMP) in {dt:.1f} s"}
+            "sample": f"{passes} passes over every {stride}th row of the {w.views[0].width}x{w.views[0].height} "
+                      f"first view ({rays} rays, {done} samples; forward + {w.loss} seed + stored-state adjoint, "
+                      f"FP64, OpenMP) in {dt:.1f} s; the rate per sample stands for the whole workload"}
 
 
 def run_reference(args):
     """The oracle as the reference arm: rank 0 only, on the host cores; each
-    step is a bounded sample (every 16th row) of the same workload."""
+    step is a bounded sample (every 2*stride-th row of the first view) of
+    the same workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_2107_12672_b300 import synthetic as syn
     w = syn.workload(args.workload)
-    op = OraclePass(w, stride=16)
+    stride = 2 * _stride(w)
+    op = OraclePass(w, stride=stride, volume=_host_volume(w, args.workload))
     for _ in range(args.warmup):
         op()
     t0 = time.perf_counter()
@@ -972,9 +1065,9 @@ def run_reference(args):
         "data": "synthetic", "config": {"workload": args.workload, "parallelism": "host cores"},
         "cpu_baseline": {"value": round(v, 6), "unit": "Gsamples/s", "cores": op.oracle.threads(),
                          "kind": "oracle",
-                         "sample": f"each step: every 16th row of the {w.views[0].width}x{w.views[0].height} "
-                                   f"image, forward + L2 seed + stored-state adjoint (FP64); "
-                                   f"{rays} rays, {n} samples in {dt:.1f} s"},
+                         "sample": f"each step: every {stride}th row of the {w.views[0].width}x"
+                                   f"{w.views[0].height} first view, forward + {w.loss} seed + stored-state "
+                                   f"adjoint (FP64); {rays} rays, {n} samples in {dt:.1f} s"},
         "e2e": {"value": round(v, 6), "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

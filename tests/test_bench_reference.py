@@ -1,7 +1,9 @@
 """The bench's reference arm (the FP64 oracle on the host cores) prints one
 JSON line with the keys of the bench contract, on rank 0 only. CPU only:
-the arm never touches a GPU. Each step is a bounded sample of the default
-workload (every 16th image row), so one step takes a second or two.
+the arm never touches a GPU. The arm is run here on the 256^3 workload
+(every 16th image row per step, a second or two); the default workload of
+both arms is the 1024^3 one, whose host volume alone takes half a minute
+to generate.
 """
 import json
 import os
@@ -13,8 +15,23 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _run(env_extra):
     env = dict(os.environ, **env_extra)
-    return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+    return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                           "--workload", "ea_256"],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+
+
+def test_default_workload_is_the_largest_single_gpu_one():
+    """With no flags both arms run the 1024^3 FP16 workload (32 views of
+    2048^2), the largest of the named workloads."""
+    sys.path.insert(0, ROOT)
+    import bench
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        args = bench.parse()
+    finally:
+        sys.argv = argv
+    assert args.workload == "ea_fp16_1024" and args.gpus == 1
 
 
 def test_reference_arm_prints_one_contract_line():
