@@ -21,7 +21,7 @@ captured once as a CUDA graph and replayed (--eager: launched step by
 step; `ms_per_step_stats` gives the median, minimum and maximum of those K
 steps). The secondary legs (forward / adjoint breakdown from eager steps,
 e2e, the other storage form, the camera-gradient modes) run
-`secondary_steps` steps each, enough for ~10 s of work, so that the whole
+`secondary_steps` steps each, enough for ~6 s of work, so that the whole
 run ends within a few minutes. The 512^3 and 1024^3 workloads run in their
 own BF16 / FP16 storage (the arithmetic is binary32 throughout) and
 `storage_variants` times the other storage form of the same workload
@@ -83,6 +83,10 @@ def parse():
     ap.add_argument("--views", type=int, default=0,
                     help="keep only the first N views (a smaller case of the workload, e.g. for ncu)")
     ap.add_argument("--image", type=int, default=0, help="render every view at S x S pixels (smaller case)")
+    ap.add_argument("--cells", action="store_true",
+                    help="gather from the volumes' cell layouts (remade inside every step)")
+    ap.add_argument("--cell-gradient", action="store_true",
+                    help="accumulate the volume gradient per cell first (DVR_FLAG_CELL_GRADIENT)")
     return ap.parse_args()
 
 
@@ -230,7 +234,8 @@ class Workload:
     workload's own dtypes (BF16 / FP16 for the 512^3 and 1024^3 workloads)
     unless others are given (the FP32 form is the plain one)."""
 
-    def __init__(self, name, device, tf_immediate=False, vol_dtype=None, tf_dtype=None, views=0, image=0):
+    def __init__(self, name, device, tf_immediate=False, vol_dtype=None, tf_dtype=None, views=0, image=0,
+                 cells=False, cell_gradient=False):
         import dataclasses
 
         import torch
@@ -262,7 +267,7 @@ class Workload:
             self.vol = [torch.as_tensor(v).to(device=device, dtype=vdt) for v in w.volumes]
         self.ea = w.model == "emission_absorption"
         self.tf = torch.as_tensor(w.tf).to(device=device, dtype=tdt).contiguous() if self.ea else None
-        self.scene = dvr.Scene.make(self.vol, self.tf, w.model, w.views)
+        self.configure(cells, cell_gradient)
         self.orbit = w.orbit is not None
         if self.orbit:
             self.params = torch.as_tensor(w.orbit.astype(np.float32)).to(device).contiguous()
@@ -316,8 +321,25 @@ class Workload:
                     aux=self.aux, sample_count=self.count)
         torch.cuda.synchronize()
         self.samples_per_pass = int(self.count.item())
-        # our kernels per step: forward, loss (the entropy loss is two), adjoint, orbit and its adjoint
-        self.launches_per_step = 3 + (1 if w.loss == "entropy" else 0) + (2 if self.orbit else 0)
+        # our kernels per step (configure): forward, loss (the entropy loss is
+        # two), adjoint, orbit and its adjoint, the cell layouts and the
+        # cell-gradient passes
+
+    def configure(self, cells, cell_gradient):
+        """Gather from the volumes' cell layouts (remade from the volumes at
+        the start of every step) or their arrays; accumulate the volume
+        gradient per cell first (with a workspace of 32 bytes per cell,
+        allocated once) or into the vertex array."""
+        import torch
+        dvr, w = self.dvr, self.w
+        self.use_cells = bool(cells)
+        self.cells = [dvr.make_cells(v) for v in self.vol] if cells else None
+        self.scene = dvr.Scene.make(self.vol, self.tf, w.model, w.views, cells=self.cells)
+        self.cell_gradient = bool(cell_gradient) and "volume" in tuple(w.grads)
+        self.cg_ws = (torch.empty(dvr.cell_workspace_bytes(self.scene), dtype=torch.uint8, device=self.device)
+                      if self.cell_gradient else None)
+        self.launches_per_step = 3 + (1 if w.loss == "entropy" else 0) + (2 if w.orbit is not None else 0) + \
+            (len(self.vol) if self.use_cells else 0) + (len(self.vol) if self.cell_gradient else 0)
 
     def zero(self):
         self.small.zero_()
@@ -331,6 +353,9 @@ class Workload:
         dvr, w = self.dvr, self.w
         sc = scene or self.scene
         self.zero()
+        if sc.cells is not None:
+            for v, c in zip(sc.volumes, sc.cells):
+                dvr.make_cells(v, out=c)
         if self.orbit:
             dvr.orbit_eye(self.params, eye=self.eye)
         if ev:
@@ -345,7 +370,8 @@ class Workload:
         if ev:
             ev[2].record()
         dvr.backward(None, None, None, None, self.eye, w.step_voxels, self.aux, self.gimg, scene=sc,
-                     grads=self.grads, want=self.want, tf_immediate=self.tf_immediate)
+                     grads=self.grads, want=self.want, tf_immediate=self.tf_immediate,
+                     cell_gradient=self.cell_gradient, workspace=self.cg_ws)
         if ev:
             ev[3].record()
         if self.orbit and "eye" in self.want:
@@ -368,6 +394,8 @@ class Workload:
             "loss": {"l2": "L2 against the target image", "entropy": "opacity entropy (Sec. 5.1), maximised"}[w.loss],
             "note": w.note,
             "reduced_case": self.reduced,
+            "gather_layout": "cells (remade every step)" if self.use_cells else "the volume's array",
+            "volume_gradient_scatter": "per cell, then per vertex" if self.cell_gradient else "per vertex",
         }
 
 
@@ -726,12 +754,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    wl = Workload(args.workload, dev, args.tf_immediate, views=args.views, image=args.image)
+    wl = Workload(args.workload, dev, args.tf_immediate, views=args.views, image=args.image, cells=args.cells,
+                  cell_gradient=args.cell_gradient)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     K = args.steps
     # one untimed step to size the secondary legs (~10 s of work each)
     probe_ms, _, _, _, _ = time_steps(wl, 1, 1, flush, None, world)
-    K2 = max(2, min(K, int(math.ceil(10_000.0 / max(probe_ms, 1e-3)))))
+    K2 = max(2, min(K, int(math.ceil(6_000.0 / max(probe_ms, 1e-3)))))
     W2 = min(args.warmup, 2) if probe_ms > 1000.0 else args.warmup
     tuning = None
     if args.tile_width:
@@ -744,11 +773,15 @@ def run_ours(args):
         if probe_ms > 1000.0 and len(wl.w.views) > 4:
             # steps of seconds: tune on the first four views (same volume,
             # TF and view sizes), one timed pass per width and round
-            tscene = wl.dvr.Scene.make(wl.vol, wl.tf, wl.w.model, wl.w.views[:4])
+            tscene = wl.dvr.Scene.make(wl.vol, wl.tf, wl.w.model, wl.w.views[:4], cells=wl.cells)
             teye, tnote = wl.eye[:4].contiguous(), "first 4 views"
         tuning = autotune.autotune(tscene, teye, wl.w.step_voxels, want=wl.want, l2_flush=flush,
-                                   reps=1 if probe_ms > 1000.0 else 5)
+                                   reps=1 if probe_ms > 1000.0 else 5,
+                                   layouts=(False, True) if not args.cells else (True,),
+                                   cell_gradients=(False, True) if not args.cell_gradient else (True,))
         tuning["tuned_on"] = tnote
+        if tuning["cells"] != wl.use_cells or tuning["cell_gradient"] != wl.cell_gradient:
+            wl.configure(tuning["cells"], tuning["cell_gradient"])
     # per-kernel breakdown from eagerly launched steps; the headline step
     # time from the same step replayed as one CUDA graph
     eager_ms, fwd_ms, bwd_ms, _, _ = time_steps(wl, K2, W2, flush, None, world)
@@ -783,8 +816,9 @@ def run_ours(args):
             # binary32 workload, the plain binary32 form beside a 16-bit one
             plain = wl.w.volume_dtype == "float32" and wl.w.tf_dtype == "float32"
             for vd, td in ((("bfloat16", "float16"),) if plain else (("float32", "float32"),)):
+                # with the gather layout and scatter of the headline workload
                 wv = Workload(args.workload, dev, args.tf_immediate, vol_dtype=vd, tf_dtype=td, views=args.views,
-                              image=args.image)
+                              image=args.image, cells=wl.use_cells, cell_gradient=wl.cell_gradient)
                 sm, fm, bm, _, _ = time_steps(wv, K2, W2, flush)
                 variants[f"volume_{vd}_tf_{td}"] = {
                     "value": round(wv.samples_per_pass / (sm * 1e-3) / 1e9, 4), "unit": "Gsamples/s",
@@ -892,7 +926,8 @@ def run_e2e(wl, args, world, K, W):
     h_out = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
 
     bufs = [wl.vol[0], torch.empty_like(wl.vol[0])]
-    scenes = [wl.scene, dvr.Scene.make([bufs[1]], wl.tf, wl.w.model, wl.w.views)]
+    cells1 = [torch.empty_like(wl.cells[0])] if wl.cells is not None else None
+    scenes = [wl.scene, dvr.Scene.make([bufs[1]], wl.tf, wl.w.model, wl.w.views, cells=cells1)]
     compute = torch.cuda.current_stream()
     copier = torch.cuda.Stream()
     graphs = []

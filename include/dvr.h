@@ -77,7 +77,7 @@
 extern "C" {
 #endif
 
-#define DVR_ABI_VERSION 7
+#define DVR_ABI_VERSION 8
 
 /* exported from the shared library (which hides everything else) */
 #if defined(__GNUC__)
@@ -121,15 +121,53 @@ extern "C" {
  * A > 0.99. Other configurations return DVR_ERR_UNSUPPORTED. */
 #define DVR_FLAG_INVERT_ALPHA32 2u
 #define DVR_FLAG_INVERT_ALPHA64 4u
+/* add the volume gradient per cell first: each ray's run of contributions
+ * to one cell (Sec. 4.4, flushed on exit of the cell) goes as two 16-byte
+ * vector reductions into a cell-major array in the workspace (32 bytes per
+ * cell, at least dvr_backward_cell_workspace_bytes in all), and a second
+ * pass adds each vertex's 8 cell entries into grad_volumes. The same sums
+ * in another order; for gradients larger than L2, where scalar reductions
+ * into the vertex array cost 8 L2 operations on 4 rows per cell exit. Not
+ * for DVR_COLOR_VOLUME. */
+#define DVR_FLAG_CELL_GRADIENT 8u
 
 /* One volume. `data` is a device pointer to nx*ny*nz samples of `dtype`,
  * layout [nz][ny][nx] (4 per vertex, [nz][ny][nx][4], for
- * DVR_COLOR_VOLUME, aligned to 4 samples); each of nx, ny, nz >= 2. */
+ * DVR_COLOR_VOLUME, aligned to 4 samples); each of nx, ny, nz >= 2.
+ *
+ * `cells` is NULL, or a device copy of the same densities in the cell
+ * layout that dvr_make_cells writes (the march kernels then read each
+ * sample's 8 trilinear corners with one 16-byte load for DVR_F16 /
+ * DVR_BF16, two for DVR_F32, instead of 8 loads; results are bit-identical
+ * to those from `data`). It must have been made from `data` as it is now
+ * (the library cannot tell when it is stale). Not for DVR_COLOR_VOLUME. */
 typedef struct {
     int32_t nx, ny, nz;
     int32_t dtype;           /* DVR_F32, DVR_F16 or DVR_BF16 */
     const void* data;
+    const void* cells;       /* NULL, or the cell layout of `data` */
 } dvr_volume;
+
+/*
+ * Cell layout of a volume (an access layout for the trilinear gathers of
+ * Alg. 1 / Alg. 2; the paper has no counterpart). Cell (i, j, k), 0 <= i <
+ * nx - 1 etc., holds the values of its 8 corners as 8 consecutive elements
+ * of the volume's dtype at element 8 * (i + (nx - 1) * (j + (ny - 1) * k)),
+ * in the order V(i,j,k), V(i,j,k+1), V(i+1,j,k), V(i+1,j,k+1), V(i,j+1,k),
+ * V(i,j+1,k+1), V(i+1,j+1,k), V(i+1,j+1,k+1): 16 bytes per cell for the
+ * 16-bit dtypes, 32 for DVR_F32, 8 times the bytes of the volume. Each value
+ * is copied bit for bit.
+ *
+ * dvr_cells_bytes: the bytes of the layout of `vol` (0 for invalid
+ *   dimensions or dtype).
+ * dvr_make_cells: writes it from vol->data into `cells` (device, 16-byte
+ *   aligned, caller-owned, at least dvr_cells_bytes bytes), asynchronously
+ *   on `stream`. vol->cells is ignored. Errors: DVR_ERR_ARG for invalid
+ *   dimensions, pointers or a buffer that is too small, DVR_ERR_DTYPE, and
+ *   DVR_ERR_CUDA if the launch fails.
+ */
+DVR_API size_t dvr_cells_bytes(const dvr_volume* vol);
+DVR_API int dvr_make_cells(const dvr_volume* vol, void* cells, size_t cells_bytes, void* stream);
 
 /* Transfer function: `rgba` is a device pointer to R rows of
  * (r, g, b, tau) in `dtype` (DVR_F32 or DVR_F16), R >= 2. Unused (may be
@@ -288,18 +326,25 @@ DVR_API int64_t dvr_tile_order(const dvr_view* views, int32_t n_views, int32_t p
  * tile_order, tile_order_len
  *                      as for dvr_forward, made for the adjoint tile width
  * workspace            device scratch of at least
- *                      dvr_backward_workspace_bytes(n_views) bytes, 16-byte
- *                      aligned, owned by the caller. The call zeroes it on
- *                      `stream` and uses it for the tile queues of the
- *                      adjoint launches (warps fetch ray tiles from a
- *                      counter, which balances rays of very different
- *                      lengths); its contents afterwards are unspecified.
+ *                      dvr_backward_workspace_bytes(n_views) bytes
+ *                      (dvr_backward_cell_workspace_bytes with
+ *                      DVR_FLAG_CELL_GRADIENT), 16-byte aligned, owned by
+ *                      the caller. The call zeroes it on `stream` and uses
+ *                      it for the tile queues of the adjoint launches (warps
+ *                      fetch ray tiles from a counter, which balances rays
+ *                      of very different lengths) and the cell-major
+ *                      gradients; its contents afterwards are unspecified.
  *                      Two calls in flight at once on different streams
  *                      need separate workspaces.
  * workspace_bytes      its size
  * Errors as dvr_forward; DVR_ERR_ARG also when the workspace is NULL,
  * misaligned or too small.
  */
+/* Workspace bytes of dvr_backward with DVR_FLAG_CELL_GRADIENT: the tile
+ * queues of n_views views plus 32 bytes per cell of every volume (0 for
+ * invalid arguments). */
+DVR_API size_t dvr_backward_cell_workspace_bytes(const dvr_volume* volumes, int32_t n_volumes, int32_t n_views);
+
 DVR_API int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                  const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
                  const float* aux, const float* grad_image, float* const* grad_volumes,
@@ -457,8 +502,13 @@ DVR_API int dvr_orbit_eye_backward(const float* params, const float* grad_eye, i
  * a fixed 256-byte array in the library's device memory (each GPU that
  * loads the library holds it until the process exits), so one call covers
  * at most 1024 views; larger calls return DVR_ERR_ARG and launch nothing.
- * - The first call on a device looks up that array's device address with
- *   the device current; make that first call before any stream capture.
+ * - Each call that is not being captured into a CUDA graph looks up that
+ *   array's device address with the device current (so a device reset,
+ *   which reloads the library's module, is followed); a call under capture
+ *   uses the address of the device's last uncaptured call, so make one
+ *   uncaptured call on the device before capturing (and again after a
+ *   reset). DVR_FLAG_CELL_GRADIENT needs far more than the array holds and
+ *   returns DVR_ERR_ARG here.
  * - Every call shares the array: each call zeroes the counters on `stream`
  *   before its launches, and two calls whose work overlaps on the GPU
  *   (different streams, or different host threads) race on them and give

@@ -11,7 +11,7 @@ from .synthetic import View
 
 __all__ = ["synthetic", "View", "forward", "backward", "forward_tangent", "tangent_contract", "render", "loss_l2", "orbit_eye",
            "orbit_eye_backward", "orbit_camera", "Scene", "split_views", "checkpoint_slots",
-           "loss_entropy", "lib"]
+           "loss_entropy", "make_cells", "cell_workspace_bytes", "lib"]
 
 
 def __getattr__(name):
@@ -20,7 +20,7 @@ def __getattr__(name):
     if name in ("forward", "backward", "forward_tangent", "tangent_contract", "render", "loss_l2", "loss_l1",
                 "tf_prior", "volume_prior", "resample", "volume_smoothness", "orbit_eye",
                 "orbit_eye_backward", "orbit_camera", "Scene", "split_views", "MODELS", "checkpoint_slots",
-                "loss_entropy"):
+                "loss_entropy", "make_cells", "cell_workspace_bytes"):
         from . import binding as _r
         return getattr(_r, name)
     if name == "lib":

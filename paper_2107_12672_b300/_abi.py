@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # kernel variants); by default the in-tree build is loaded.
 LIB_PATH = os.environ.get("DVR_LIBRARY") or os.path.join(_HERE, "_lib", "libdvr.so")
 
-ABI_VERSION = 7          # DVR_ABI_VERSION of the header these argtypes follow
+ABI_VERSION = 8          # DVR_ABI_VERSION of the header these argtypes follow
 DVR_OK = 0
 DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
 DVR_ABSORPTION, DVR_EMISSION_ABSORPTION, DVR_COLOR_VOLUME = 0, 1, 2
@@ -24,6 +24,7 @@ DVR_PROBE_L2_READ, DVR_PROBE_L1_READ, DVR_PROBE_L2_RED = 0, 1, 2
 DVR_FLAG_TF_IMMEDIATE = 1
 DVR_FLAG_INVERT_ALPHA32 = 2
 DVR_FLAG_INVERT_ALPHA64 = 4
+DVR_FLAG_CELL_GRADIENT = 8
 
 # every symbol include/dvr.h declares
 SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_set_tile_width", "dvr_get_tile_width",
@@ -32,12 +33,12 @@ SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_set_tile_width", "dvr_get_t
            "dvr_tangent_contract", "dvr_loss_l2", "dvr_loss_l1", "dvr_tf_prior", "dvr_volume_prior",
            "dvr_resample", "dvr_orbit_eye", "dvr_orbit_eye_backward", "dvr_backward_noalloc", "dvr_probe",
            "dvr_tile_order", "dvr_checkpoint_slots", "dvr_forward_checkpointed", "dvr_backward_checkpointed",
-           "dvr_loss_entropy")
+           "dvr_loss_entropy", "dvr_cells_bytes", "dvr_make_cells", "dvr_backward_cell_workspace_bytes")
 
 
 class DvrVolume(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
-                ("dtype", ctypes.c_int32), ("data", ctypes.c_void_p)]
+                ("dtype", ctypes.c_int32), ("data", ctypes.c_void_p), ("cells", ctypes.c_void_p)]
 
 
 class DvrTF(ctypes.Structure):
@@ -98,6 +99,12 @@ def load() -> ctypes.CDLL:
         lib.dvr_backward_workspace_bytes.restype = ctypes.c_size_t
         lib.dvr_backward_noalloc.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, P, P, U32, P]
         lib.dvr_backward_noalloc.restype = ctypes.c_int
+        lib.dvr_backward_cell_workspace_bytes.argtypes = [P, I32, I32]
+        lib.dvr_backward_cell_workspace_bytes.restype = ctypes.c_size_t
+        lib.dvr_cells_bytes.argtypes = [P]
+        lib.dvr_cells_bytes.restype = ctypes.c_size_t
+        lib.dvr_make_cells.argtypes = [P, P, ctypes.c_size_t, P]
+        lib.dvr_make_cells.restype = ctypes.c_int
         lib.dvr_probe.argtypes = [I32, P, ctypes.c_size_t, I32, P, P]
         lib.dvr_probe.restype = ctypes.c_int
         lib.dvr_forward_tangent.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P]

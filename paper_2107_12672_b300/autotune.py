@@ -1,12 +1,18 @@
-"""Autotuner for the ray tiling of the march kernels.
+"""Autotuner for the march kernels: ray tiling, gather layout and scatter.
 
 A warp marches a tile of `width x (32 / width)` pixels; which shape touches
 the fewest cache sectors per gather depends on the view direction, the
 volume layout and the pass, so the tuner times the forward and the adjoint
 passes of the caller's own workload for each candidate width and keeps the
-fastest width for each pass (the choice never changes results: every ray is
-computed the same way). Choices are cached per device and workload
-signature for the life of the process, and optionally in a JSON file.
+fastest width for each pass. It also decides where the gathers read from
+(the volume's array, or its cell layout: 8 corners per cell, 8x the bytes,
+one or two 16-byte loads per cell; the layout is remade before each timed
+forward, as a step that changes the volume must) and, when a volume
+gradient is asked for, how it is accumulated (into the vertex array, or
+per cell first: DVR_FLAG_CELL_GRADIENT). None of the choices changes
+results beyond the order of the gradient's additions. Choices are cached per
+device and workload signature for the life of the process, and optionally
+in a JSON file.
 """
 from __future__ import annotations
 
@@ -16,7 +22,7 @@ import os
 import torch
 
 from . import _abi
-from .binding import Scene, backward, forward
+from .binding import Scene, backward, cell_workspace_bytes, forward, make_cells
 
 CANDIDATES = (4, 8, 16, 32)
 _cache: dict = {}
@@ -43,16 +49,22 @@ def get_tile_width(adjoint: bool = False) -> int:
 
 
 def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 5,
-             candidates=CANDIDATES, cache_file: str | None = None, l2_flush: torch.Tensor | None = None) -> dict:
+             candidates=CANDIDATES, cache_file: str | None = None, l2_flush: torch.Tensor | None = None,
+             layouts=(False,), cell_gradients=(False,)) -> dict:
     """Time the forward and the adjoint pass for each tile width (two
-    interleaved rounds, the faster of the two kept), set the fastest width
-    of each pass, and return {"width": forward width, "adjoint_width": ...,
-    "ms": {"forward": {width: ms}, "adjoint": {width: ms}}}. Cached per
-    signature. With `l2_flush` (a device buffer larger than L2), the buffer
-    is overwritten before each timed pass, so that the passes start with
-    the volume out of L2 as in a loop that touches other data between
-    steps; each pass is then timed on its own."""
-    key = signature(scene, want)
+    interleaved rounds, the faster of the two kept) and each gather layout
+    in `layouts` (False: the volume's array, True: its cell layout, built
+    before each forward and timed with it) and, for the adjoint of a volume
+    gradient, each scatter in `cell_gradients`; set the fastest width of
+    each pass and return {"width", "adjoint_width", "cells",
+    "cell_gradient", "ms": {...}}. The layout is chosen by forward + adjoint
+    time at each side's best width. Cached per signature. With `l2_flush`
+    (a device buffer larger than L2), the buffer is overwritten before each
+    timed pass, so that the passes start with the volume out of L2 as in a
+    loop that touches other data between steps."""
+    gvol = "volume" in want
+    cell_gradients = cell_gradients if gvol else (False,)
+    key = signature(scene, want) + f"|cells{tuple(layouts)}|cg{tuple(cell_gradients)}"
     if key not in _cache and cache_file and os.path.exists(cache_file):
         try:
             _cache.update(json.load(open(cache_file)))
@@ -66,19 +78,16 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
     aux = torch.empty((scene.pixels, 2), device=dev)
     seed = torch.full_like(image, 1e-3)
     grads = {}
-    if "volume" in want:
+    if gvol:
         grads["volume"] = [torch.zeros(v.shape, device=dev) for v in scene.volumes]
     if "tf" in want and scene.tf is not None:
         grads["tf"] = torch.zeros((scene.tf.shape[0], 4), device=dev)
     if "eye" in want:
         grads["eye"] = torch.zeros((len(scene.views), 3), device=dev)
     w_want = tuple(grads.keys())
-
-    def fwd():
-        forward(None, None, None, None, eye, step_voxels, scene=scene, image=image, aux=aux)
-
-    def bwd():
-        backward(None, None, None, None, eye, step_voxels, aux, seed, scene=scene, grads=grads, want=w_want)
+    cg_ws = None
+    if True in cell_gradients:
+        cg_ws = torch.empty(cell_workspace_bytes(scene), dtype=torch.uint8, device=dev)
 
     def timed(fn):
         if l2_flush is None:
@@ -99,20 +108,50 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in ev) / reps
 
-    times = {"forward": {}, "adjoint": {}}
-    for _ in range(2):
-        for width in candidates:
-            set_tile_width(width)
-            fwd()
-            bwd()
-            torch.cuda.synchronize()
-            for name, fn in (("forward", fwd), ("adjoint", bwd)):
-                t = timed(fn)
-                times[name][width] = min(t, times[name].get(width, t))
-    best_f = min(times["forward"], key=times["forward"].get)
-    best_b = min(times["adjoint"], key=times["adjoint"].get)
+    times = {}
+    for use_cells in layouts:
+        cells = [make_cells(v) for v in scene.volumes] if use_cells else None
+        sc = Scene.make(scene.volumes, scene.tf, scene.model, scene.views, cells=cells)
+
+        def fwd():
+            if cells is not None:
+                for v, c in zip(sc.volumes, cells):
+                    make_cells(v, out=c)
+            forward(None, None, None, None, eye, step_voxels, scene=sc, image=image, aux=aux)
+
+        for cg in cell_gradients:
+            def bwd():
+                backward(None, None, None, None, eye, step_voxels, aux, seed, scene=sc, grads=grads, want=w_want,
+                         cell_gradient=cg, workspace=cg_ws if cg else None)
+
+            fk, bk = f"forward|cells={int(use_cells)}", f"adjoint|cells={int(use_cells)}|cell_gradient={int(cg)}"
+            times.setdefault(fk, {})
+            times.setdefault(bk, {})
+            for _ in range(2):
+                for width in candidates:
+                    set_tile_width(width)
+                    fwd()
+                    bwd()
+                    torch.cuda.synchronize()
+                    for name, fn in ((fk, fwd), (bk, bwd)):
+                        if name == fk and cg != cell_gradients[0]:
+                            continue            # the forward does not depend on the scatter
+                        t = timed(fn)
+                        times[name][width] = min(t, times[name].get(width, t))
+        del cells, sc
+    best = None
+    for use_cells in layouts:
+        f = times[f"forward|cells={int(use_cells)}"]
+        bf = min(f, key=f.get)
+        for cg in cell_gradients:
+            b = times[f"adjoint|cells={int(use_cells)}|cell_gradient={int(cg)}"]
+            bb = min(b, key=b.get)
+            total = f[bf] + b[bb]
+            if best is None or total < best[0]:
+                best = (total, bf, bb, use_cells, cg)
+    _, best_f, best_b, use_cells, cg = best
     set_tile_width(best_f, best_b)
-    result = {"width": best_f, "adjoint_width": best_b,
+    result = {"width": best_f, "adjoint_width": best_b, "cells": bool(use_cells), "cell_gradient": bool(cg),
               "ms": {n: {str(k): round(v, 4) for k, v in t.items()} for n, t in times.items()}}
     _cache[key] = result
     if cache_file:

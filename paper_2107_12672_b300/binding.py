@@ -20,7 +20,7 @@ import torch
 from . import _abi
 from .synthetic import View
 
-__all__ = ["View", "Scene", "forward", "backward", "forward_tangent", "tangent_contract", "loss_l2",
+__all__ = ["View", "Scene", "make_cells", "cell_workspace_bytes", "forward", "backward", "forward_tangent", "tangent_contract", "loss_l2",
            "loss_l1", "tf_prior", "volume_prior", "resample", "volume_smoothness", "orbit_eye", "orbit_eye_backward",
            "render", "orbit_camera", "split_views", "MODELS"]
 
@@ -66,10 +66,14 @@ class Scene:
     offsets: list
 
     @staticmethod
-    def make(volumes, tf, model, views) -> "Scene":
+    def make(volumes, tf, model, views, cells=None) -> "Scene":
+        """`cells`: None, or one cell layout per volume (make_cells), which
+        the march kernels then read instead of the volumes' arrays."""
         if isinstance(volumes, torch.Tensor):
             volumes = [volumes]
         model = _model(model)
+        if cells is not None and len(cells) != len(volumes):
+            raise ValueError("one cell layout per volume")
         vd = (_abi.DvrVolume * len(volumes))()
         for i, v in enumerate(volumes):
             _require_cuda(v, f"volume {i}")
@@ -81,7 +85,11 @@ class Scene:
             if v.dtype not in _DTYPES:
                 raise ValueError(f"volume dtype {v.dtype} unsupported")
             nz, ny, nx = v.shape[:3]
-            vd[i] = _abi.DvrVolume(nx, ny, nz, _DTYPES[v.dtype], v.data_ptr())
+            c = None
+            if cells is not None:
+                _require_cuda(cells[i], f"cells {i}")
+                c = cells[i].data_ptr()
+            vd[i] = _abi.DvrVolume(nx, ny, nz, _DTYPES[v.dtype], v.data_ptr(), c)
         td = None
         if model == _abi.DVR_EMISSION_ABSORPTION:
             _require_cuda(tf, "tf")
@@ -100,7 +108,9 @@ class Scene:
             offsets.append(off)
             off += int(w.width) * int(w.height)
         ch = 1 if model == _abi.DVR_ABSORPTION else 4
-        return Scene(list(volumes), tf, model, list(views), vd, td, wd, off, ch, offsets)
+        sc = Scene(list(volumes), tf, model, list(views), vd, td, wd, off, ch, offsets)
+        sc.cells = list(cells) if cells is not None else None      # kept alive with the descriptors
+        return sc
 
     def tf_ref(self):
         return ctypes.byref(self.tf_desc) if self.tf_desc is not None else None
@@ -133,6 +143,34 @@ class Scene:
         if stream is not None:
             ws.record_stream(stream)
         return ws
+
+
+def cell_workspace_bytes(scene: Scene) -> int:
+    """Workspace bytes of backward(..., cell_gradient=True) on this scene
+    (dvr_backward_cell_workspace_bytes)."""
+    return int(_abi.load().dvr_backward_cell_workspace_bytes(scene.vol_desc, len(scene.volumes),
+                                                             len(scene.views)))
+
+
+def make_cells(volume: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The cell layout of `volume` (dvr_make_cells): per cell its 8 corner
+    values, 8x the volume's bytes, as a flat tensor of the volume's dtype
+    (written into `out` if given). Remake it whenever the volume changes."""
+    _require_cuda(volume, "volume")
+    if volume.dim() != 3 or volume.dtype not in _DTYPES:
+        raise ValueError("cell layout: a 3-D float32/float16/bfloat16 volume")
+    lib = _abi.load()
+    nz, ny, nx = volume.shape
+    desc = _abi.DvrVolume(nx, ny, nz, _DTYPES[volume.dtype], volume.data_ptr(), None)
+    nbytes = int(lib.dvr_cells_bytes(ctypes.byref(desc)))
+    n = nbytes // volume.element_size()
+    if out is None:
+        out = torch.empty(n, dtype=volume.dtype, device=volume.device)
+    elif out.numel() * out.element_size() < nbytes or out.dtype != volume.dtype or not out.is_contiguous():
+        raise ValueError("out is too small, of another dtype or not contiguous")
+    _abi.check(lib.dvr_make_cells(ctypes.byref(desc), out.data_ptr(), out.numel() * out.element_size(),
+                                  _stream_ptr(stream)), "dvr_make_cells")
+    return out
 
 
 def checkpoint_slots(scene: "Scene", step_voxels, k: int) -> int:
@@ -178,14 +216,18 @@ def forward(volumes, tf, model, views, eye, step_voxels, *, scene: Scene | None 
 
 def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, want=("volume", "tf", "eye"),
              scene: Scene | None = None, grads: dict | None = None, tf_immediate=False, inversion="depth",
-             stream=None, checkpoints=None):
+             stream=None, checkpoints=None, cell_gradient=False, workspace=None):
     """Alg. 2 for all views in one launch. Returns a dict with float32
     gradients for the requested parameters ("volume" -> list, "tf", "eye",
     "step"); buffers passed in `grads` are accumulated into. `inversion`
     selects how the opacity before each sample is recovered: "depth"
     (default), or the ablations "alpha32" / "alpha64" (the paper's form),
     which with `checkpoints` = (tensor, K) from a checkpointed forward
-    restart from the forward's value every K samples."""
+    restart from the forward's value every K samples. `cell_gradient`
+    accumulates the volume gradient per cell first
+    (DVR_FLAG_CELL_GRADIENT); its workspace, 32 bytes per cell, comes from
+    `workspace` (a uint8 tensor of at least cell_workspace_bytes(scene)
+    bytes, kept by the caller) or else from torch's caching allocator."""
     sc = scene or Scene.make(volumes, tf, model, views)
     dev = sc.volumes[0].device
     g = dict(grads or {})
@@ -203,7 +245,14 @@ def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, wa
     flags = _abi.DVR_FLAG_TF_IMMEDIATE if tf_immediate else 0
     flags |= {"depth": 0, "alpha32": _abi.DVR_FLAG_INVERT_ALPHA32, "alpha64": _abi.DVR_FLAG_INVERT_ALPHA64}[inversion]
     lib = _abi.load()
-    ws = sc.workspace(lib, stream)
+    if cell_gradient and "volume" in g:
+        flags |= _abi.DVR_FLAG_CELL_GRADIENT
+        ws = workspace if workspace is not None else torch.empty(cell_workspace_bytes(sc), dtype=torch.uint8,
+                                                                 device=dev)
+        if stream is not None and workspace is None:
+            ws.record_stream(stream)
+    else:
+        ws = workspace if workspace is not None else sc.workspace(lib, stream)
     if checkpoints is not None:
         ck, k = checkpoints
         rc = lib.dvr_backward_checkpointed(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,

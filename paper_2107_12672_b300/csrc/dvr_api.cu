@@ -69,6 +69,13 @@ size_t workspace_bytes(int n_views)
     return (launches * kQueueStride + 255) / 256 * 256;
 }
 
+// Bytes of the cell-major volume gradient of one volume (32 per cell),
+// rounded up to 256.
+size_t cell_gradient_bytes(const dvr_volume& v)
+{
+    return ((size_t)(v.nx - 1) * (size_t)(v.ny - 1) * (size_t)(v.nz - 1) * 32 + 255) / 256 * 256;
+}
+
 struct Common {
     int dtype = 0;
     int channels = 1;
@@ -109,6 +116,12 @@ int check_common(const dvr_volume* vols, int nvol, const dvr_tf* tf, int model, 
         if (!aligned(v.data, model == DVR_COLOR_VOLUME ? 4 * esz : esz))
             return fail(DVR_ERR_ARG, "volume %d: data is not aligned to its %s", i,
                         model == DVR_COLOR_VOLUME ? "4-sample vertex" : "element size");
+        if (v.cells && model == DVR_COLOR_VOLUME)
+            return fail(DVR_ERR_ARG, "volume %d: the cell layout is not for DVR_COLOR_VOLUME", i);
+        if (v.cells && !aligned(v.cells, 16))
+            return fail(DVR_ERR_ARG, "volume %d: cells is not 16-byte aligned", i);
+        if ((v.cells != nullptr) != (vols[0].cells != nullptr))
+            return fail(DVR_ERR_ARG, "volume %d: either every volume of a call has its cell layout or none", i);
     }
     if (model == DVR_EMISSION_ABSORPTION) {
         if (!tf || !tf->rgba) return fail(DVR_ERR_ARG, "emission-absorption needs a transfer function");
@@ -149,6 +162,7 @@ void pack(dvr::Params& p, int tw, const dvr_volume* vols, int nvol, const dvr_tf
     memset(&p, 0, sizeof(p));
     for (int i = 0; i < nvol; ++i) {
         p.vol[i].data = vols[i].data;
+        p.vol[i].cells = vols[i].cells;
         p.vol[i].n[0] = vols[i].nx;
         p.vol[i].n[1] = vols[i].ny;
         p.vol[i].n[2] = vols[i].nz;
@@ -265,7 +279,8 @@ int backward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf
                   int64_t tile_order_len, const float* ckpt, int32_t ck_k, int32_t ck_slots, void* workspace,
                   size_t workspace_bytes_, void* stream)
 {
-    if (flags & ~(DVR_FLAG_TF_IMMEDIATE | DVR_FLAG_INVERT_ALPHA32 | DVR_FLAG_INVERT_ALPHA64))
+    if (flags & ~(DVR_FLAG_TF_IMMEDIATE | DVR_FLAG_INVERT_ALPHA32 | DVR_FLAG_INVERT_ALPHA64 |
+                  DVR_FLAG_CELL_GRADIENT))
         return fail(DVR_ERR_ARG, "unknown flag bits 0x%x", flags);
     if ((flags & DVR_FLAG_INVERT_ALPHA32) && (flags & DVR_FLAG_INVERT_ALPHA64))
         return fail(DVR_ERR_ARG, "choose one inversion ablation");
@@ -297,9 +312,22 @@ int backward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf
     const int tfm = grad_tf ? ((flags & DVR_FLAG_TF_IMMEDIATE) ? dvr::kTFImmediate : dvr::kTFDelayed)
                             : dvr::kTFNone;
     const bool pos = grad_eye != nullptr || grad_step != nullptr;
-    const size_t ws = workspace_bytes(n_views);
+    // with DVR_FLAG_CELL_GRADIENT the workspace also holds a cell-major
+    // gradient per volume that takes a gradient, after the queue counters
+    const bool cellg = (flags & DVR_FLAG_CELL_GRADIENT) && gvol;
+    if ((flags & DVR_FLAG_CELL_GRADIENT) && model == DVR_COLOR_VOLUME)
+        return fail(DVR_ERR_UNSUPPORTED, "DVR_FLAG_CELL_GRADIENT: not for DVR_COLOR_VOLUME");
+    size_t ws = workspace_bytes(n_views);
+    size_t cg_off[dvr::kMaxVolumes] = {0};
+    if (cellg)
+        for (int i = 0; i < n_volumes; ++i)
+            if (grad_volumes[i]) {
+                cg_off[i] = ws;
+                ws += cell_gradient_bytes(volumes[i]);
+            }
     if (!workspace || workspace_bytes_ < ws)
-        return fail(DVR_ERR_ARG, "workspace %p of %zu bytes: %zu bytes needed", workspace, workspace_bytes_, ws);
+        return fail(DVR_ERR_ARG, "workspace %p of %zu bytes: %zu bytes needed%s", workspace, workspace_bytes_, ws,
+                    cellg ? " (with the cell-major gradients of DVR_FLAG_CELL_GRADIENT)" : "");
     if (!aligned(workspace, 16)) return fail(DVR_ERR_ARG, "workspace is not 16-byte aligned");
     if (!gvol && tfm == dvr::kTFNone && !pos) return DVR_OK;   // nothing requested
     // the scattering kernel variant is chosen per launch: when any volume
@@ -328,6 +356,8 @@ int backward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf
                 p.vol[i].grad = grad_volumes[i];
                 const long long bytes = 4ll * volumes[i].nx * volumes[i].ny * volumes[i].nz;
                 p.vol[i].grad_vec = bytes <= dvr::l2_bytes();
+                if (cellg && grad_volumes[i])
+                    p.vol[i].cgrad = reinterpret_cast<float*>(static_cast<char*>(workspace) + cg_off[i]);
             }
         p.aux = const_cast<float*>(aux);
         p.grad_image = grad_image;
@@ -342,6 +372,14 @@ int backward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf
             : dvr::launch_backward(p, model, c.dtype, gvol, tfm, pos, inv, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "dvr_backward launch");
     }
+    if (cellg)
+        for (int i = 0; i < n_volumes; ++i)
+            if (grad_volumes[i]) {
+                cudaError_t e = dvr::launch_cells_to_vertices(
+                    reinterpret_cast<const float*>(static_cast<const char*>(workspace) + cg_off[i]), volumes[i].nx,
+                    volumes[i].ny, volumes[i].nz, grad_volumes[i], (cudaStream_t)stream);
+                if (e != cudaSuccess) return cuda_fail(e, "dvr_backward cell gradient pass");
+            }
     return DVR_OK;
 }
 
@@ -426,6 +464,45 @@ int dvr_probe(int32_t kind, void* buffer, size_t bytes, int32_t reps, float* sin
 }
 
 size_t dvr_backward_workspace_bytes(int32_t n_views) { return workspace_bytes(n_views); }
+
+size_t dvr_backward_cell_workspace_bytes(const dvr_volume* volumes, int32_t n_volumes, int32_t n_views)
+{
+    if (!volumes || n_volumes < 1 || n_volumes > dvr::kMaxVolumes || n_views < 1) return 0;
+    size_t ws = workspace_bytes(n_views);
+    for (int i = 0; i < n_volumes; ++i) {
+        if (volumes[i].nx < 2 || volumes[i].ny < 2 || volumes[i].nz < 2) return 0;
+        ws += cell_gradient_bytes(volumes[i]);
+    }
+    return ws;
+}
+
+size_t dvr_cells_bytes(const dvr_volume* vol)
+{
+    if (!vol || vol->nx < 2 || vol->ny < 2 || vol->nz < 2) return 0;
+    if ((double)vol->nx * vol->ny * vol->nz >= 4294967296.0) return 0;
+    if (vol->dtype != DVR_F32 && vol->dtype != DVR_F16 && vol->dtype != DVR_BF16) return 0;
+    const size_t esz = vol->dtype == DVR_F32 ? 4 : 2;
+    return (size_t)(vol->nx - 1) * (size_t)(vol->ny - 1) * (size_t)(vol->nz - 1) * 8 * esz;
+}
+
+int dvr_make_cells(const dvr_volume* vol, void* cells, size_t cells_bytes, void* stream)
+{
+    g_err[0] = 0;
+    if (!vol) return fail(DVR_ERR_ARG, "dvr_make_cells: vol is NULL");
+    if (vol->dtype != DVR_F32 && vol->dtype != DVR_F16 && vol->dtype != DVR_BF16)
+        return fail(DVR_ERR_DTYPE, "dvr_make_cells: dtype %d unsupported", vol->dtype);
+    if (vol->nx < 2 || vol->ny < 2 || vol->nz < 2 || (double)vol->nx * vol->ny * vol->nz >= 4294967296.0)
+        return fail(DVR_ERR_ARG, "dvr_make_cells: dimensions %d x %d x %d invalid", vol->nx, vol->ny, vol->nz);
+    const size_t esz = vol->dtype == DVR_F32 ? 4 : 2;
+    if (!vol->data || !aligned(vol->data, esz)) return fail(DVR_ERR_ARG, "dvr_make_cells: data NULL or misaligned");
+    const size_t need = dvr_cells_bytes(vol);
+    if (!cells || !aligned(cells, 16) || cells_bytes < need)
+        return fail(DVR_ERR_ARG, "dvr_make_cells: cells %p of %zu bytes (16-byte aligned, %zu needed)", cells,
+                    cells_bytes, need);
+    cudaError_t e = dvr::launch_make_cells(vol->data, vol->dtype, vol->nx, vol->ny, vol->nz, cells,
+                                           (cudaStream_t)stream);
+    return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_make_cells launch");
+}
 
 int64_t dvr_tile_order(const dvr_view* views, int32_t n_views, int32_t pass, uint32_t* order, int64_t capacity)
 {
@@ -714,14 +791,20 @@ void* g_noalloc_addr[64];   // device address of g_noalloc_scratch, per device
 
 // In host code g_noalloc_scratch names a host-side shadow, not device memory,
 // so the kernels get the address the runtime reports for the current device.
-int noalloc_scratch(void** out)
+int noalloc_scratch(cudaStream_t stream, void** out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "dvr_backward_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= 64) return fail(DVR_ERR_ARG, "dvr_backward_noalloc: device %d beyond 63", dev);
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    // the address is asked for again on every call that is not being
+    // captured into a graph (a device reset reloads the module and moves
+    // the array); during a capture the address of the last call is used
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(stream, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "dvr_backward_noalloc: cudaStreamIsCapturing");
+    if (cap == cudaStreamCaptureStatusNone || !g_noalloc_addr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "dvr_backward_noalloc: cudaGetSymbolAddress");
@@ -746,7 +829,7 @@ extern "C" int dvr_backward_noalloc(const dvr_volume* volumes, int32_t n_volumes
                     "static array holds %zu (at most %d views per call; use dvr_backward with a workspace)",
                     n_views, need, kNoallocScratchBytes, kNoallocMaxViews);
     void* scratch = nullptr;
-    const int rc = noalloc_scratch(&scratch);
+    const int rc = noalloc_scratch((cudaStream_t)stream, &scratch);
     if (rc) return rc;
     // dvr_backward zeroes the counters on `stream` before it launches
     return dvr_backward(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, aux, grad_image,

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "dvr.h"
 
 namespace dvr {
@@ -48,7 +50,9 @@ constexpr int kFixBits = 40;         // fraction bits of a fixed-point sample po
 
 struct VolumeDesc {
     const void* data;
+    const void* cells;               // the cell layout of data (dvr_make_cells), or null
     float* grad;                     // adjoint only, may be null
+    float* cgrad;                    // cell-major gradient ([cells][8]) the adjoint adds into instead, or null
     int n[3];
     int nmax;
     int grad_vec;                    // scatter the gradient with 16-byte vector reductions
@@ -395,13 +399,15 @@ __device__ __forceinline__ void march_prev(const March& m, long long q[3])
 }
 
 // Trilinear interpolation at grid coordinate g (clamped to the box), split
-// into locating the cell and loading its 8 corners (cell_fetch) and the
-// interpolation itself (cell_value), so that a march can issue the loads of
+// into locating the cell (cell_locate), loading its 8 corners (cell_load,
+// or a record of the cell layout) and the interpolation itself
+// (cell_value), so that a march can issue the loads of
 // the next sample before it interpolates the current one. The corners are
 // held as z pairs, vz[x + 2y] = (corner (x, y, 0), corner (x, y, 1)), so that
 // the x and y lerps of both z planes run as packed pairs.
 struct Cell {
     uint32_t base;                   // index of corner (0,0,0)
+    uint32_t cell;                   // index of the cell (its record in the cell layout)
     float fx, fy, fz;
     bool in[3];                      // false where g was clamped
     float2 vz[4];
@@ -466,6 +472,7 @@ __device__ __forceinline__ void cell_locate(const Grid& G, const long long q[3],
     }
     c.fx = fr[0]; c.fy = fr[1]; c.fz = fr[2];
     c.base = (uint32_t)j[0] + (uint32_t)G.n[0] * ((uint32_t)j[1] + (uint32_t)G.n[1] * (uint32_t)j[2]);
+    c.cell = (uint32_t)j[0] + (uint32_t)(G.n[0] - 1) * ((uint32_t)j[1] + (uint32_t)(G.n[1] - 1) * (uint32_t)j[2]);
 }
 
 template <typename VT>
@@ -483,13 +490,55 @@ __device__ __forceinline__ void cell_load(const VT* __restrict__ vol, const Grid
     c.vz[3].y = Load<VT>::get(p + sz + sy + 1);
 }
 
+// The 8 corners of cell c from the cell layout (dvr_make_cells): one
+// 16-byte record for 16-bit storage, two for binary32, holding the z pairs
+// vz[0..3] in order. 16-bit records keep each pair as its 32-bit word in
+// vz[k].x until cell_decode_cells; binary32 ones arrive decoded.
+template <typename VT> struct CellLoad;
+template <> struct CellLoad<float> {
+    static __device__ __forceinline__ void get(const void* cells, Cell& c)
+    {
+        const float4* r = reinterpret_cast<const float4*>(cells) + 2 * (size_t)c.cell;
+        const float4 a = __ldg(r), b = __ldg(r + 1);
+        c.vz[0] = make_float2(a.x, a.y);
+        c.vz[1] = make_float2(a.z, a.w);
+        c.vz[2] = make_float2(b.x, b.y);
+        c.vz[3] = make_float2(b.z, b.w);
+    }
+};
+template <typename VT> struct CellLoad16 {
+    static __device__ __forceinline__ void get(const void* cells, Cell& c)
+    {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(cells) + c.cell);
+        c.vz[0].x = __uint_as_float(u.x);
+        c.vz[1].x = __uint_as_float(u.y);
+        c.vz[2].x = __uint_as_float(u.z);
+        c.vz[3].x = __uint_as_float(u.w);
+    }
+};
+template <> struct CellLoad<__half> : CellLoad16<__half> {};
+template <> struct CellLoad<__nv_bfloat16> : CellLoad16<__nv_bfloat16> {};
+
+// Binary32 values of the corners CellLoad fetched: a 16-bit word's low
+// half is the z = 0 corner, its high half the z = 1 corner.
 template <typename VT>
-__device__ __forceinline__ void cell_fetch(const VT* __restrict__ vol, const Grid& G, const long long q[3],
-                                           Cell& c)
+__device__ __forceinline__ void cell_decode_cells(Cell& c)
 {
-    cell_locate(G, q, c);
-    cell_load<VT>(vol, G, c);
+    if constexpr (std::is_same<VT, __half>::value) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t w = __float_as_uint(c.vz[k].x);
+            c.vz[k] = __half22float2(*reinterpret_cast<const __half2*>(&w));
+        }
+    } else if constexpr (std::is_same<VT, __nv_bfloat16>::value) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t w = __float_as_uint(c.vz[k].x);
+            c.vz[k] = make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+        }
+    }
 }
+
 
 // The binary32 values of the corners cell_load fetched (a no-op unless
 // the storage is BF16).
@@ -584,13 +633,41 @@ __device__ __forceinline__ void depth_add_density(float& sh, float& sl, float dt
     sl = __fmaf_rn(dt, d.dd, sl);
 }
 
-template <typename VT>
-__device__ __forceinline__ void fetch_sample(const VT* __restrict__ vol, const Grid& G, const March& m,
+// The gather source of a march: the volume's own array, or its cell
+// layout (CELLS).
+template <typename VT, bool CELLS>
+struct Source {
+    const VT* __restrict__ vol;
+    const void* __restrict__ cells;
+};
+
+template <typename VT, bool CELLS>
+__device__ __forceinline__ void source_load(const Source<VT, CELLS>& src, const Grid& G, Cell& c)
+{
+    if constexpr (CELLS)
+        CellLoad<VT>::get(src.cells, c);
+    else
+        cell_load<VT>(src.vol, G, c);
+}
+
+// The binary32 corners of a fetched cell (a no-op for binary32 storage).
+template <typename VT, bool CELLS>
+__device__ __forceinline__ void source_decode(Cell& c)
+{
+    if constexpr (CELLS)
+        cell_decode_cells<VT>(c);
+    else
+        cell_decode<VT>(c);
+}
+
+template <typename VT, bool CELLS>
+__device__ __forceinline__ void fetch_sample(const Source<VT, CELLS>& src, const Grid& G, const March& m,
                                              int i, Cell& c)
 {
     long long q[3];
     march_pos(m, i, q);
-    cell_fetch<VT>(vol, G, q, c);
+    cell_locate(G, q, c);
+    source_load<VT, CELLS>(src, G, c);
 }
 
 // The march's fetch of the sample at q when the previous sample (in march
@@ -603,25 +680,25 @@ struct MCell {
     bool reuse;
 };
 
-template <typename VT>
-__device__ __forceinline__ void fetch_sample_reuse(const VT* __restrict__ vol, const Grid& G, const long long q[3],
-                                                   uint32_t prev_base, MCell& mc)
+template <typename VT, bool CELLS>
+__device__ __forceinline__ void fetch_sample_reuse(const Source<VT, CELLS>& src, const Grid& G,
+                                                   const long long q[3], uint32_t prev_base, MCell& mc)
 {
     cell_locate(G, q, mc.c);
     mc.reuse = mc.c.base == prev_base;
-    if (!mc.reuse) cell_load<VT>(vol, G, mc.c);
+    if (!mc.reuse) source_load<VT, CELLS>(src, G, mc.c);
 }
 
 // Corners of a fetched sample: its own loads (decoded here, where they are
 // consumed), or the decoded corners of the previous one.
-template <typename VT>
+template <typename VT, bool CELLS>
 __device__ __forceinline__ void cell_resolve(MCell& mc, const float2 last[4])
 {
     if (mc.reuse) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) mc.c.vz[k] = last[k];
     } else {
-        cell_decode<VT>(mc.c);
+        source_decode<VT, CELLS>(mc.c);
     }
 }
 

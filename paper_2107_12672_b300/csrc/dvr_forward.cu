@@ -16,7 +16,8 @@ namespace dvr {
 // CKPT: also record the transmittance 1 - A_i before every K-th sample
 // (i = 0, K, 2K, ...) of each ray, for the adjoint's opacity recovery in
 // the paper's alpha form.
-template <int MODEL, typename VT, bool CKPT = false>
+// CELLS: gather the corners from the volume's cell layout.
+template <int MODEL, typename VT, bool CKPT = false, bool CELLS = false>
 __global__ void __launch_bounds__(kWarps * 32, DVR_FWD_MIN_BLOCKS)
 forward_kernel(const __grid_constant__ Params p)
 {
@@ -38,7 +39,7 @@ forward_kernel(const __grid_constant__ Params p)
         tile_pixel(p, vw, tile - p.tile_start[v], lane, px, py);
         const bool valid = px < vw.width && py < vw.height;
         const VolumeDesc& vd = p.vol[vw.volume];
-        const VT* __restrict__ vol = reinterpret_cast<const VT*>(vd.data);
+        const Source<VT, CELLS> src{reinterpret_cast<const VT*>(vd.data), vd.cells};
 
         Grid G;
         make_grid(vd, p.step_voxels, G);
@@ -69,9 +70,9 @@ forward_kernel(const __grid_constant__ Params p)
         float2 last_v[4];
         long long q[3] = {m.g0[0], m.g0[1], m.g0[2]};   // position of the next fetch
         if (N > 0) {
-            fetch_sample_reuse<VT>(vol, G, q, 0xffffffffu, n1);
+            fetch_sample_reuse(src, G, q, 0xffffffffu, n1);
             march_next(m, q);
-            fetch_sample_reuse<VT>(vol, G, q, n1.c.base, n2);
+            fetch_sample_reuse(src, G, q, n1.c.base, n2);
             march_next(m, q);
         }
 #pragma unroll 3
@@ -85,11 +86,11 @@ forward_kernel(const __grid_constant__ Params p)
                 --ck_left;
             }
             MCell cur = n1;
-            cell_resolve<VT>(cur, last_v);
+            cell_resolve<VT, CELLS>(cur, last_v);
 #pragma unroll
             for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
             n1 = n2;
-            fetch_sample_reuse<VT>(vol, G, q, n1.c.base, n2);      // sample i + 2
+            fetch_sample_reuse(src, G, q, n1.c.base, n2);      // sample i + 2
             march_next(m, q);
             const Cell& c = cur.c;
             const Density d = cell_density(c);
@@ -133,10 +134,10 @@ forward_kernel(const __grid_constant__ Params p)
     }
 }
 
-template <int MODEL, typename VT, bool CKPT = false>
+template <int MODEL, typename VT, bool CKPT = false, bool CELLS = false>
 static cudaError_t launch(const Params& p, cudaStream_t stream)
 {
-    auto k = forward_kernel<MODEL, VT, CKPT>;
+    auto k = forward_kernel<MODEL, VT, CKPT, CELLS>;
     const int blocks = (p.total_tiles + kWarps - 1) / kWarps;
     // shared memory holds only this TF, the rest of the SM's 256 KB stays
     // L1 cache for the gathers
@@ -150,6 +151,22 @@ cudaError_t launch_forward(const Params& p, int model, int vol_dtype, cudaStream
     if (p.ckpt) {
         if (model != DVR_EMISSION_ABSORPTION || vol_dtype != DVR_F32) return cudaErrorNotSupported;
         return launch<DVR_EMISSION_ABSORPTION, float, true>(p, stream);
+    }
+    if (p.vol[0].cells) {                   // every volume of the launch has its cell layout
+        if (model == DVR_EMISSION_ABSORPTION) {
+            switch (vol_dtype) {
+            case DVR_F32: return launch<DVR_EMISSION_ABSORPTION, float, false, true>(p, stream);
+            case DVR_F16: return launch<DVR_EMISSION_ABSORPTION, __half, false, true>(p, stream);
+            case DVR_BF16: return launch<DVR_EMISSION_ABSORPTION, __nv_bfloat16, false, true>(p, stream);
+            }
+        } else {
+            switch (vol_dtype) {
+            case DVR_F32: return launch<DVR_ABSORPTION, float, false, true>(p, stream);
+            case DVR_F16: return launch<DVR_ABSORPTION, __half, false, true>(p, stream);
+            case DVR_BF16: return launch<DVR_ABSORPTION, __nv_bfloat16, false, true>(p, stream);
+            }
+        }
+        return cudaErrorInvalidValue;
     }
     if (model == DVR_EMISSION_ABSORPTION) {
         switch (vol_dtype) {

@@ -103,7 +103,7 @@ __device__ __forceinline__ void ray_tangent(const float e[3], const Ray& R, int 
         }
 }
 
-template <int MODEL, typename VT>
+template <int MODEL, typename VT, bool CELLS = false>
 __global__ void __launch_bounds__(kWarps * 32)
 tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
 {
@@ -124,7 +124,7 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
     const bool valid = px < vw.width && py < vw.height;
     if (!valid) return;                          // no warp-wide operations follow
     const VolumeDesc& vd = p.vol[vw.volume];
-    const VT* __restrict__ vol = reinterpret_cast<const VT*>(vd.data);
+    const Source<VT, CELLS> src{reinterpret_cast<const VT*>(vd.data), vd.cells};
     Grid G;
     make_grid(vd, p.step_voxels, G);
     const float* ep = p.eye + 3 * (p.view_base + v);
@@ -144,11 +144,11 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
     TFCache tfc;
     tf_cache_init(tfc);
     Cell nxt;
-    if (N > 0) fetch_sample<VT>(vol, G, m, 0, nxt);
+    if (N > 0) fetch_sample(src, G, m, 0, nxt);
     for (int i = 0; i < N; ++i) {
         Cell c = nxt;
-        cell_decode<VT>(c);
-        fetch_sample<VT>(vol, G, m, i + 1, nxt);
+        source_decode<VT, CELLS>(c);
+        fetch_sample(src, G, m, i + 1, nxt);
         float dg[3];
         const Density d = cell_density_grad(c, dg);
         const float ti = (float)i * G.dt;
@@ -254,7 +254,11 @@ template <int MODEL, typename VT>
 static cudaError_t launch_t(const Params& p, float* tangent, cudaStream_t s)
 {
     const size_t smem = MODEL == DVR_EMISSION_ABSORPTION ? 2 * sizeof(float4) * (size_t)p.R : 0;
-    tangent_kernel<MODEL, VT><<<(p.total_tiles + kWarps - 1) / kWarps, kWarps * 32, smem, s>>>(p, tangent);
+    const dim3 grid((p.total_tiles + kWarps - 1) / kWarps);
+    if (p.vol[0].cells)
+        tangent_kernel<MODEL, VT, true><<<grid, kWarps * 32, smem, s>>>(p, tangent);
+    else
+        tangent_kernel<MODEL, VT, false><<<grid, kWarps * 32, smem, s>>>(p, tangent);
     return cudaGetLastError();
 }
 

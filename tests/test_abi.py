@@ -42,7 +42,8 @@ def test_struct_layout_matches_header(tmp_path):
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "dvr.h"\n'
         "int main(void){\n"
-        'printf("%zu %zu %zu\\n", sizeof(dvr_volume), offsetof(dvr_volume, dtype), offsetof(dvr_volume, data));\n'
+        'printf("%zu %zu %zu %zu\\n", sizeof(dvr_volume), offsetof(dvr_volume, dtype), offsetof(dvr_volume, data),'
+        " offsetof(dvr_volume, cells));\n"
         'printf("%zu %zu\\n", sizeof(dvr_tf), offsetof(dvr_tf, rgba));\n'
         'printf("%zu %zu %zu %zu\\n", sizeof(dvr_view), offsetof(dvr_view, volume), offsetof(dvr_view, lens),'
         " offsetof(dvr_view, pixel_offset));\n"
@@ -51,7 +52,7 @@ def test_struct_layout_matches_header(tmp_path):
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     lines = subprocess.check_output([str(exe)], text=True).split("\n")
     V, T, W = _abi.DvrVolume, _abi.DvrTF, _abi.DvrView
-    assert lines[0].split() == [str(ctypes.sizeof(V)), str(V.dtype.offset), str(V.data.offset)]
+    assert lines[0].split() == [str(ctypes.sizeof(V)), str(V.dtype.offset), str(V.data.offset), str(V.cells.offset)]
     assert lines[1].split() == [str(ctypes.sizeof(T)), str(T.rgba.offset)]
     assert lines[2].split() == [str(ctypes.sizeof(W)), str(W.volume.offset), str(W.lens.offset),
                                 str(W.pixel_offset.offset)]
@@ -86,6 +87,9 @@ def _one_view(w=4, h=4, volume=0, lens=0.4, ortho=0):
     ("null_image", -1),
     ("ea_without_tf", -1),
     ("misaligned_image", -1),
+    ("misaligned_cells", -1),
+    ("cells_for_colour_volume", -1),
+    ("cells_on_some_volumes", -1),
 ])
 def test_argument_errors_need_no_gpu(case, code):
     """Invalid arguments are rejected on the host before any CUDA call."""
@@ -119,6 +123,17 @@ def test_argument_errors_need_no_gpu(case, code):
     elif case == "misaligned_image":
         tf = _abi.DvrTF(4, 0, 4096)
         rc = _call_forward(vols, 1, ctypes.byref(tf), 1, view, 1, image=4100)
+    elif case == "misaligned_cells":
+        vols[0].cells = 8200
+        rc = _call_forward(vols, 1, None, 0, view, 1)
+    elif case == "cells_for_colour_volume":
+        vols[0].cells = 8192
+        rc = _call_forward(vols, 1, None, 2, view, 1)
+    elif case == "cells_on_some_volumes":
+        two = (_abi.DvrVolume * 2)()
+        two[0] = _abi.DvrVolume(8, 8, 8, _abi.DVR_F32, 4096, 8192)
+        two[1] = _abi.DvrVolume(8, 8, 8, _abi.DVR_F32, 4096, None)
+        rc = _call_forward(two, 2, None, 0, view, 1)
     assert rc == code
     assert lib.dvr_last_error().decode()
 
@@ -286,3 +301,18 @@ def test_loss_entropy_argument_errors(channels, stats):
     lib = _abi.load()
     rc = lib.dvr_loss_entropy(4096, channels, _one_view(), 1, 1.0, 4096, None, stats, None)
     assert rc == -1 and lib.dvr_last_error()
+
+
+def test_cell_layout_size_and_argument_errors():
+    """dvr_cells_bytes is 8 elements per cell; dvr_make_cells refuses a
+    buffer that is too small or misaligned, before any CUDA call."""
+    lib = _abi.load()
+    v = _abi.DvrVolume(5, 6, 7, _abi.DVR_BF16, 4096, None)
+    assert lib.dvr_cells_bytes(ctypes.byref(v)) == 4 * 5 * 6 * 8 * 2
+    v32 = _abi.DvrVolume(5, 6, 7, _abi.DVR_F32, 4096, None)
+    assert lib.dvr_cells_bytes(ctypes.byref(v32)) == 4 * 5 * 6 * 8 * 4
+    assert lib.dvr_cells_bytes(ctypes.byref(_abi.DvrVolume(1, 6, 7, _abi.DVR_F32, 4096, None))) == 0
+    assert lib.dvr_make_cells(ctypes.byref(v), 8192, 100, None) == _abi.DVR_OK - 1
+    assert lib.dvr_make_cells(ctypes.byref(v), 8200, 1 << 20, None) == _abi.DVR_OK - 1
+    assert lib.dvr_make_cells(ctypes.byref(_abi.DvrVolume(5, 6, 7, 9, 4096, None)), 8192, 1 << 20, None) == -2
+    assert lib.dvr_last_error().decode()

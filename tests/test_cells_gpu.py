@@ -1,0 +1,156 @@
+"""The cell layout of a volume (dvr_make_cells): per cell its 8 corner
+values side by side, which the march kernels gather with one or two 16-byte
+loads. Its contents against their definition, and every march with it
+against the same march on the volume's own array: images, optical depths
+and forward-mode tangents bit for bit (the same corner values enter the
+same arithmetic), gradients up to the order of atomic additions."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2107_12672_b300 as dvr
+from paper_2107_12672_b300 import synthetic as syn
+from tests.gpu_helpers import assert_close, seeded_grad_image, to_dev
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = [torch.float32, torch.float16, torch.bfloat16]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_cell_layout_contents(dtype):
+    """Cell (i, j, k) holds V(i,j,k), V(i,j,k+1), V(i+1,j,k), V(i+1,j,k+1),
+    V(i,j+1,k), V(i,j+1,k+1), V(i+1,j+1,k), V(i+1,j+1,k+1), bit for bit, on
+    a box with three different sizes."""
+    v = to_dev(np.random.default_rng(1).normal(size=(7, 5, 9)).astype(np.float32), dtype)
+    c = dvr.make_cells(v).view(6, 4, 8, 8)          # [k][j][i][corner]
+    ref = torch.stack([v[:-1, :-1, :-1], v[1:, :-1, :-1], v[:-1, :-1, 1:], v[1:, :-1, 1:],
+                       v[:-1, 1:, :-1], v[1:, 1:, :-1], v[:-1, 1:, 1:], v[1:, 1:, 1:]], dim=-1)
+    assert torch.equal(c.view(torch.int16) if dtype != torch.float32 else c.view(torch.int32),
+                       ref.contiguous().view(torch.int16) if dtype != torch.float32 else ref.contiguous().view(torch.int32))
+
+
+def _march(w, vols, tf, cells, G, want):
+    sc = dvr.Scene.make(vols, tf, w.model, w.views, cells=cells)
+    eye = to_dev(w.eye)
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    img, aux = dvr.forward(None, None, None, None, eye, w.step_voxels, scene=sc, sample_count=count)
+    g = dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=sc, want=want)
+    torch.cuda.synchronize()
+    return img, aux, int(count.item()), g
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("model", ["emission_absorption", "absorption"])
+def test_cells_equal_linear(dtype, model):
+    """Forward and adjoint (volume, TF and eye gradients) of several views of
+    uneven sizes over two non-cubic volumes, ragged tiles included, with and
+    without the cell layout."""
+    rng = np.random.default_rng(7)
+    vols = [to_dev(syn.value_noise(n, seed=s)[:, :n - 3, :], dtype) for n, s in ((33, 2), (24, 3))]
+    vols = [v.contiguous() for v in vols]
+    tf = to_dev(syn.random_tf(16, seed=4)) if model == "emission_absorption" else None
+    views = [syn.View(37, 29), syn.View(20, 21, volume_index=1), syn.View(16, 11, ortho=True, ortho_height=1.2)]
+    eye = (syn.fibonacci_sphere(3) * 2.2).astype(np.float32)
+    w = syn.Workload("cells", model, vols, tf, views, eye, None, 0.4, ("volume", "tf", "camera"))
+    nc = 4 if model == "emission_absorption" else 1
+    G = to_dev(seeded_grad_image(sum(v.width * v.height for v in views), nc, 9))
+    want = ("volume", "tf", "eye") if tf is not None else ("volume", "eye")
+    a = _march(w, vols, tf, None, G, want)
+    cells = [dvr.make_cells(v) for v in vols]
+    b = _march(w, vols, tf, cells, G, want)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and a[2] == b[2]
+    for i in range(len(vols)):
+        assert_close(b[3]["volume"][i].cpu().numpy(), a[3]["volume"][i].cpu().numpy(), 1e-4, f"volume {i}")
+    if tf is not None:
+        assert_close(b[3]["tf"].cpu().numpy(), a[3]["tf"].cpu().numpy(), 1e-4, "tf")
+    assert_close(b[3]["eye"].cpu().numpy(), a[3]["eye"].cpu().numpy(), 1e-4, "eye")
+
+
+def test_cells_forward_tangent_bit_identical():
+    """The forward-mode pass reads the cell layout too: same image and
+    tangents bit for bit."""
+    w = syn.workload("ea_256", scale=0.125)
+    vol = to_dev(w.volumes[0], torch.float16)
+    tf = to_dev(w.tf)
+    eye = to_dev(w.eye)
+    out = []
+    for cells in (None, [dvr.make_cells(vol)]):
+        sc = dvr.Scene.make([vol], tf, w.model, w.views, cells=cells)
+        img, tan = dvr.forward_tangent(None, None, None, None, eye, w.step_voxels, scene=sc)
+        torch.cuda.synchronize()
+        out.append((img, tan))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+
+
+def test_cells_full_size_1024():
+    """The 1024^3 FP16 volume (value noise + 32 blobs) on two of its 2048^2
+    views: images bit for bit, volume and TF gradients to the order of
+    atomics, with a cell layout of 16 GiB."""
+    w = syn.workload("ea_fp16_1024")
+    vol = syn.large_volume(w.target["n"]).to(torch.float16)
+    tf = to_dev(w.tf)
+    w.views, w.eye = w.views[:2], w.eye[:2]
+    G = torch.zeros((sum(v.width * v.height for v in w.views), 4), device="cuda")
+    G[::97] = 1.0
+    a = _march(w, [vol], tf, None, G, ("volume", "tf"))
+    cells = [dvr.make_cells(vol)]
+    b = _march(w, [vol], tf, cells, G, ("volume", "tf"))
+    assert torch.equal(a[0], b[0]) and a[2] == b[2]
+    diff = (a[3]["volume"][0] - b[3]["volume"][0]).abs().max().item()
+    assert diff <= 1e-5 * a[3]["volume"][0].abs().max().item(), diff
+    assert_close(b[3]["tf"].cpu().numpy(), a[3]["tf"].cpu().numpy(), 1e-4, "tf")
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("model", ["emission_absorption", "absorption"])
+def test_cell_gradient_equals_vertex_scatter(dtype, model):
+    """DVR_FLAG_CELL_GRADIENT (each cell run as two vector reductions into
+    a cell-major array, then a pass adding each vertex's 8 cell entries)
+    gives the volume gradient of the vertex scatter up to the order of the
+    additions, for two volumes of different shapes; the other gradients are
+    unchanged, with and without the cell layout for the gathers."""
+    vols = [to_dev(syn.value_noise(n, seed=s)[:, :n - 3, :], dtype).contiguous() for n, s in ((33, 2), (24, 3))]
+    tf = to_dev(syn.random_tf(16, seed=4)) if model == "emission_absorption" else None
+    views = [syn.View(37, 29), syn.View(20, 21, volume_index=1), syn.View(16, 11, ortho=True, ortho_height=1.2)]
+    eye = to_dev((syn.fibonacci_sphere(3) * 2.2).astype(np.float32))
+    nc = 4 if model == "emission_absorption" else 1
+    G = to_dev(seeded_grad_image(sum(v.width * v.height for v in views), nc, 9))
+    want = ("volume", "tf", "eye") if tf is not None else ("volume", "eye")
+    for cells in (None, [dvr.make_cells(v) for v in vols]):
+        sc = dvr.Scene.make(vols, tf, model, views, cells=cells)
+        _, aux = dvr.forward(None, None, None, None, eye, 0.4, scene=sc)
+        a = dvr.backward(None, None, None, None, eye, 0.4, aux, G, scene=sc, want=want)
+        b = dvr.backward(None, None, None, None, eye, 0.4, aux, G, scene=sc, want=want, cell_gradient=True)
+        torch.cuda.synchronize()
+        for i in range(len(vols)):
+            assert_close(b["volume"][i].cpu().numpy(), a["volume"][i].cpu().numpy(), 1e-4, f"volume {i}")
+        for k in want[1:]:
+            assert_close(b[k].cpu().numpy(), a[k].cpu().numpy(), 1e-4, k)
+
+
+def test_cell_gradient_accumulates_and_full_size():
+    """The cell-gradient pass adds into the caller's gradient (Alg. 2's +=)
+    and zeroes its cell array on every call: two calls give twice one call.
+    At full size (1024^3 FP16, two 2048^2 views, a 34 GB cell array) it
+    equals the vertex scatter."""
+    w = syn.workload("ea_fp16_1024")
+    vol = syn.large_volume(w.target["n"]).to(torch.float16)
+    tf = to_dev(w.tf)
+    w.views, w.eye = w.views[:2], w.eye[:2]
+    eye = to_dev(w.eye)
+    sc = dvr.Scene.make([vol], tf, w.model, w.views)
+    _, aux = dvr.forward(None, None, None, None, eye, w.step_voxels, scene=sc)
+    G = torch.zeros((sc.pixels, 4), device="cuda")
+    G[::97] = 1.0
+    ws = torch.empty(dvr.cell_workspace_bytes(sc), dtype=torch.uint8, device="cuda")
+    a = dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=sc, want=("volume",))["volume"][0]
+    g = {"volume": [torch.zeros_like(a)]}
+    for _ in range(2):
+        dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=sc, want=("volume",), grads=g,
+                     cell_gradient=True, workspace=ws)
+    torch.cuda.synchronize()
+    b = g["volume"][0]
+    scale = a.abs().max().item()
+    assert scale > 0
+    assert (b - 2 * a).abs().max().item() <= 1e-5 * scale
