@@ -78,15 +78,21 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default 8x4 ray tiles")
     ap.add_argument("--tile-width", type=int, default=0, help="fix the warp tile width (1..32)")
+    ap.add_argument("--adjoint-tile-width", type=int, default=0,
+                    help="with --tile-width: the adjoint's width (default: the same)")
     ap.add_argument("--no-variants", action="store_true", help="skip the BF16/FP16 storage comparison")
     ap.add_argument("--eager", action="store_true", help="time eagerly launched steps instead of a CUDA graph")
     ap.add_argument("--views", type=int, default=0,
                     help="keep only the first N views (a smaller case of the workload, e.g. for ncu)")
     ap.add_argument("--image", type=int, default=0, help="render every view at S x S pixels (smaller case)")
-    ap.add_argument("--cells", action="store_true",
-                    help="gather from the volumes' cell layouts (remade inside every step)")
-    ap.add_argument("--cell-gradient", action="store_true",
-                    help="accumulate the volume gradient per cell first (DVR_FLAG_CELL_GRADIENT)")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="the 1024^3 workload's volume at N^3 vertices instead (smaller case, same generator)")
+    ap.add_argument("--cells", type=int, default=-1, choices=(-1, 0, 1, 4),
+                    help="gather from the volumes' arrays (0) or cell layouts with records in row order (1) or "
+                         "bricks of 4^3 cells (4), remade inside every step (default: autotuned)")
+    ap.add_argument("--cell-gradient", type=int, default=-1, choices=(-1, 0, 1),
+                    help="accumulate the volume gradient per cell first (DVR_FLAG_CELL_GRADIENT) or not "
+                         "(default: autotuned)")
     return ap.parse_args()
 
 
@@ -102,7 +108,8 @@ def peaks():
 # the device sources a march kernel is compiled from (its own file, the
 # shared device header and the launch declarations)
 KERNEL_SOURCES = {"forward": ("dvr_forward.cu", "dvr_device.cuh", "dvr_launch.h"),
-                  "backward": ("dvr_backward.cu", "dvr_device.cuh", "dvr_launch.h")}
+                  "backward": ("dvr_backward.cu", "dvr_backward.cuh", "dvr_backward_cells.cu",
+                               "dvr_backward_cells4.cu", "dvr_device.cuh", "dvr_launch.h")}
 
 
 def kernel_source_hash(kernel: str):
@@ -235,7 +242,7 @@ class Workload:
     unless others are given (the FP32 form is the plain one)."""
 
     def __init__(self, name, device, tf_immediate=False, vol_dtype=None, tf_dtype=None, views=0, image=0,
-                 cells=False, cell_gradient=False):
+                 cells=False, cell_gradient=False, grid=0):
         import dataclasses
 
         import torch
@@ -253,7 +260,10 @@ class Workload:
                 w.orbit = w.orbit[:views]
         if image:
             w.views = [dataclasses.replace(v, width=image, height=image) for v in w.views]
-        self.reduced = {"views": views or None, "image": image or None} if (views or image) else None
+        if grid and name == "ea_fp16_1024":
+            w.target["n"] = grid
+        self.reduced = ({"views": views or None, "image": image or None, "grid": grid or None}
+                        if (views or image or grid) else None)
         self.w = w
         self.name = name
         self.device = device
@@ -326,15 +336,17 @@ class Workload:
         # cell-gradient passes
 
     def configure(self, cells, cell_gradient):
-        """Gather from the volumes' cell layouts (remade from the volumes at
-        the start of every step) or their arrays; accumulate the volume
-        gradient per cell first (with a workspace of 32 bytes per cell,
-        allocated once) or into the vertex array."""
+        """Gather from the volumes' arrays (cells 0) or their cell layouts
+        with records in row order (1) or 4^3 bricks (4), remade from the
+        volumes at the start of every step; accumulate the volume gradient
+        per cell first (with a workspace of 32 bytes per record, allocated
+        once) or into the vertex array."""
         import torch
         dvr, w = self.dvr, self.w
-        self.use_cells = bool(cells)
-        self.cells = [dvr.make_cells(v) for v in self.vol] if cells else None
-        self.scene = dvr.Scene.make(self.vol, self.tf, w.model, w.views, cells=self.cells)
+        self.use_cells = int(cells)
+        self.cells = [dvr.make_cells(v, brick=self.use_cells) for v in self.vol] if cells else None
+        self.scene = dvr.Scene.make(self.vol, self.tf, w.model, w.views, cells=self.cells,
+                                    cells_brick=self.use_cells or 1)
         self.cell_gradient = bool(cell_gradient) and "volume" in tuple(w.grads)
         self.cg_ws = (torch.empty(dvr.cell_workspace_bytes(self.scene), dtype=torch.uint8, device=self.device)
                       if self.cell_gradient else None)
@@ -355,7 +367,7 @@ class Workload:
         self.zero()
         if sc.cells is not None:
             for v, c in zip(sc.volumes, sc.cells):
-                dvr.make_cells(v, out=c)
+                dvr.make_cells(v, out=c, brick=sc.cells_brick)
         if self.orbit:
             dvr.orbit_eye(self.params, eye=self.eye)
         if ev:
@@ -394,7 +406,8 @@ class Workload:
             "loss": {"l2": "L2 against the target image", "entropy": "opacity entropy (Sec. 5.1), maximised"}[w.loss],
             "note": w.note,
             "reduced_case": self.reduced,
-            "gather_layout": "cells (remade every step)" if self.use_cells else "the volume's array",
+            "gather_layout": {0: "the volume's array", 1: "cell records in row order (remade every step)",
+                              4: "cell records in 4^3 bricks (remade every step)"}[self.use_cells],
             "volume_gradient_scatter": "per cell, then per vertex" if self.cell_gradient else "per vertex",
         }
 
@@ -754,8 +767,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    wl = Workload(args.workload, dev, args.tf_immediate, views=args.views, image=args.image, cells=args.cells,
-                  cell_gradient=args.cell_gradient)
+    wl = Workload(args.workload, dev, args.tf_immediate, views=args.views, image=args.image,
+                  cells=max(args.cells, 0), cell_gradient=args.cell_gradient > 0, grid=args.grid)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     K = args.steps
     # one untimed step to size the secondary legs (~10 s of work each)
@@ -765,20 +778,21 @@ def run_ours(args):
     tuning = None
     if args.tile_width:
         from paper_2107_12672_b300 import autotune
-        autotune.set_tile_width(args.tile_width)
-        tuning = {"width": args.tile_width, "adjoint_width": args.tile_width, "fixed": True}
+        aw = args.adjoint_tile_width or args.tile_width
+        autotune.set_tile_width(args.tile_width, aw)
+        tuning = {"width": args.tile_width, "adjoint_width": aw, "fixed": True}
     elif not args.no_autotune:
         from paper_2107_12672_b300 import autotune
         tscene, teye, tnote = wl.scene, wl.eye, "all views"
         if probe_ms > 1000.0 and len(wl.w.views) > 4:
             # steps of seconds: tune on the first four views (same volume,
             # TF and view sizes), one timed pass per width and round
-            tscene = wl.dvr.Scene.make(wl.vol, wl.tf, wl.w.model, wl.w.views[:4], cells=wl.cells)
+            tscene = wl.dvr.Scene.make(wl.vol, wl.tf, wl.w.model, wl.w.views[:4])
             teye, tnote = wl.eye[:4].contiguous(), "first 4 views"
         tuning = autotune.autotune(tscene, teye, wl.w.step_voxels, want=wl.want, l2_flush=flush,
                                    reps=1 if probe_ms > 1000.0 else 5,
-                                   layouts=(False, True) if not args.cells else (True,),
-                                   cell_gradients=(False, True) if not args.cell_gradient else (True,))
+                                   layouts=(0, 1, 4) if args.cells < 0 else (args.cells,),
+                                   cell_gradients=(False, True) if args.cell_gradient < 0 else (bool(args.cell_gradient),))
         tuning["tuned_on"] = tnote
         if tuning["cells"] != wl.use_cells or tuning["cell_gradient"] != wl.cell_gradient:
             wl.configure(tuning["cells"], tuning["cell_gradient"])
@@ -818,7 +832,7 @@ def run_ours(args):
             for vd, td in ((("bfloat16", "float16"),) if plain else (("float32", "float32"),)):
                 # with the gather layout and scatter of the headline workload
                 wv = Workload(args.workload, dev, args.tf_immediate, vol_dtype=vd, tf_dtype=td, views=args.views,
-                              image=args.image, cells=wl.use_cells, cell_gradient=wl.cell_gradient)
+                              image=args.image, cells=wl.use_cells, cell_gradient=wl.cell_gradient, grid=args.grid)
                 sm, fm, bm, _, _ = time_steps(wv, K2, W2, flush)
                 variants[f"volume_{vd}_tf_{td}"] = {
                     "value": round(wv.samples_per_pass / (sm * 1e-3) / 1e9, 4), "unit": "Gsamples/s",
@@ -927,7 +941,8 @@ def run_e2e(wl, args, world, K, W):
 
     bufs = [wl.vol[0], torch.empty_like(wl.vol[0])]
     cells1 = [torch.empty_like(wl.cells[0])] if wl.cells is not None else None
-    scenes = [wl.scene, dvr.Scene.make([bufs[1]], wl.tf, wl.w.model, wl.w.views, cells=cells1)]
+    scenes = [wl.scene, dvr.Scene.make([bufs[1]], wl.tf, wl.w.model, wl.w.views, cells=cells1,
+                                       cells_brick=wl.use_cells or 1)]
     compute = torch.cuda.current_stream()
     copier = torch.cuda.Stream()
     graphs = []

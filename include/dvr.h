@@ -77,7 +77,7 @@
 extern "C" {
 #endif
 
-#define DVR_ABI_VERSION 8
+#define DVR_ABI_VERSION 10
 
 /* exported from the shared library (which hides everything else) */
 #if defined(__GNUC__)
@@ -92,6 +92,14 @@ extern "C" {
 #define DVR_ERR_DTYPE (-2)       /* unsupported storage type for this argument */
 #define DVR_ERR_CUDA (-3)        /* a CUDA runtime call or launch failed */
 #define DVR_ERR_UNSUPPORTED (-4) /* valid request this build does not implement */
+#define DVR_ERR_BOUNDS (-5)      /* bounds-checked build: a kernel index failed its check */
+
+/* index sites of the bounds-checked build (dvr_bounds_status) */
+#define DVR_SITE_VOLUME 1        /* the 8 corners of a cell in a volume's array */
+#define DVR_SITE_CELLS 2         /* a record of a cell layout (or of the cell-major gradient) */
+#define DVR_SITE_PIXEL 3         /* image, aux, seed, tangent and checkpoint rows of a pixel */
+#define DVR_SITE_TF 4            /* TF rows k and k + 1 of a lookup (and their gradient rows) */
+#define DVR_SITE_CELL_GRADIENT 5 /* a record read by the cell-to-vertex pass */
 
 /* storage types */
 #define DVR_F32 0
@@ -127,8 +135,9 @@ extern "C" {
  * cell, at least dvr_backward_cell_workspace_bytes in all), and a second
  * pass adds each vertex's 8 cell entries into grad_volumes. The same sums
  * in another order; for gradients larger than L2, where scalar reductions
- * into the vertex array cost 8 L2 operations on 4 rows per cell exit. Not
- * for DVR_COLOR_VOLUME. */
+ * into the vertex array cost 8 L2 operations on 4 rows per cell exit. The
+ * records follow the order of the volume's cell layout (row order without
+ * one). Not for DVR_COLOR_VOLUME. */
 #define DVR_FLAG_CELL_GRADIENT 8u
 
 /* One volume. `data` is a device pointer to nx*ny*nz samples of `dtype`,
@@ -136,35 +145,46 @@ extern "C" {
  * DVR_COLOR_VOLUME, aligned to 4 samples); each of nx, ny, nz >= 2.
  *
  * `cells` is NULL, or a device copy of the same densities in the cell
- * layout that dvr_make_cells writes (the march kernels then read each
- * sample's 8 trilinear corners with one 16-byte load for DVR_F16 /
- * DVR_BF16, two for DVR_F32, instead of 8 loads; results are bit-identical
- * to those from `data`). It must have been made from `data` as it is now
- * (the library cannot tell when it is stale). Not for DVR_COLOR_VOLUME. */
+ * layout that dvr_make_cells writes, in the record order `cells_brick`
+ * (the march kernels then read each sample's 8 trilinear corners with one
+ * 16-byte load for DVR_F16 / DVR_BF16, two for DVR_F32, instead of 8 loads;
+ * results are bit-identical to those from `data`). It must have been made
+ * from `data` as it is now, with the same cells_brick (the library cannot
+ * tell when it is stale). Not for DVR_COLOR_VOLUME. `reserved` must be 0. */
 typedef struct {
     int32_t nx, ny, nz;
     int32_t dtype;           /* DVR_F32, DVR_F16 or DVR_BF16 */
     const void* data;
     const void* cells;       /* NULL, or the cell layout of `data` */
+    int32_t cells_brick;     /* record order of `cells` (and of the cell-major gradient): 0 or 1, 4 */
+    int32_t reserved;
 } dvr_volume;
 
 /*
  * Cell layout of a volume (an access layout for the trilinear gathers of
  * Alg. 1 / Alg. 2; the paper has no counterpart). Cell (i, j, k), 0 <= i <
  * nx - 1 etc., holds the values of its 8 corners as 8 consecutive elements
- * of the volume's dtype at element 8 * (i + (nx - 1) * (j + (ny - 1) * k)),
- * in the order V(i,j,k), V(i,j,k+1), V(i+1,j,k), V(i+1,j,k+1), V(i,j+1,k),
- * V(i,j+1,k+1), V(i+1,j+1,k), V(i+1,j+1,k+1): 16 bytes per cell for the
- * 16-bit dtypes, 32 for DVR_F32, 8 times the bytes of the volume. Each value
- * is copied bit for bit.
+ * of the volume's dtype, the record of index r at element 8 r, in the order
+ * V(i,j,k), V(i,j,k+1), V(i+1,j,k), V(i+1,j,k+1), V(i,j+1,k), V(i,j+1,k+1),
+ * V(i+1,j+1,k), V(i+1,j+1,k+1): 16 bytes per cell for the 16-bit dtypes, 32
+ * for DVR_F32, 8 times the bytes of the volume. Each value is copied bit for
+ * bit. The record index r of cell (i, j, k) follows vol->cells_brick:
+ *   0 or 1: row order, r = i + (nx - 1) (j + (ny - 1) k);
+ *   4: bricks of 4 x 4 x 4 cells, r = 64 (bi + bx (bj + by bk)) + (i & 3)
+ *      + 4 (j & 3) + 16 (k & 3) with (bi, bj, bk) = (i, j, k) / 4 and
+ *      bx = ceil((nx - 1) / 4), by = ceil((ny - 1) / 4); the records of
+ *      brick positions beyond the cells are left as they are.
+ * The brick order keeps the cells around a ray's position within 2 KB of
+ * each other instead of rows (nx - 1) records apart; the autotuner picks
+ * the order.
  *
- * dvr_cells_bytes: the bytes of the layout of `vol` (0 for invalid
- *   dimensions or dtype).
+ * dvr_cells_bytes: the bytes of the layout of `vol` in its order (0 for
+ *   invalid dimensions, dtype or order).
  * dvr_make_cells: writes it from vol->data into `cells` (device, 16-byte
  *   aligned, caller-owned, at least dvr_cells_bytes bytes), asynchronously
  *   on `stream`. vol->cells is ignored. Errors: DVR_ERR_ARG for invalid
- *   dimensions, pointers or a buffer that is too small, DVR_ERR_DTYPE, and
- *   DVR_ERR_CUDA if the launch fails.
+ *   dimensions, order, pointers or a buffer that is too small,
+ *   DVR_ERR_DTYPE, and DVR_ERR_CUDA if the launch fails.
  */
 DVR_API size_t dvr_cells_bytes(const dvr_volume* vol);
 DVR_API int dvr_make_cells(const dvr_volume* vol, void* cells, size_t cells_bytes, void* stream);
@@ -341,7 +361,8 @@ DVR_API int64_t dvr_tile_order(const dvr_view* views, int32_t n_views, int32_t p
  * misaligned or too small.
  */
 /* Workspace bytes of dvr_backward with DVR_FLAG_CELL_GRADIENT: the tile
- * queues of n_views views plus 32 bytes per cell of every volume (0 for
+ * queues of n_views views plus 32 bytes per record of every volume (per
+ * cell, with brick positions beyond the cells in the brick order; 0 for
  * invalid arguments). */
 DVR_API size_t dvr_backward_cell_workspace_bytes(const dvr_volume* volumes, int32_t n_volumes, int32_t n_views);
 
@@ -521,6 +542,41 @@ DVR_API int dvr_backward_noalloc(const dvr_volume* volumes, int32_t n_volumes, c
                                  float step_voxels, const float* aux, const float* grad_image,
                                  float* const* grad_volumes, float* grad_tf, float* grad_eye,
                                  float* grad_step, uint32_t flags, void* stream);
+
+/*
+ * Bounds-checked build. The library compiled with DVR_DEBUG_BOUNDS
+ * (libdvr_bounds.so beside libdvr.so; same ABI, slower kernels) compares
+ * every index its kernels form for the sites DVR_SITE_* with that site's
+ * extent before the access: the volume's nx ny nz values, the records of
+ * the cell layout, the pixels of the call's views (max over views of
+ * pixel_offset + width * height), the TF's R rows. An index that fails is
+ * counted, the first failure (site, index, extent) is recorded, and the
+ * access is redirected to element 0 (loads) or dropped (stores): no bad
+ * index reaches memory and no kernel traps. The extents are those the
+ * arguments declare; a caller buffer smaller than its declared size is not
+ * detected.
+ * - dvr_forward, dvr_forward_checkpointed, dvr_backward (and
+ *   _checkpointed, _noalloc), dvr_forward_tangent and dvr_make_cells then
+ *   synchronise `stream` (unless it is being captured into a CUDA graph)
+ *   and return DVR_ERR_BOUNDS, with the first failure in dvr_last_error,
+ *   if any check on the device failed since the last report; the records
+ *   are cleared. In a graph, read them with dvr_bounds_status after the
+ *   replay.
+ * - dvr_bounds_checked: 1 in the bounds-checked build, 0 otherwise.
+ * - dvr_bounds_status(out, reset): synchronises the device, then
+ *   out[0..3] = {failed checks, site of the first, its index, its extent}
+ *   (host array of 4); reset != 0 clears the records. DVR_ERR_UNSUPPORTED
+ *   without DVR_DEBUG_BOUNDS.
+ * - dvr_bounds_cap(site, extent): a test hook. The checks of `site` use
+ *   min(extent, the true extent) while extent > 0 (0 restores the true
+ *   one), so a test can make in-bounds indices fail their check and see
+ *   the report without any bad access. Synchronises the device.
+ *   DVR_ERR_ARG for an unknown site or a negative extent;
+ *   DVR_ERR_UNSUPPORTED without DVR_DEBUG_BOUNDS.
+ */
+DVR_API int dvr_bounds_checked(void);
+DVR_API int dvr_bounds_status(int64_t* out, int32_t reset);
+DVR_API int dvr_bounds_cap(int32_t site, int64_t extent);
 
 #ifdef __cplusplus
 }

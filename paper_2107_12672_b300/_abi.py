@@ -11,11 +11,13 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-# DVR_LIBRARY may name another build of the same library (e.g. to compare
-# kernel variants); by default the in-tree build is loaded.
+# DVR_LIBRARY may name another build of the same library (e.g. the
+# bounds-checked build BOUNDS_LIB_PATH); by default the in-tree build is
+# loaded.
+BOUNDS_LIB_PATH = os.path.join(_HERE, "_lib", "libdvr_bounds.so")
 LIB_PATH = os.environ.get("DVR_LIBRARY") or os.path.join(_HERE, "_lib", "libdvr.so")
 
-ABI_VERSION = 8          # DVR_ABI_VERSION of the header these argtypes follow
+ABI_VERSION = 10         # DVR_ABI_VERSION of the header these argtypes follow
 DVR_OK = 0
 DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
 DVR_ABSORPTION, DVR_EMISSION_ABSORPTION, DVR_COLOR_VOLUME = 0, 1, 2
@@ -25,6 +27,8 @@ DVR_FLAG_TF_IMMEDIATE = 1
 DVR_FLAG_INVERT_ALPHA32 = 2
 DVR_FLAG_INVERT_ALPHA64 = 4
 DVR_FLAG_CELL_GRADIENT = 8
+DVR_ERR_BOUNDS = -5
+DVR_SITE_VOLUME, DVR_SITE_CELLS, DVR_SITE_PIXEL, DVR_SITE_TF, DVR_SITE_CELL_GRADIENT = 1, 2, 3, 4, 5
 
 # every symbol include/dvr.h declares
 SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_set_tile_width", "dvr_get_tile_width",
@@ -33,12 +37,14 @@ SYMBOLS = ("dvr_abi_version", "dvr_last_error", "dvr_set_tile_width", "dvr_get_t
            "dvr_tangent_contract", "dvr_loss_l2", "dvr_loss_l1", "dvr_tf_prior", "dvr_volume_prior",
            "dvr_resample", "dvr_orbit_eye", "dvr_orbit_eye_backward", "dvr_backward_noalloc", "dvr_probe",
            "dvr_tile_order", "dvr_checkpoint_slots", "dvr_forward_checkpointed", "dvr_backward_checkpointed",
-           "dvr_loss_entropy", "dvr_cells_bytes", "dvr_make_cells", "dvr_backward_cell_workspace_bytes")
+           "dvr_loss_entropy", "dvr_cells_bytes", "dvr_make_cells", "dvr_backward_cell_workspace_bytes",
+           "dvr_bounds_checked", "dvr_bounds_status", "dvr_bounds_cap")
 
 
 class DvrVolume(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
-                ("dtype", ctypes.c_int32), ("data", ctypes.c_void_p), ("cells", ctypes.c_void_p)]
+                ("dtype", ctypes.c_int32), ("data", ctypes.c_void_p), ("cells", ctypes.c_void_p),
+                ("cells_brick", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class DvrTF(ctypes.Structure):
@@ -116,6 +122,11 @@ def load() -> ctypes.CDLL:
         lib.dvr_resample.argtypes = [P, I32, I32, I32, P, I32, I32, I32, P]
         lib.dvr_orbit_eye.argtypes = [P, I32, P, P]
         lib.dvr_orbit_eye_backward.argtypes = [P, P, I32, P, P]
+        lib.dvr_bounds_checked.restype = ctypes.c_int
+        lib.dvr_bounds_status.argtypes = [P, I32]
+        lib.dvr_bounds_status.restype = ctypes.c_int
+        lib.dvr_bounds_cap.argtypes = [I32, I64]
+        lib.dvr_bounds_cap.restype = ctypes.c_int
         for name in ("dvr_forward", "dvr_backward", "dvr_forward_tangent", "dvr_tangent_contract",
                      "dvr_loss_l2", "dvr_loss_l1", "dvr_tf_prior", "dvr_volume_prior", "dvr_resample",
                      "dvr_orbit_eye", "dvr_orbit_eye_backward"):

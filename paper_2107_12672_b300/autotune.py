@@ -6,8 +6,9 @@ volume layout and the pass, so the tuner times the forward and the adjoint
 passes of the caller's own workload for each candidate width and keeps the
 fastest width for each pass. It also decides where the gathers read from
 (the volume's array, or its cell layout: 8 corners per cell, 8x the bytes,
-one or two 16-byte loads per cell; the layout is remade before each timed
-forward, as a step that changes the volume must) and, when a volume
+one or two 16-byte loads per cell, records in row order or in bricks of
+4^3 cells; the layout is remade before each timed forward, as a step that
+changes the volume must) and, when a volume
 gradient is asked for, how it is accumulated (into the vertex array, or
 per cell first: DVR_FLAG_CELL_GRADIENT). None of the choices changes
 results beyond the order of the gradient's additions. Choices are cached per
@@ -50,11 +51,12 @@ def get_tile_width(adjoint: bool = False) -> int:
 
 def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 5,
              candidates=CANDIDATES, cache_file: str | None = None, l2_flush: torch.Tensor | None = None,
-             layouts=(False,), cell_gradients=(False,)) -> dict:
+             layouts=(0,), cell_gradients=(False,)) -> dict:
     """Time the forward and the adjoint pass for each tile width (two
     interleaved rounds, the faster of the two kept) and each gather layout
-    in `layouts` (False: the volume's array, True: its cell layout, built
-    before each forward and timed with it) and, for the adjoint of a volume
+    in `layouts` (0: the volume's array; 1 / 4: its cell layout with records
+    in row order / in bricks of 4^3 cells, built before each forward and
+    timed with it) and, for the adjoint of a volume
     gradient, each scatter in `cell_gradients`; set the fastest width of
     each pass and return {"width", "adjoint_width", "cells",
     "cell_gradient", "ms": {...}}. The layout is chosen by forward + adjoint
@@ -85,9 +87,6 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
     if "eye" in want:
         grads["eye"] = torch.zeros((len(scene.views), 3), device=dev)
     w_want = tuple(grads.keys())
-    cg_ws = None
-    if True in cell_gradients:
-        cg_ws = torch.empty(cell_workspace_bytes(scene), dtype=torch.uint8, device=dev)
 
     def timed(fn):
         if l2_flush is None:
@@ -110,13 +109,15 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
 
     times = {}
     for use_cells in layouts:
-        cells = [make_cells(v) for v in scene.volumes] if use_cells else None
-        sc = Scene.make(scene.volumes, scene.tf, scene.model, scene.views, cells=cells)
+        cells = [make_cells(v, brick=use_cells) for v in scene.volumes] if use_cells else None
+        sc = Scene.make(scene.volumes, scene.tf, scene.model, scene.views, cells=cells, cells_brick=use_cells or 1)
+        # the cell-major gradients' size depends on the record order (bricks pad)
+        cg_ws = torch.empty(cell_workspace_bytes(sc), dtype=torch.uint8, device=dev) if True in cell_gradients else None
 
         def fwd():
             if cells is not None:
                 for v, c in zip(sc.volumes, cells):
-                    make_cells(v, out=c)
+                    make_cells(v, out=c, brick=use_cells)
             forward(None, None, None, None, eye, step_voxels, scene=sc, image=image, aux=aux)
 
         for cg in cell_gradients:
@@ -138,7 +139,7 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
                             continue            # the forward does not depend on the scatter
                         t = timed(fn)
                         times[name][width] = min(t, times[name].get(width, t))
-        del cells, sc
+        del cells, sc, cg_ws
     best = None
     for use_cells in layouts:
         f = times[f"forward|cells={int(use_cells)}"]
@@ -151,7 +152,7 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
                 best = (total, bf, bb, use_cells, cg)
     _, best_f, best_b, use_cells, cg = best
     set_tile_width(best_f, best_b)
-    result = {"width": best_f, "adjoint_width": best_b, "cells": bool(use_cells), "cell_gradient": bool(cg),
+    result = {"width": best_f, "adjoint_width": best_b, "cells": int(use_cells), "cell_gradient": bool(cg),
               "ms": {n: {str(k): round(v, 4) for k, v in t.items()} for n, t in times.items()}}
     _cache[key] = result
     if cache_file:

@@ -66,9 +66,10 @@ class Scene:
     offsets: list
 
     @staticmethod
-    def make(volumes, tf, model, views, cells=None) -> "Scene":
-        """`cells`: None, or one cell layout per volume (make_cells), which
-        the march kernels then read instead of the volumes' arrays."""
+    def make(volumes, tf, model, views, cells=None, cells_brick=1) -> "Scene":
+        """`cells`: None, or one cell layout per volume (make_cells, all in
+        the record order `cells_brick`), which the march kernels then read
+        instead of the volumes' arrays."""
         if isinstance(volumes, torch.Tensor):
             volumes = [volumes]
         model = _model(model)
@@ -89,7 +90,7 @@ class Scene:
             if cells is not None:
                 _require_cuda(cells[i], f"cells {i}")
                 c = cells[i].data_ptr()
-            vd[i] = _abi.DvrVolume(nx, ny, nz, _DTYPES[v.dtype], v.data_ptr(), c)
+            vd[i] = _abi.DvrVolume(nx, ny, nz, _DTYPES[v.dtype], v.data_ptr(), c, int(cells_brick), 0)
         td = None
         if model == _abi.DVR_EMISSION_ABSORPTION:
             _require_cuda(tf, "tf")
@@ -110,6 +111,7 @@ class Scene:
         ch = 1 if model == _abi.DVR_ABSORPTION else 4
         sc = Scene(list(volumes), tf, model, list(views), vd, td, wd, off, ch, offsets)
         sc.cells = list(cells) if cells is not None else None      # kept alive with the descriptors
+        sc.cells_brick = int(cells_brick)
         return sc
 
     def tf_ref(self):
@@ -152,16 +154,17 @@ def cell_workspace_bytes(scene: Scene) -> int:
                                                              len(scene.views)))
 
 
-def make_cells(volume: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+def make_cells(volume: torch.Tensor, out: torch.Tensor | None = None, stream=None, brick: int = 1) -> torch.Tensor:
     """The cell layout of `volume` (dvr_make_cells): per cell its 8 corner
     values, 8x the volume's bytes, as a flat tensor of the volume's dtype
-    (written into `out` if given). Remake it whenever the volume changes."""
+    (written into `out` if given), records in row order (brick 1) or in
+    bricks of 4^3 cells (brick 4). Remake it whenever the volume changes."""
     _require_cuda(volume, "volume")
     if volume.dim() != 3 or volume.dtype not in _DTYPES:
         raise ValueError("cell layout: a 3-D float32/float16/bfloat16 volume")
     lib = _abi.load()
     nz, ny, nx = volume.shape
-    desc = _abi.DvrVolume(nx, ny, nz, _DTYPES[volume.dtype], volume.data_ptr(), None)
+    desc = _abi.DvrVolume(nx, ny, nz, _DTYPES[volume.dtype], volume.data_ptr(), None, int(brick), 0)
     nbytes = int(lib.dvr_cells_bytes(ctypes.byref(desc)))
     n = nbytes // volume.element_size()
     if out is None:

@@ -5,7 +5,10 @@
 Compiles every csrc/*.cu with nvcc into _build/ and links
 paper_2107_12672_b300/_lib/libdvr.so (static CUDA runtime, C ABI of
 include/dvr.h). Rebuilds only what changed (sources or headers newer than
-the objects).
+the objects). With --bounds it builds the bounds-checked library instead
+(DVR_DEBUG_BOUNDS: every kernel index checked against its extent, failures
+reported by the entry points), _lib/libdvr_bounds.so, from objects in
+_build/bounds/.
 """
 from __future__ import annotations
 
@@ -24,6 +27,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libdvr.so")
+BOUNDS_LIB = os.path.join(LIBDIR, "libdvr_bounds.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
@@ -42,12 +46,12 @@ def _headers():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def _compile(src: str, verbose: bool, force: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, verbose: bool, force: bool, bounds: bool = False) -> str:
+    obj = os.path.join(BUILD, "bounds" if bounds else "", os.path.basename(src) + ".o")
     newest = max(os.path.getmtime(p) for p in [src, *_headers()])
     if not force and os.path.exists(obj) and os.path.getmtime(obj) >= newest:
         return obj
-    cmd = [nvcc(), *NVCC_FLAGS, "-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc(), *NVCC_FLAGS, *(["-DDVR_DEBUG_BOUNDS"] if bounds else []), "-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,26 +63,29 @@ def _compile(src: str, verbose: bool, force: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libdvr.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
+    """Compile and link libdvr.so (or, with bounds, libdvr_bounds.so);
+    returns its path."""
+    lib = BOUNDS_LIB if bounds else LIB
+    os.makedirs(os.path.join(BUILD, "bounds") if bounds else BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose, force), srcs))
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, verbose, force, bounds), srcs))
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--verbose", action="store_true", help="print ptxas register/smem usage")
+    ap.add_argument("--bounds", action="store_true", help="the bounds-checked library (DVR_DEBUG_BOUNDS)")
     a = ap.parse_args()
-    print(build(force=a.force, verbose=a.verbose))
+    print(build(force=a.force, verbose=a.verbose, bounds=a.bounds))

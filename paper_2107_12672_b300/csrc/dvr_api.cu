@@ -17,6 +17,61 @@
 #include "dvr_loss.h"
 #include "dvr_probe.h"
 
+// ------------------------------------------------------------ bounds records
+// Every translation unit of a DVR_DEBUG_BOUNDS build registers the address
+// of its device-side BoundsRecord here during static initialisation.
+namespace dvr {
+
+static std::vector<const void*>& bounds_records()
+{
+    static std::vector<const void*> r;
+    return r;
+}
+
+int register_bounds_record(const void* symbol)
+{
+    bounds_records().push_back(symbol);
+    return (int)bounds_records().size();
+}
+
+cudaError_t bounds_take(BoundsRecord* out, bool reset)
+{
+    memset(out, 0, sizeof(*out));
+    for (const void* sym : bounds_records()) {
+        BoundsRecord r;
+        cudaError_t e = cudaMemcpyFromSymbol(&r, sym, sizeof(r));
+        if (e != cudaSuccess) return e;
+        if (r.count && !out->count) {
+            out->site = r.site;
+            out->index = r.index;
+            out->extent = r.extent;
+        }
+        out->count += r.count;
+        if (reset && r.count) {
+            r.count = 0;
+            r.site = r.index = r.extent = 0;
+            e = cudaMemcpyToSymbol(sym, &r, sizeof(r));
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t bounds_cap(int site, long long cap)
+{
+    for (const void* sym : bounds_records()) {
+        BoundsRecord r;
+        cudaError_t e = cudaMemcpyFromSymbol(&r, sym, sizeof(r));
+        if (e != cudaSuccess) return e;
+        r.cap[site] = cap;
+        e = cudaMemcpyToSymbol(sym, &r, sizeof(r));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace dvr
+
 namespace {
 
 thread_local char g_err[512] = "";
@@ -39,6 +94,44 @@ int cuda_fail(cudaError_t e, const char* what)
 }
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+const char* site_name(long long s)
+{
+    switch (s) {
+    case dvr::kSiteVolume: return "volume";
+    case dvr::kSiteCells: return "cell layout";
+    case dvr::kSitePixel: return "pixel arrays";
+    case dvr::kSiteTF: return "TF rows";
+    case dvr::kSiteCellGradient: return "cell-major gradient";
+    }
+    return "?";
+}
+
+// The end of an entry point that launches checked kernels. In a
+// DVR_DEBUG_BOUNDS build it waits for `stream` (unless the stream is being
+// captured into a graph) and turns failed checks into DVR_ERR_BOUNDS; in
+// other builds it returns DVR_OK.
+int finish(void* stream, const char* what)
+{
+#ifdef DVR_DEBUG_BOUNDS
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (cap != cudaStreamCaptureStatusNone) return DVR_OK;
+    e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    dvr::BoundsRecord r;
+    e = dvr::bounds_take(&r, true);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (r.count)
+        return fail(DVR_ERR_BOUNDS, "%s: %llu indices failed their bounds check (accesses skipped); first: %s "
+                    "index %lld, extent %lld", what, r.count, site_name(r.site), r.index, r.extent);
+#else
+    (void)stream;
+    (void)what;
+#endif
+    return DVR_OK;
+}
 
 // Adjoint workspace: one tile-queue counter per launch (views are launched
 // in groups of kMaxViewsPerLaunch), each on its own 128-byte line.
@@ -69,11 +162,28 @@ size_t workspace_bytes(int n_views)
     return (launches * kQueueStride + 255) / 256 * 256;
 }
 
-// Bytes of the cell-major volume gradient of one volume (32 per cell),
-// rounded up to 256.
+// Record order of a volume's cell layout: 1 (row order) or 4 (bricks), or
+// 0 if invalid.
+int cells_order(const dvr_volume& v)
+{
+    return v.cells_brick == 0 || v.cells_brick == 1 ? 1 : (v.cells_brick == 4 ? 4 : 0);
+}
+
+// Records of the cell layout (and of the cell-major gradient) of a volume
+// in the order `brick`: the cells, or whole bricks of 4^3 cells.
+size_t cell_records(const dvr_volume& v, int brick)
+{
+    if (brick == 4)
+        return (size_t)((v.nx - 1 + 3) / 4) * (size_t)((v.ny - 1 + 3) / 4) * (size_t)((v.nz - 1 + 3) / 4) * 64;
+    return (size_t)(v.nx - 1) * (size_t)(v.ny - 1) * (size_t)(v.nz - 1);
+}
+
+// Bytes of the cell-major volume gradient of one volume (32 per record, in
+// the order of its cell layout, row order without one), rounded up to 256.
 size_t cell_gradient_bytes(const dvr_volume& v)
 {
-    return ((size_t)(v.nx - 1) * (size_t)(v.ny - 1) * (size_t)(v.nz - 1) * 32 + 255) / 256 * 256;
+    const int brick = v.cells ? cells_order(v) : 1;
+    return (cell_records(v, brick) * 32 + 255) / 256 * 256;
 }
 
 struct Common {
@@ -122,6 +232,10 @@ int check_common(const dvr_volume* vols, int nvol, const dvr_tf* tf, int model, 
             return fail(DVR_ERR_ARG, "volume %d: cells is not 16-byte aligned", i);
         if ((v.cells != nullptr) != (vols[0].cells != nullptr))
             return fail(DVR_ERR_ARG, "volume %d: either every volume of a call has its cell layout or none", i);
+        if (v.reserved != 0) return fail(DVR_ERR_ARG, "volume %d: reserved field must be 0", i);
+        if (!cells_order(v)) return fail(DVR_ERR_ARG, "volume %d: cells_brick %d is not 0, 1 or 4", i, v.cells_brick);
+        if (v.cells && cells_order(v) != cells_order(vols[0]))
+            return fail(DVR_ERR_ARG, "volume %d: the cell layouts of one call must share their record order", i);
     }
     if (model == DVR_EMISSION_ABSORPTION) {
         if (!tf || !tf->rgba) return fail(DVR_ERR_ARG, "emission-absorption needs a transfer function");
@@ -163,6 +277,7 @@ void pack(dvr::Params& p, int tw, const dvr_volume* vols, int nvol, const dvr_tf
     for (int i = 0; i < nvol; ++i) {
         p.vol[i].data = vols[i].data;
         p.vol[i].cells = vols[i].cells;
+        p.vol[i].cells_brick = cells_order(vols[i]);
         p.vol[i].n[0] = vols[i].nx;
         p.vol[i].n[1] = vols[i].ny;
         p.vol[i].n[2] = vols[i].nz;
@@ -183,6 +298,8 @@ void pack(dvr::Params& p, int tw, const dvr_volume* vols, int nvol, const dvr_tf
         d.lens = w.lens;
         d.tiles_x = (w.width + tw - 1) / tw;
         d.pixel_offset = w.pixel_offset;
+        const long long end = w.pixel_offset + (long long)w.width * w.height;
+        if (end > p.pixel_end) p.pixel_end = end;
         p.tile_start[i - v0] = tiles;
         tiles += d.tiles_x * ((w.height + th - 1) / th);
     }
@@ -377,7 +494,8 @@ int backward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf
             if (grad_volumes[i]) {
                 cudaError_t e = dvr::launch_cells_to_vertices(
                     reinterpret_cast<const float*>(static_cast<const char*>(workspace) + cg_off[i]), volumes[i].nx,
-                    volumes[i].ny, volumes[i].nz, grad_volumes[i], (cudaStream_t)stream);
+                    volumes[i].ny, volumes[i].nz, volumes[i].cells ? cells_order(volumes[i]) : 1, grad_volumes[i],
+                    (cudaStream_t)stream);
                 if (e != cudaSuccess) return cuda_fail(e, "dvr_backward cell gradient pass");
             }
     return DVR_OK;
@@ -470,7 +588,7 @@ size_t dvr_backward_cell_workspace_bytes(const dvr_volume* volumes, int32_t n_vo
     if (!volumes || n_volumes < 1 || n_volumes > dvr::kMaxVolumes || n_views < 1) return 0;
     size_t ws = workspace_bytes(n_views);
     for (int i = 0; i < n_volumes; ++i) {
-        if (volumes[i].nx < 2 || volumes[i].ny < 2 || volumes[i].nz < 2) return 0;
+        if (volumes[i].nx < 2 || volumes[i].ny < 2 || volumes[i].nz < 2 || !cells_order(volumes[i])) return 0;
         ws += cell_gradient_bytes(volumes[i]);
     }
     return ws;
@@ -481,8 +599,9 @@ size_t dvr_cells_bytes(const dvr_volume* vol)
     if (!vol || vol->nx < 2 || vol->ny < 2 || vol->nz < 2) return 0;
     if ((double)vol->nx * vol->ny * vol->nz >= 4294967296.0) return 0;
     if (vol->dtype != DVR_F32 && vol->dtype != DVR_F16 && vol->dtype != DVR_BF16) return 0;
+    if (!cells_order(*vol)) return 0;
     const size_t esz = vol->dtype == DVR_F32 ? 4 : 2;
-    return (size_t)(vol->nx - 1) * (size_t)(vol->ny - 1) * (size_t)(vol->nz - 1) * 8 * esz;
+    return cell_records(*vol, cells_order(*vol)) * 8 * esz;
 }
 
 int dvr_make_cells(const dvr_volume* vol, void* cells, size_t cells_bytes, void* stream)
@@ -495,13 +614,14 @@ int dvr_make_cells(const dvr_volume* vol, void* cells, size_t cells_bytes, void*
         return fail(DVR_ERR_ARG, "dvr_make_cells: dimensions %d x %d x %d invalid", vol->nx, vol->ny, vol->nz);
     const size_t esz = vol->dtype == DVR_F32 ? 4 : 2;
     if (!vol->data || !aligned(vol->data, esz)) return fail(DVR_ERR_ARG, "dvr_make_cells: data NULL or misaligned");
+    if (!cells_order(*vol)) return fail(DVR_ERR_ARG, "dvr_make_cells: cells_brick %d is not 0, 1 or 4", vol->cells_brick);
     const size_t need = dvr_cells_bytes(vol);
     if (!cells || !aligned(cells, 16) || cells_bytes < need)
         return fail(DVR_ERR_ARG, "dvr_make_cells: cells %p of %zu bytes (16-byte aligned, %zu needed)", cells,
                     cells_bytes, need);
-    cudaError_t e = dvr::launch_make_cells(vol->data, vol->dtype, vol->nx, vol->ny, vol->nz, cells,
-                                           (cudaStream_t)stream);
-    return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_make_cells launch");
+    cudaError_t e = dvr::launch_make_cells(vol->data, vol->dtype, vol->nx, vol->ny, vol->nz, cells_order(*vol),
+                                           cells, (cudaStream_t)stream);
+    return e == cudaSuccess ? finish(stream, "dvr_make_cells") : cuda_fail(e, "dvr_make_cells launch");
 }
 
 int64_t dvr_tile_order(const dvr_view* views, int32_t n_views, int32_t pass, uint32_t* order, int64_t capacity)
@@ -554,8 +674,9 @@ int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, 
                 int64_t tile_order_len, void* stream)
 {
     g_err[0] = 0;
-    return forward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, image, aux, sample_count,
-                        tile_order, tile_order_len, nullptr, 0, 0, stream);
+    const int rc = forward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, image, aux,
+                                sample_count, tile_order, tile_order_len, nullptr, 0, 0, stream);
+    return rc ? rc : finish(stream, "dvr_forward");
 }
 
 int32_t dvr_checkpoint_slots(const dvr_volume* volumes, int32_t n_volumes, float step_voxels, int32_t k)
@@ -576,8 +697,9 @@ int dvr_forward_checkpointed(const dvr_volume* volumes, int32_t n_volumes, const
     const int rc = check_ckpt(volumes, n_volumes, model, step_voxels, checkpoints, k, slots,
                               "dvr_forward_checkpointed");
     if (rc) return rc;
-    return forward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, image, aux, sample_count,
-                        nullptr, 0, checkpoints, k, slots, stream);
+    const int rf = forward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, image, aux,
+                                sample_count, nullptr, 0, checkpoints, k, slots, stream);
+    return rf ? rf : finish(stream, "dvr_forward_checkpointed");
 }
 int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                  const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
@@ -586,9 +708,10 @@ int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
                  int64_t tile_order_len, void* workspace, size_t workspace_bytes_, void* stream)
 {
     g_err[0] = 0;
-    return backward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, aux, grad_image,
-                         grad_volumes, grad_tf, grad_eye, grad_step, flags, tile_order, tile_order_len, nullptr, 0,
-                         0, workspace, workspace_bytes_, stream);
+    const int rc = backward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, aux, grad_image,
+                                 grad_volumes, grad_tf, grad_eye, grad_step, flags, tile_order, tile_order_len,
+                                 nullptr, 0, 0, workspace, workspace_bytes_, stream);
+    return rc ? rc : finish(stream, "dvr_backward");
 }
 
 int dvr_backward_checkpointed(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
@@ -605,9 +728,10 @@ int dvr_backward_checkpointed(const dvr_volume* volumes, int32_t n_volumes, cons
     const int rc = check_ckpt(volumes, n_volumes, model, step_voxels, checkpoints, k, slots,
                               "dvr_backward_checkpointed");
     if (rc) return rc;
-    return backward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, aux, grad_image,
-                         grad_volumes, grad_tf, grad_eye, grad_step, flags, nullptr, 0, checkpoints, k, slots,
-                         workspace, workspace_bytes_, stream);
+    const int rb = backward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, aux, grad_image,
+                                 grad_volumes, grad_tf, grad_eye, grad_step, flags, nullptr, 0, checkpoints, k,
+                                 slots, workspace, workspace_bytes_, stream);
+    return rb ? rb : finish(stream, "dvr_backward_checkpointed");
 }
 int dvr_forward_tangent(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                         const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
@@ -631,7 +755,7 @@ int dvr_forward_tangent(const dvr_volume* volumes, int32_t n_volumes, const dvr_
         cudaError_t e = dvr::launch_tangent(p, model, c.dtype, tangent, (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "dvr_forward_tangent launch");
     }
-    return DVR_OK;
+    return finish(stream, "dvr_forward_tangent");
 }
 
 int dvr_tangent_contract(const dvr_view* views, int32_t n_views, int32_t model, const float* tangent,
@@ -769,6 +893,53 @@ int dvr_orbit_eye_backward(const float* params, const float* grad_eye, int32_t n
         return fail(DVR_ERR_ARG, "need n >= 1 and non-null params, grad_eye, grad_params");
     cudaError_t e = dvr::launch_orbit_eye_backward(params, grad_eye, n, grad_params, (cudaStream_t)stream);
     return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_orbit_eye_backward launch");
+}
+
+int dvr_bounds_checked(void)
+{
+#ifdef DVR_DEBUG_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int dvr_bounds_status(int64_t* out, int32_t reset)
+{
+    g_err[0] = 0;
+#ifdef DVR_DEBUG_BOUNDS
+    if (!out) return fail(DVR_ERR_ARG, "dvr_bounds_status: out is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "dvr_bounds_status");
+    dvr::BoundsRecord r;
+    e = dvr::bounds_take(&r, reset != 0);
+    if (e != cudaSuccess) return cuda_fail(e, "dvr_bounds_status");
+    out[0] = (int64_t)r.count;
+    out[1] = r.site;
+    out[2] = r.index;
+    out[3] = r.extent;
+    return DVR_OK;
+#else
+    (void)out;
+    (void)reset;
+    return fail(DVR_ERR_UNSUPPORTED, "dvr_bounds_status: this library was built without DVR_DEBUG_BOUNDS");
+#endif
+}
+
+int dvr_bounds_cap(int32_t site, int64_t extent)
+{
+    g_err[0] = 0;
+#ifdef DVR_DEBUG_BOUNDS
+    if (site < DVR_SITE_VOLUME || site > DVR_SITE_CELL_GRADIENT || extent < 0)
+        return fail(DVR_ERR_ARG, "dvr_bounds_cap: site %d or extent %lld invalid", site, (long long)extent);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = dvr::bounds_cap(site, extent);
+    return e == cudaSuccess ? DVR_OK : cuda_fail(e, "dvr_bounds_cap");
+#else
+    (void)site;
+    (void)extent;
+    return fail(DVR_ERR_UNSUPPORTED, "dvr_bounds_cap: this library was built without DVR_DEBUG_BOUNDS");
+#endif
 }
 
 }  // extern "C"

@@ -1,7 +1,8 @@
 // The adjoint march kernel (Alg. 2) and its variant selection, templated
-// on the gather source (the volume's array, or its cell layout): included
-// by dvr_backward.cu (the volume's array) and dvr_backward_cells.cu (the
-// cell layout), which compile in parallel.
+// on the gather source (the volume's array, or its cell layout in one of
+// two record orders): included by dvr_backward.cu (the volume's array),
+// dvr_backward_cells.cu (row order) and dvr_backward_cells4.cu (4^3
+// bricks), which compile in parallel.
 #pragma once
 
 #include <atomic>
@@ -139,7 +140,7 @@ __device__ __forceinline__ void cell_run_flush(float* g, float* cg, bool v16, ui
     for (int j = 0; j < 4; ++j) r.a[j] = make_float2(0.f, 0.f);
 }
 
-template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV = kInvDepth, bool CELLS = false>
+template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV = kInvDepth, int CB = 0>
 __global__ void __launch_bounds__(kWarps * 32, GVOL ? (sizeof(VT) == 2 ? DVR_BWD_MIN_BLOCKS_16 : DVR_BWD_MIN_BLOCKS)
                                                     : DVR_BWD_QUEUE_MIN_BLOCKS)
 backward_kernel(const __grid_constant__ Params p)
@@ -180,7 +181,7 @@ backward_kernel(const __grid_constant__ Params p)
         tile_pixel(p, vw, tile - p.tile_start[v], lane, px, py);
         const bool valid = px < vw.width && py < vw.height;
         const VolumeDesc& vd = p.vol[vw.volume];
-        const Source<VT, CELLS> src{reinterpret_cast<const VT*>(vd.data), vd.cells};
+        const Source<VT, CB> src{reinterpret_cast<const VT*>(vd.data), vd.cells};
         float* __restrict__ gvol = vd.grad;
         float* __restrict__ gcell = vd.cgrad;
 
@@ -196,8 +197,8 @@ backward_kernel(const __grid_constant__ Params p)
 
         // seed (first line of Alg. 2) and the stored optical depth
         float Ch0 = 0.f, Ch1 = 0.f, Ch2 = 0.f, Ah = 0.f, sh = 0.f, sl = 0.f;
-        if (N > 0) {
-            const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
+        const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
+        if (N > 0 && in_bounds<kSitePixel>(pix, p.pixel_end)) {
             if (EA) {
                 const float4 g4 = __ldg(reinterpret_cast<const float4*>(p.grad_image) + pix);
                 Ch0 = g4.x; Ch1 = g4.y; Ch2 = g4.z; Ah = g4.w;
@@ -225,8 +226,8 @@ backward_kernel(const __grid_constant__ Params p)
         // recovery drifts over at most K samples
         const float* ck = nullptr;
         int ck_i = -1, ck_m = -1;      // next checkpointed sample below the march, its slot
-        if (INV != kInvDepth && p.ckpt && N > 0) {
-            ck = p.ckpt + (vw.pixel_offset + (long long)py * vw.width + px) * p.ckpt_slots;
+        if (INV != kInvDepth && p.ckpt && N > 0 && in_bounds<kSitePixel>(pix, p.pixel_end)) {
+            ck = p.ckpt + pix * p.ckpt_slots;
             ck_m = min((N - 1) / p.ckpt_k, p.ckpt_slots - 1);
             ck_i = ck_m * p.ckpt_k;
         }
@@ -263,7 +264,7 @@ backward_kernel(const __grid_constant__ Params p)
 #pragma unroll (GVOL ? 1 : 3)
         for (int i = N - 1; i >= 0; --i, fi -= 1.f) {
             MCell cur = n1;
-            cell_resolve<VT, CELLS>(cur, last_v);
+            cell_resolve<VT, CB>(cur, last_v);
 #pragma unroll
             for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
             n1 = n2;
@@ -470,10 +471,10 @@ backward_kernel(const __grid_constant__ Params p)
     }
 }
 
-template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV, bool CELLS>
+template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV, int CB>
 static cudaError_t launch_one(const Params& p, cudaStream_t stream)
 {
-    auto k = backward_kernel<MODEL, VT, GVOL, TFM, POS, INV, CELLS>;
+    auto k = backward_kernel<MODEL, VT, GVOL, TFM, POS, INV, CB>;
     size_t smem = 0;
     if (MODEL == DVR_EMISSION_ABSORPTION) {
         smem = sizeof(float4) * 2 * (size_t)p.R;
@@ -517,63 +518,64 @@ static cudaError_t launch_one(const Params& p, cudaStream_t stream)
 
 // The inversion ablations exist for the volume's own array only (a call
 // with the cell layout and an ablation reads the array).
-template <int MODEL, typename VT, bool GVOL, int TFM, bool CELLS>
+template <int MODEL, typename VT, bool GVOL, int TFM, int CB>
 static cudaError_t pick_pos(const Params& p, bool pos, int inv, cudaStream_t s)
 {
-    if constexpr (!CELLS && MODEL == DVR_EMISSION_ABSORPTION && std::is_same<VT, float>::value &&
+    if constexpr (CB == 0 && MODEL == DVR_EMISSION_ABSORPTION && std::is_same<VT, float>::value &&
                   (TFM == kTFPrivate || TFM == kTFWarp)) {
         if (inv == kInvAlpha32)
-            return pos ? launch_one<MODEL, VT, GVOL, TFM, true, kInvAlpha32, false>(p, s)
-                       : launch_one<MODEL, VT, GVOL, TFM, false, kInvAlpha32, false>(p, s);
+            return pos ? launch_one<MODEL, VT, GVOL, TFM, true, kInvAlpha32, 0>(p, s)
+                       : launch_one<MODEL, VT, GVOL, TFM, false, kInvAlpha32, 0>(p, s);
         if (inv == kInvAlpha64)
-            return pos ? launch_one<MODEL, VT, GVOL, TFM, true, kInvAlpha64, false>(p, s)
-                       : launch_one<MODEL, VT, GVOL, TFM, false, kInvAlpha64, false>(p, s);
+            return pos ? launch_one<MODEL, VT, GVOL, TFM, true, kInvAlpha64, 0>(p, s)
+                       : launch_one<MODEL, VT, GVOL, TFM, false, kInvAlpha64, 0>(p, s);
     }
     if (inv != kInvDepth) return cudaErrorNotSupported;
-    return pos ? launch_one<MODEL, VT, GVOL, TFM, true, kInvDepth, CELLS>(p, s)
-               : launch_one<MODEL, VT, GVOL, TFM, false, kInvDepth, CELLS>(p, s);
+    return pos ? launch_one<MODEL, VT, GVOL, TFM, true, kInvDepth, CB>(p, s)
+               : launch_one<MODEL, VT, GVOL, TFM, false, kInvDepth, CB>(p, s);
 }
 
-template <int MODEL, typename VT, bool GVOL, bool CELLS>
+template <int MODEL, typename VT, bool GVOL, int CB>
 static cudaError_t pick_tf(const Params& p, int tfm, bool pos, int inv, cudaStream_t s)
 {
     if constexpr (MODEL != DVR_EMISSION_ABSORPTION) {
-        return pick_pos<MODEL, VT, GVOL, kTFNone, CELLS>(p, pos, inv, s);
+        return pick_pos<MODEL, VT, GVOL, kTFNone, CB>(p, pos, inv, s);
     } else {
-        if (tfm == kTFNone) return pick_pos<MODEL, VT, GVOL, kTFNone, CELLS>(p, pos, inv, s);
-        if (tfm == kTFImmediate) return pick_pos<MODEL, VT, GVOL, kTFImmediate, CELLS>(p, pos, inv, s);
-        if (p.R <= kPrivateMaxR) return pick_pos<MODEL, VT, GVOL, kTFPrivate, CELLS>(p, pos, inv, s);
-        return pick_pos<MODEL, VT, GVOL, kTFWarp, CELLS>(p, pos, inv, s);
+        if (tfm == kTFNone) return pick_pos<MODEL, VT, GVOL, kTFNone, CB>(p, pos, inv, s);
+        if (tfm == kTFImmediate) return pick_pos<MODEL, VT, GVOL, kTFImmediate, CB>(p, pos, inv, s);
+        if (p.R <= kPrivateMaxR) return pick_pos<MODEL, VT, GVOL, kTFPrivate, CB>(p, pos, inv, s);
+        return pick_pos<MODEL, VT, GVOL, kTFWarp, CB>(p, pos, inv, s);
     }
 }
 
-template <int MODEL, typename VT, bool CELLS>
+template <int MODEL, typename VT, int CB>
 static cudaError_t pick_vol(const Params& p, bool gvol, int tfm, bool pos, int inv, cudaStream_t s)
 {
-    return gvol ? pick_tf<MODEL, VT, true, CELLS>(p, tfm, pos, inv, s)
-                : pick_tf<MODEL, VT, false, CELLS>(p, tfm, pos, inv, s);
+    return gvol ? pick_tf<MODEL, VT, true, CB>(p, tfm, pos, inv, s)
+                : pick_tf<MODEL, VT, false, CB>(p, tfm, pos, inv, s);
 }
 
-template <int MODEL, bool CELLS>
+template <int MODEL, int CB>
 static cudaError_t pick_dtype(const Params& p, int dtype, bool gvol, int tfm, bool pos, int inv, cudaStream_t s)
 {
     switch (dtype) {
-    case DVR_F32: return pick_vol<MODEL, float, CELLS>(p, gvol, tfm, pos, inv, s);
-    case DVR_F16: return pick_vol<MODEL, __half, CELLS>(p, gvol, tfm, pos, inv, s);
-    case DVR_BF16: return pick_vol<MODEL, __nv_bfloat16, CELLS>(p, gvol, tfm, pos, inv, s);
+    case DVR_F32: return pick_vol<MODEL, float, CB>(p, gvol, tfm, pos, inv, s);
+    case DVR_F16: return pick_vol<MODEL, __half, CB>(p, gvol, tfm, pos, inv, s);
+    case DVR_BF16: return pick_vol<MODEL, __nv_bfloat16, CB>(p, gvol, tfm, pos, inv, s);
     }
     return cudaErrorInvalidValue;
 }
 
-// Every variant for one gather source (CELLS: the cell layout).
-template <bool CELLS>
+// Every variant for one gather source (CB: 0 the volume's array, 1 / 4 the
+// cell layout with records in row order / in bricks of 4^3 cells).
+template <int CB>
 static cudaError_t launch_backward_source(const Params& p, int model, int vol_dtype, bool grad_volume,
                                           int tf_mode, bool grad_position, int inv_mode, cudaStream_t stream)
 {
     if (model == DVR_EMISSION_ABSORPTION)
-        return pick_dtype<DVR_EMISSION_ABSORPTION, CELLS>(p, vol_dtype, grad_volume, tf_mode, grad_position,
-                                                          inv_mode, stream);
-    return pick_dtype<DVR_ABSORPTION, CELLS>(p, vol_dtype, grad_volume, kTFNone, grad_position, inv_mode, stream);
+        return pick_dtype<DVR_EMISSION_ABSORPTION, CB>(p, vol_dtype, grad_volume, tf_mode, grad_position,
+                                                       inv_mode, stream);
+    return pick_dtype<DVR_ABSORPTION, CB>(p, vol_dtype, grad_volume, kTFNone, grad_position, inv_mode, stream);
 }
 
 }  // namespace dvr

@@ -144,8 +144,8 @@ forward_color_kernel(const __grid_constant__ Params p)
             T = transmittance(sh, sl);
         }
         C0 += P0; C1 += P1; C2 += P2;
-        if (valid) {
-            const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
+        const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
+        if (valid && in_bounds<kSitePixel>(pix, p.pixel_end)) {
             reinterpret_cast<float4*>(p.image)[pix] = make_float4(C0, C1, C2, -expm1f(-(sh + sl)));
             if (p.aux) {
                 float h2, l2;
@@ -188,8 +188,8 @@ backward_color_kernel(const __grid_constant__ Params p)
     make_march(R, G, m);
 
     float Ch0 = 0.f, Ch1 = 0.f, Ch2 = 0.f, Ah = 0.f, sh = 0.f, sl = 0.f;
-    if (N > 0) {
-        const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
+    const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
+    if (N > 0 && in_bounds<kSitePixel>(pix, p.pixel_end)) {
         const float4 g4 = __ldg(reinterpret_cast<const float4*>(p.grad_image) + pix);
         Ch0 = g4.x; Ch1 = g4.y; Ch2 = g4.z; Ah = g4.w;
         const float2 s2 = __ldg(reinterpret_cast<const float2*>(p.aux) + pix);

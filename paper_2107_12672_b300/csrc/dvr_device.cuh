@@ -51,6 +51,7 @@ constexpr int kFixBits = 40;         // fraction bits of a fixed-point sample po
 struct VolumeDesc {
     const void* data;
     const void* cells;               // the cell layout of data (dvr_make_cells), or null
+    int cells_brick;                 // order of its records: 1 (row order) or 4 (bricks of 4^3 cells)
     float* grad;                     // adjoint only, may be null
     float* cgrad;                    // cell-major gradient ([cells][8]) the adjoint adds into instead, or null
     int n[3];
@@ -90,7 +91,55 @@ struct Params {
     float* ckpt;                     // transmittance before samples 0, K, 2K, ... ([pixel][ckpt_slots]) or null
     int ckpt_k;
     int ckpt_slots;
+    long long pixel_end;             // one past the largest pixel index of the launch's views
 };
+
+// ---------------------------------------------------------- bounds checks
+// In a build with DVR_DEBUG_BOUNDS every index the kernels compute for the
+// volume, its cell layout, the pixel arrays and the TF rows is compared with
+// its extent before the access. A failing comparison counts the failure,
+// records the first one (site, index, extent) in this translation unit's
+// BoundsRecord and redirects the access to element 0 (loads) or drops it
+// (stores): a wrong index never reaches memory and no kernel traps. The
+// library's entry points read and clear the records after their launches
+// (bounds_take). Without DVR_DEBUG_BOUNDS the checks compile to nothing.
+enum BoundsSite { kSiteVolume = DVR_SITE_VOLUME, kSiteCells = DVR_SITE_CELLS, kSitePixel = DVR_SITE_PIXEL,
+                  kSiteTF = DVR_SITE_TF, kSiteCellGradient = DVR_SITE_CELL_GRADIENT, kSiteCount = 6 };
+
+struct BoundsRecord {
+    unsigned long long count;        // failed checks since the last bounds_take
+    long long site, index, extent;   // the first of them
+    long long cap[kSiteCount];       // test hook: a positive cap[s] lowers site s's extent to it
+};
+
+// Host side (dvr_api.cu): every translation unit registers its record, and
+// bounds_take sums them (count), returns the first failure and, with
+// reset, clears them; bounds_cap sets cap[site] in all of them.
+int register_bounds_record(const void* symbol);
+cudaError_t bounds_take(BoundsRecord* out, bool reset);
+cudaError_t bounds_cap(int site, long long cap);
+
+#ifdef DVR_DEBUG_BOUNDS
+static __device__ BoundsRecord g_bounds;
+static const int g_bounds_registered = register_bounds_record(&g_bounds);
+
+template <int SITE>
+__device__ __forceinline__ bool in_bounds(long long i, long long n)
+{
+    const long long cap = *(volatile const long long*)&g_bounds.cap[SITE];
+    if (cap > 0 && cap < n) n = cap;
+    if ((unsigned long long)i < (unsigned long long)n) return true;
+    if (atomicAdd(&g_bounds.count, 1ull) == 0ull) {
+        g_bounds.site = SITE;
+        g_bounds.index = i;
+        g_bounds.extent = n;
+    }
+    return false;
+}
+#else
+template <int SITE>
+__device__ __forceinline__ constexpr bool in_bounds(long long, long long) { return true; }
+#endif
 
 // ---------------------------------------------------------------- storage
 // get() loads one stored value; decode() turns what get() returned into its
@@ -209,6 +258,7 @@ struct Grid {
     float inv_h;                     // max(n) - 1
     int n[3];
     int top[3];                      // (n - 1) in the high word of a fixed-point position
+    uint32_t nb4[2];                 // bricks of 4^3 cells along x and y (the brick order of cell records)
 };
 
 __device__ __forceinline__ void make_grid(const VolumeDesc& v, float step, Grid& g)
@@ -220,6 +270,7 @@ __device__ __forceinline__ void make_grid(const VolumeDesc& v, float step, Grid&
     for (int a = 0; a < 3; ++a) {
         g.n[a] = v.n[a];
         g.top[a] = (v.n[a] - 1) << (kFixBits - 32);
+        if (a < 2) g.nb4[a] = (uint32_t)(v.n[a] - 1 + 3) >> 2;
         g.half[a] = __fmul_rn(__fdiv_rn((float)(v.n[a] - 1), den), 0.5f);
     }
 }
@@ -407,7 +458,7 @@ __device__ __forceinline__ void march_prev(const March& m, long long q[3])
 // the x and y lerps of both z planes run as packed pairs.
 struct Cell {
     uint32_t base;                   // index of corner (0,0,0)
-    uint32_t cell;                   // index of the cell (its record in the cell layout)
+    uint32_t cell;                   // index of the cell's record (cell layout, cell-major gradient)
     float fx, fy, fz;
     bool in[3];                      // false where g was clamped
     float2 vz[4];
@@ -448,6 +499,32 @@ static __device__ __noinline__ AxisClamp clamp_axis(long long q, int n)
     return r;
 }
 
+// Index of cell (i, j, k) in the records of the cell layout: row order
+// (CB <= 1: x fastest), or bricks of 4 x 4 x 4 cells, bricks in row order
+// and cells in row order within a brick (CB = 4: the 8 cells around a ray's
+// position share 2 KB of 16-byte records instead of rows 16 KB apart).
+template <int CB>
+__host__ __device__ __forceinline__ uint32_t cell_index(const int n[3], const uint32_t nb4[2], uint32_t i,
+                                                        uint32_t j, uint32_t k)
+{
+    if constexpr (CB == 4)
+        return ((((k >> 2) * nb4[1] + (j >> 2)) * nb4[0] + (i >> 2)) << 6) | ((k & 3u) << 4) | ((j & 3u) << 2) |
+               (i & 3u);
+    else
+        return i + (uint32_t)(n[0] - 1) * (j + (uint32_t)(n[1] - 1) * k);
+}
+
+// Number of records of the cell layout (bricks padded to whole bricks).
+template <int CB>
+__host__ __device__ __forceinline__ long long cell_records(const int n[3])
+{
+    if constexpr (CB == 4)
+        return (long long)((n[0] + 2) >> 2) * ((n[1] + 2) >> 2) * ((n[2] + 2) >> 2) * 64;
+    else
+        return (long long)(n[0] - 1) * (n[1] - 1) * (n[2] - 1);
+}
+
+template <int CB = 0>
 __device__ __forceinline__ void cell_locate(const Grid& G, const long long q[3], Cell& c)
 {
     int j[3];
@@ -472,7 +549,14 @@ __device__ __forceinline__ void cell_locate(const Grid& G, const long long q[3],
     }
     c.fx = fr[0]; c.fy = fr[1]; c.fz = fr[2];
     c.base = (uint32_t)j[0] + (uint32_t)G.n[0] * ((uint32_t)j[1] + (uint32_t)G.n[1] * (uint32_t)j[2]);
-    c.cell = (uint32_t)j[0] + (uint32_t)(G.n[0] - 1) * ((uint32_t)j[1] + (uint32_t)(G.n[1] - 1) * (uint32_t)j[2]);
+    c.cell = cell_index<CB>(G.n, G.nb4, (uint32_t)j[0], (uint32_t)j[1], (uint32_t)j[2]);
+#ifdef DVR_DEBUG_BOUNDS
+    // corner (1, 1, 1) is the cell's last value; a record (or the cell-major
+    // gradient's pair of float4) per cell, bricks padded to whole bricks
+    const long long sy = G.n[0], sz = (long long)G.n[0] * G.n[1];
+    if (!in_bounds<kSiteVolume>((long long)c.base + sz + sy + 1, sz * G.n[2])) c.base = 0;
+    if (!in_bounds<kSiteCells>(c.cell, cell_records<CB>(G.n))) c.cell = 0;
+#endif
 }
 
 template <typename VT>
@@ -633,41 +717,42 @@ __device__ __forceinline__ void depth_add_density(float& sh, float& sl, float dt
     sl = __fmaf_rn(dt, d.dd, sl);
 }
 
-// The gather source of a march: the volume's own array, or its cell
-// layout (CELLS).
-template <typename VT, bool CELLS>
+// The gather source of a march: the volume's own array (CB = 0), or its
+// cell layout with records in row order (CB = 1) or in bricks of 4^3 cells
+// (CB = 4).
+template <typename VT, int CB>
 struct Source {
     const VT* __restrict__ vol;
     const void* __restrict__ cells;
 };
 
-template <typename VT, bool CELLS>
-__device__ __forceinline__ void source_load(const Source<VT, CELLS>& src, const Grid& G, Cell& c)
+template <typename VT, int CB>
+__device__ __forceinline__ void source_load(const Source<VT, CB>& src, const Grid& G, Cell& c)
 {
-    if constexpr (CELLS)
+    if constexpr (CB > 0)
         CellLoad<VT>::get(src.cells, c);
     else
         cell_load<VT>(src.vol, G, c);
 }
 
 // The binary32 corners of a fetched cell (a no-op for binary32 storage).
-template <typename VT, bool CELLS>
+template <typename VT, int CB>
 __device__ __forceinline__ void source_decode(Cell& c)
 {
-    if constexpr (CELLS)
+    if constexpr (CB > 0)
         cell_decode_cells<VT>(c);
     else
         cell_decode<VT>(c);
 }
 
-template <typename VT, bool CELLS>
-__device__ __forceinline__ void fetch_sample(const Source<VT, CELLS>& src, const Grid& G, const March& m,
+template <typename VT, int CB>
+__device__ __forceinline__ void fetch_sample(const Source<VT, CB>& src, const Grid& G, const March& m,
                                              int i, Cell& c)
 {
     long long q[3];
     march_pos(m, i, q);
-    cell_locate(G, q, c);
-    source_load<VT, CELLS>(src, G, c);
+    cell_locate<CB>(G, q, c);
+    source_load<VT, CB>(src, G, c);
 }
 
 // The march's fetch of the sample at q when the previous sample (in march
@@ -680,25 +765,25 @@ struct MCell {
     bool reuse;
 };
 
-template <typename VT, bool CELLS>
-__device__ __forceinline__ void fetch_sample_reuse(const Source<VT, CELLS>& src, const Grid& G,
+template <typename VT, int CB>
+__device__ __forceinline__ void fetch_sample_reuse(const Source<VT, CB>& src, const Grid& G,
                                                    const long long q[3], uint32_t prev_base, MCell& mc)
 {
-    cell_locate(G, q, mc.c);
+    cell_locate<CB>(G, q, mc.c);
     mc.reuse = mc.c.base == prev_base;
-    if (!mc.reuse) source_load<VT, CELLS>(src, G, mc.c);
+    if (!mc.reuse) source_load<VT, CB>(src, G, mc.c);
 }
 
 // Corners of a fetched sample: its own loads (decoded here, where they are
 // consumed), or the decoded corners of the previous one.
-template <typename VT, bool CELLS>
+template <typename VT, int CB>
 __device__ __forceinline__ void cell_resolve(MCell& mc, const float2 last[4])
 {
     if (mc.reuse) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) mc.c.vz[k] = last[k];
     } else {
-        source_decode<VT, CELLS>(mc.c);
+        source_decode<VT, CB>(mc.c);
     }
 }
 
@@ -737,6 +822,7 @@ __device__ __forceinline__ void tf_lookup(const float4* __restrict__ tf, int R, 
     const float u = s.slope ? __fmaf_rn(d.dd, Rm1, __fmul_rn(d.v0, Rm1)) : __fmul_rn(dc, Rm1);
     s.k = min((int)u, R - 2);
     s.fr = s.slope ? __fmaf_rn(d.dd, Rm1, __fmaf_rn(d.v0, Rm1, -(float)s.k)) : __fsub_rn(u, (float)s.k);
+    if (!in_bounds<kSiteTF>(s.k, R - 1)) s.k = 0;      // rows k and k + 1 (and their gradient rows)
     if (s.k != t.k) {
         t.a = tf[2 * s.k];
         t.dc = tf[2 * s.k + 1];

@@ -16,8 +16,9 @@ namespace dvr {
 // CKPT: also record the transmittance 1 - A_i before every K-th sample
 // (i = 0, K, 2K, ...) of each ray, for the adjoint's opacity recovery in
 // the paper's alpha form.
-// CELLS: gather the corners from the volume's cell layout.
-template <int MODEL, typename VT, bool CKPT = false, bool CELLS = false>
+// CB: gather the corners from the volume's array (0) or its cell layout
+// with records in row order (1) or in bricks of 4^3 cells (4).
+template <int MODEL, typename VT, bool CKPT = false, int CB = 0>
 __global__ void __launch_bounds__(kWarps * 32, DVR_FWD_MIN_BLOCKS)
 forward_kernel(const __grid_constant__ Params p)
 {
@@ -39,7 +40,7 @@ forward_kernel(const __grid_constant__ Params p)
         tile_pixel(p, vw, tile - p.tile_start[v], lane, px, py);
         const bool valid = px < vw.width && py < vw.height;
         const VolumeDesc& vd = p.vol[vw.volume];
-        const Source<VT, CELLS> src{reinterpret_cast<const VT*>(vd.data), vd.cells};
+        const Source<VT, CB> src{reinterpret_cast<const VT*>(vd.data), vd.cells};
 
         Grid G;
         make_grid(vd, p.step_voxels, G);
@@ -56,8 +57,9 @@ forward_kernel(const __grid_constant__ Params p)
         float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;   // colour of the finished blocks
         float P0 = 0.f, P1 = 0.f, P2 = 0.f;            // colour of the current block
         // checkpoints of this ray: slot m holds 1 - A before sample m K
-        float* ck = CKPT && valid ? p.ckpt + (vw.pixel_offset + (long long)py * vw.width + px) * p.ckpt_slots
-                                  : nullptr;
+        const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
+        const bool store = valid && in_bounds<kSitePixel>(pix, p.pixel_end);
+        float* ck = CKPT && store ? p.ckpt + pix * p.ckpt_slots : nullptr;
         int ck_left = 0, ck_m = 0;   // samples until the next checkpoint, its slot
         // software pipeline: the corners of samples i+1 and i+2 are in
         // flight while sample i is composited (positions past the ray end are
@@ -86,7 +88,7 @@ forward_kernel(const __grid_constant__ Params p)
                 --ck_left;
             }
             MCell cur = n1;
-            cell_resolve<VT, CELLS>(cur, last_v);
+            cell_resolve<VT, CB>(cur, last_v);
 #pragma unroll
             for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
             n1 = n2;
@@ -113,8 +115,7 @@ forward_kernel(const __grid_constant__ Params p)
             }
         }
         C0 += P0; C1 += P1; C2 += P2;
-        if (valid) {
-            const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
+        if (store) {
             const float A = -expm1f(-(sh + sl));
             if (MODEL == DVR_EMISSION_ABSORPTION)
                 reinterpret_cast<float4*>(p.image)[pix] = make_float4(C0, C1, C2, A);
@@ -134,10 +135,10 @@ forward_kernel(const __grid_constant__ Params p)
     }
 }
 
-template <int MODEL, typename VT, bool CKPT = false, bool CELLS = false>
+template <int MODEL, typename VT, bool CKPT = false, int CB = 0>
 static cudaError_t launch(const Params& p, cudaStream_t stream)
 {
-    auto k = forward_kernel<MODEL, VT, CKPT, CELLS>;
+    auto k = forward_kernel<MODEL, VT, CKPT, CB>;
     const int blocks = (p.total_tiles + kWarps - 1) / kWarps;
     // shared memory holds only this TF, the rest of the SM's 256 KB stays
     // L1 cache for the gathers
@@ -146,27 +147,34 @@ static cudaError_t launch(const Params& p, cudaStream_t stream)
     return cudaGetLastError();
 }
 
+template <int CB>
+static cudaError_t launch_cells(const Params& p, int model, int vol_dtype, cudaStream_t stream)
+{
+    if (model == DVR_EMISSION_ABSORPTION) {
+        switch (vol_dtype) {
+        case DVR_F32: return launch<DVR_EMISSION_ABSORPTION, float, false, CB>(p, stream);
+        case DVR_F16: return launch<DVR_EMISSION_ABSORPTION, __half, false, CB>(p, stream);
+        case DVR_BF16: return launch<DVR_EMISSION_ABSORPTION, __nv_bfloat16, false, CB>(p, stream);
+        }
+    } else {
+        switch (vol_dtype) {
+        case DVR_F32: return launch<DVR_ABSORPTION, float, false, CB>(p, stream);
+        case DVR_F16: return launch<DVR_ABSORPTION, __half, false, CB>(p, stream);
+        case DVR_BF16: return launch<DVR_ABSORPTION, __nv_bfloat16, false, CB>(p, stream);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_forward(const Params& p, int model, int vol_dtype, cudaStream_t stream)
 {
     if (p.ckpt) {
         if (model != DVR_EMISSION_ABSORPTION || vol_dtype != DVR_F32) return cudaErrorNotSupported;
         return launch<DVR_EMISSION_ABSORPTION, float, true>(p, stream);
     }
-    if (p.vol[0].cells) {                   // every volume of the launch has its cell layout
-        if (model == DVR_EMISSION_ABSORPTION) {
-            switch (vol_dtype) {
-            case DVR_F32: return launch<DVR_EMISSION_ABSORPTION, float, false, true>(p, stream);
-            case DVR_F16: return launch<DVR_EMISSION_ABSORPTION, __half, false, true>(p, stream);
-            case DVR_BF16: return launch<DVR_EMISSION_ABSORPTION, __nv_bfloat16, false, true>(p, stream);
-            }
-        } else {
-            switch (vol_dtype) {
-            case DVR_F32: return launch<DVR_ABSORPTION, float, false, true>(p, stream);
-            case DVR_F16: return launch<DVR_ABSORPTION, __half, false, true>(p, stream);
-            case DVR_BF16: return launch<DVR_ABSORPTION, __nv_bfloat16, false, true>(p, stream);
-            }
-        }
-        return cudaErrorInvalidValue;
+    if (p.vol[0].cells) {                   // every volume of the launch has its cell layout, one order
+        if (p.vol[0].cells_brick == 4) return launch_cells<4>(p, model, vol_dtype, stream);
+        return launch_cells<1>(p, model, vol_dtype, stream);
     }
     if (model == DVR_EMISSION_ABSORPTION) {
         switch (vol_dtype) {

@@ -103,7 +103,7 @@ __device__ __forceinline__ void ray_tangent(const float e[3], const Ray& R, int 
         }
 }
 
-template <int MODEL, typename VT, bool CELLS = false>
+template <int MODEL, typename VT, int CB = 0>
 __global__ void __launch_bounds__(kWarps * 32)
 tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
 {
@@ -124,7 +124,7 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
     const bool valid = px < vw.width && py < vw.height;
     if (!valid) return;                          // no warp-wide operations follow
     const VolumeDesc& vd = p.vol[vw.volume];
-    const Source<VT, CELLS> src{reinterpret_cast<const VT*>(vd.data), vd.cells};
+    const Source<VT, CB> src{reinterpret_cast<const VT*>(vd.data), vd.cells};
     Grid G;
     make_grid(vd, p.step_voxels, G);
     const float* ep = p.eye + 3 * (p.view_base + v);
@@ -147,7 +147,7 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
     if (N > 0) fetch_sample(src, G, m, 0, nxt);
     for (int i = 0; i < N; ++i) {
         Cell c = nxt;
-        source_decode<VT, CELLS>(c);
+        source_decode<VT, CB>(c);
         fetch_sample(src, G, m, i + 1, nxt);
         float dg[3];
         const Density d = cell_density_grad(c, dg);
@@ -199,6 +199,7 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
     }
     C0 += P0; C1 += P1; C2 += P2;
     const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
+    if (!in_bounds<kSitePixel>(pix, p.pixel_end)) return;
     const float S = sh + sl;
     if (EA) {
         if (p.image) reinterpret_cast<float4*>(p.image)[pix] = make_float4(C0, C1, C2, -expm1f(-S));
@@ -255,10 +256,12 @@ static cudaError_t launch_t(const Params& p, float* tangent, cudaStream_t s)
 {
     const size_t smem = MODEL == DVR_EMISSION_ABSORPTION ? 2 * sizeof(float4) * (size_t)p.R : 0;
     const dim3 grid((p.total_tiles + kWarps - 1) / kWarps);
-    if (p.vol[0].cells)
-        tangent_kernel<MODEL, VT, true><<<grid, kWarps * 32, smem, s>>>(p, tangent);
+    if (p.vol[0].cells && p.vol[0].cells_brick == 4)
+        tangent_kernel<MODEL, VT, 4><<<grid, kWarps * 32, smem, s>>>(p, tangent);
+    else if (p.vol[0].cells)
+        tangent_kernel<MODEL, VT, 1><<<grid, kWarps * 32, smem, s>>>(p, tangent);
     else
-        tangent_kernel<MODEL, VT, false><<<grid, kWarps * 32, smem, s>>>(p, tangent);
+        tangent_kernel<MODEL, VT, 0><<<grid, kWarps * 32, smem, s>>>(p, tangent);
     return cudaGetLastError();
 }
 

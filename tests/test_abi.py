@@ -37,13 +37,38 @@ def test_library_loads_and_exports_every_symbol():
     assert exported == set(_declared())
 
 
+def test_bounds_checked_library_exports_the_same_abi():
+    """libdvr_bounds.so (DVR_DEBUG_BOUNDS) exports exactly the symbols of
+    the header and says it is the checked build; the release library says
+    it is not and refuses the bounds calls without a GPU."""
+    from paper_2107_12672_b300 import build
+    path = build.build(bounds=True)
+    lib = ctypes.CDLL(path)
+    lib.dvr_last_error.restype = ctypes.c_char_p
+    assert lib.dvr_abi_version() == _abi.ABI_VERSION
+    assert lib.dvr_bounds_checked() == 1
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    assert set(re.findall(r"\bT (dvr_\w+)", out)) == set(_declared())
+    # argument errors come before any CUDA call
+    assert lib.dvr_bounds_cap(ctypes.c_int32(0), ctypes.c_int64(5)) == -1
+    assert lib.dvr_bounds_cap(ctypes.c_int32(_abi.DVR_SITE_CELL_GRADIENT + 1), ctypes.c_int64(5)) == -1
+    assert lib.dvr_bounds_cap(ctypes.c_int32(_abi.DVR_SITE_TF), ctypes.c_int64(-1)) == -1
+    assert lib.dvr_bounds_status(None, 0) == -1
+    rel = _abi.load()
+    assert rel.dvr_bounds_checked() == 0
+    out4 = (ctypes.c_int64 * 4)()
+    assert rel.dvr_bounds_status(out4, 1) == -4
+    assert b"DVR_DEBUG_BOUNDS" in rel.dvr_last_error()
+    assert rel.dvr_bounds_cap(_abi.DVR_SITE_TF, 5) == -4
+
+
 def test_struct_layout_matches_header(tmp_path):
     prog = tmp_path / "layout.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "dvr.h"\n'
         "int main(void){\n"
-        'printf("%zu %zu %zu %zu\\n", sizeof(dvr_volume), offsetof(dvr_volume, dtype), offsetof(dvr_volume, data),'
-        " offsetof(dvr_volume, cells));\n"
+        'printf("%zu %zu %zu %zu %zu\\n", sizeof(dvr_volume), offsetof(dvr_volume, dtype), offsetof(dvr_volume, data),'
+        " offsetof(dvr_volume, cells), offsetof(dvr_volume, cells_brick));\n"
         'printf("%zu %zu\\n", sizeof(dvr_tf), offsetof(dvr_tf, rgba));\n'
         'printf("%zu %zu %zu %zu\\n", sizeof(dvr_view), offsetof(dvr_view, volume), offsetof(dvr_view, lens),'
         " offsetof(dvr_view, pixel_offset));\n"
@@ -52,7 +77,8 @@ def test_struct_layout_matches_header(tmp_path):
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     lines = subprocess.check_output([str(exe)], text=True).split("\n")
     V, T, W = _abi.DvrVolume, _abi.DvrTF, _abi.DvrView
-    assert lines[0].split() == [str(ctypes.sizeof(V)), str(V.dtype.offset), str(V.data.offset), str(V.cells.offset)]
+    assert lines[0].split() == [str(ctypes.sizeof(V)), str(V.dtype.offset), str(V.data.offset), str(V.cells.offset),
+                                str(V.cells_brick.offset)]
     assert lines[1].split() == [str(ctypes.sizeof(T)), str(T.rgba.offset)]
     assert lines[2].split() == [str(ctypes.sizeof(W)), str(W.volume.offset), str(W.lens.offset),
                                 str(W.pixel_offset.offset)]
@@ -90,6 +116,7 @@ def _one_view(w=4, h=4, volume=0, lens=0.4, ortho=0):
     ("misaligned_cells", -1),
     ("cells_for_colour_volume", -1),
     ("cells_on_some_volumes", -1),
+    ("bad_cells_brick", -1),
 ])
 def test_argument_errors_need_no_gpu(case, code):
     """Invalid arguments are rejected on the host before any CUDA call."""
@@ -134,6 +161,10 @@ def test_argument_errors_need_no_gpu(case, code):
         two[0] = _abi.DvrVolume(8, 8, 8, _abi.DVR_F32, 4096, 8192)
         two[1] = _abi.DvrVolume(8, 8, 8, _abi.DVR_F32, 4096, None)
         rc = _call_forward(two, 2, None, 0, view, 1)
+    elif case == "bad_cells_brick":
+        vols[0].cells = 8192
+        vols[0].cells_brick = 8
+        rc = _call_forward(vols, 1, None, 0, view, 1)
     assert rc == code
     assert lib.dvr_last_error().decode()
 
@@ -312,6 +343,10 @@ def test_cell_layout_size_and_argument_errors():
     v32 = _abi.DvrVolume(5, 6, 7, _abi.DVR_F32, 4096, None)
     assert lib.dvr_cells_bytes(ctypes.byref(v32)) == 4 * 5 * 6 * 8 * 4
     assert lib.dvr_cells_bytes(ctypes.byref(_abi.DvrVolume(1, 6, 7, _abi.DVR_F32, 4096, None))) == 0
+    # bricks of 4^3 cells: whole bricks (4 x 5 x 6 cells -> 1 x 2 x 2 bricks)
+    v4 = _abi.DvrVolume(5, 6, 7, _abi.DVR_BF16, 4096, None, 4, 0)
+    assert lib.dvr_cells_bytes(ctypes.byref(v4)) == 1 * 2 * 2 * 64 * 8 * 2
+    assert lib.dvr_cells_bytes(ctypes.byref(_abi.DvrVolume(5, 6, 7, _abi.DVR_BF16, 4096, None, 2, 0))) == 0
     assert lib.dvr_make_cells(ctypes.byref(v), 8192, 100, None) == _abi.DVR_OK - 1
     assert lib.dvr_make_cells(ctypes.byref(v), 8200, 1 << 20, None) == _abi.DVR_OK - 1
     assert lib.dvr_make_cells(ctypes.byref(_abi.DvrVolume(5, 6, 7, 9, 4096, None)), 8192, 1 << 20, None) == -2

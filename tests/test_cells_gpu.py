@@ -17,21 +17,37 @@ pytestmark = pytest.mark.gpu
 DTYPES = [torch.float32, torch.float16, torch.bfloat16]
 
 
+def _bits(t):
+    return t.view(torch.int16) if t.element_size() == 2 else t.view(torch.int32)
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
-def test_cell_layout_contents(dtype):
+@pytest.mark.parametrize("brick", [1, 4])
+def test_cell_layout_contents(dtype, brick):
     """Cell (i, j, k) holds V(i,j,k), V(i,j,k+1), V(i+1,j,k), V(i+1,j,k+1),
-    V(i,j+1,k), V(i,j+1,k+1), V(i+1,j+1,k), V(i+1,j+1,k+1), bit for bit, on
-    a box with three different sizes."""
-    v = to_dev(np.random.default_rng(1).normal(size=(7, 5, 9)).astype(np.float32), dtype)
-    c = dvr.make_cells(v).view(6, 4, 8, 8)          # [k][j][i][corner]
+    V(i,j+1,k), V(i,j+1,k+1), V(i+1,j+1,k), V(i+1,j+1,k+1), bit for bit, at
+    record i + (nx-1)(j + (ny-1)k) (row order) or 64 (bi + bx (bj + by bk))
+    + (i & 3) + 4 (j & 3) + 16 (k & 3) (bricks of 4^3 cells, (bi, bj, bk) =
+    (i, j, k) / 4), on a box with three different sizes that are no
+    multiples of 4."""
+    v = to_dev(np.random.default_rng(1).normal(size=(7, 6, 11)).astype(np.float32), dtype)
+    c = dvr.make_cells(v, brick=brick).view(-1, 8)
     ref = torch.stack([v[:-1, :-1, :-1], v[1:, :-1, :-1], v[:-1, :-1, 1:], v[1:, :-1, 1:],
-                       v[:-1, 1:, :-1], v[1:, 1:, :-1], v[:-1, 1:, 1:], v[1:, 1:, 1:]], dim=-1)
-    assert torch.equal(c.view(torch.int16) if dtype != torch.float32 else c.view(torch.int32),
-                       ref.contiguous().view(torch.int16) if dtype != torch.float32 else ref.contiguous().view(torch.int32))
+                       v[:-1, 1:, :-1], v[1:, 1:, :-1], v[:-1, 1:, 1:], v[1:, 1:, 1:]], dim=-1)   # [k][j][i][8]
+    nz, ny, nx = 6, 5, 10                                                                        # cells per axis
+    k, j, i = torch.meshgrid(torch.arange(nz), torch.arange(ny), torch.arange(nx), indexing="ij")
+    if brick == 1:
+        rec = i + nx * (j + ny * k)
+    else:
+        bx, by = (nx + 3) // 4, (ny + 3) // 4
+        rec = 64 * (i // 4 + bx * (j // 4 + by * (k // 4))) + (i % 4) + 4 * (j % 4) + 16 * (k % 4)
+        assert c.shape[0] == bx * by * ((nz + 3) // 4) * 64
+    got = c[rec.reshape(-1).to(c.device)]
+    assert torch.equal(_bits(got.contiguous()), _bits(ref.reshape(-1, 8).contiguous()))
 
 
-def _march(w, vols, tf, cells, G, want):
-    sc = dvr.Scene.make(vols, tf, w.model, w.views, cells=cells)
+def _march(w, vols, tf, cells, G, want, brick=1):
+    sc = dvr.Scene.make(vols, tf, w.model, w.views, cells=cells, cells_brick=brick)
     eye = to_dev(w.eye)
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
     img, aux = dvr.forward(None, None, None, None, eye, w.step_voxels, scene=sc, sample_count=count)
@@ -42,7 +58,8 @@ def _march(w, vols, tf, cells, G, want):
 
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("model", ["emission_absorption", "absorption"])
-def test_cells_equal_linear(dtype, model):
+@pytest.mark.parametrize("brick", [1, 4])
+def test_cells_equal_linear(dtype, model, brick):
     """Forward and adjoint (volume, TF and eye gradients) of several views of
     uneven sizes over two non-cubic volumes, ragged tiles included, with and
     without the cell layout."""
@@ -57,8 +74,8 @@ def test_cells_equal_linear(dtype, model):
     G = to_dev(seeded_grad_image(sum(v.width * v.height for v in views), nc, 9))
     want = ("volume", "tf", "eye") if tf is not None else ("volume", "eye")
     a = _march(w, vols, tf, None, G, want)
-    cells = [dvr.make_cells(v) for v in vols]
-    b = _march(w, vols, tf, cells, G, want)
+    cells = [dvr.make_cells(v, brick=brick) for v in vols]
+    b = _march(w, vols, tf, cells, G, want, brick)
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and a[2] == b[2]
     for i in range(len(vols)):
         assert_close(b[3]["volume"][i].cpu().numpy(), a[3]["volume"][i].cpu().numpy(), 1e-4, f"volume {i}")
@@ -75,12 +92,13 @@ def test_cells_forward_tangent_bit_identical():
     tf = to_dev(w.tf)
     eye = to_dev(w.eye)
     out = []
-    for cells in (None, [dvr.make_cells(vol)]):
-        sc = dvr.Scene.make([vol], tf, w.model, w.views, cells=cells)
+    for brick, cells in ((1, None), (1, [dvr.make_cells(vol)]), (4, [dvr.make_cells(vol, brick=4)])):
+        sc = dvr.Scene.make([vol], tf, w.model, w.views, cells=cells, cells_brick=brick)
         img, tan = dvr.forward_tangent(None, None, None, None, eye, w.step_voxels, scene=sc)
         torch.cuda.synchronize()
         out.append((img, tan))
-    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    for o in out[1:]:
+        assert torch.equal(out[0][0], o[0]) and torch.equal(out[0][1], o[1])
 
 
 def test_cells_full_size_1024():
@@ -94,8 +112,8 @@ def test_cells_full_size_1024():
     G = torch.zeros((sum(v.width * v.height for v in w.views), 4), device="cuda")
     G[::97] = 1.0
     a = _march(w, [vol], tf, None, G, ("volume", "tf"))
-    cells = [dvr.make_cells(vol)]
-    b = _march(w, [vol], tf, cells, G, ("volume", "tf"))
+    cells = [dvr.make_cells(vol, brick=4)]
+    b = _march(w, [vol], tf, cells, G, ("volume", "tf"), brick=4)
     assert torch.equal(a[0], b[0]) and a[2] == b[2]
     diff = (a[3]["volume"][0] - b[3]["volume"][0]).abs().max().item()
     assert diff <= 1e-5 * a[3]["volume"][0].abs().max().item(), diff
@@ -117,8 +135,8 @@ def test_cell_gradient_equals_vertex_scatter(dtype, model):
     nc = 4 if model == "emission_absorption" else 1
     G = to_dev(seeded_grad_image(sum(v.width * v.height for v in views), nc, 9))
     want = ("volume", "tf", "eye") if tf is not None else ("volume", "eye")
-    for cells in (None, [dvr.make_cells(v) for v in vols]):
-        sc = dvr.Scene.make(vols, tf, model, views, cells=cells)
+    for brick, cells in ((1, None), (1, [dvr.make_cells(v) for v in vols]), (4, [dvr.make_cells(v, brick=4) for v in vols])):
+        sc = dvr.Scene.make(vols, tf, model, views, cells=cells, cells_brick=brick)
         _, aux = dvr.forward(None, None, None, None, eye, 0.4, scene=sc)
         a = dvr.backward(None, None, None, None, eye, 0.4, aux, G, scene=sc, want=want)
         b = dvr.backward(None, None, None, None, eye, 0.4, aux, G, scene=sc, want=want, cell_gradient=True)
