@@ -261,7 +261,13 @@ backward_kernel(const __grid_constant__ Params p)
             march_prev(m, q);
         }
         float fi = (float)(N - 1);     // sample index i as a float (exact below 2^24)
-#pragma unroll (GVOL ? 1 : 3)
+        // unrolled so that the gather pipeline's registers rotate instead of
+        // being copied: x3 for the tile-queue kernels; x2 for the
+        // volume-gradient kernels on the cell layout (1024^3 FP16, 4 views:
+        // 258.5 -> 238.1 instructions per warp-sample, 188.3 -> 177.2 ms);
+        // the volume-gradient kernels on the array stay rolled (x2 cost them
+        // 26% on 512^3, with 8 corner loads in flight per sample)
+#pragma unroll (GVOL ? (CB > 0 ? 2 : 1) : 3)
         for (int i = N - 1; i >= 0; --i, fi -= 1.f) {
             MCell cur = n1;
             cell_resolve<VT, CB>(cur, last_v);

@@ -33,6 +33,13 @@ constexpr int kFixBits = 40;         // fraction bits of a fixed-point sample po
 #ifndef DVR_FWD_MIN_BLOCKS
 #define DVR_FWD_MIN_BLOCKS 4
 #endif
+// The forward on the cell layout of a 16-bit volume holds 4 words of a
+// record per sample in flight instead of 8 corners: 5 blocks (at most 102
+// registers, 93 used, no spills). 1024^3 FP16, 4 views of 2048^2: forward
+// 84.2 -> 74.3 ms. (The array and binary32 forwards spill at 5.)
+#ifndef DVR_FWD_MIN_BLOCKS_CELLS16
+#define DVR_FWD_MIN_BLOCKS_CELLS16 5
+#endif
 #ifndef DVR_BWD_MIN_BLOCKS
 #define DVR_BWD_MIN_BLOCKS 1
 #endif
@@ -759,18 +766,26 @@ __device__ __forceinline__ void fetch_sample(const Source<VT, CB>& src, const Gr
 // order) lies in cell `prev_base`: if it is in the same cell, no corner is
 // loaded (the lane sits out the warp's load instructions, which then touch
 // fewer cache sectors) and c.reuse is set; cell_resolve later copies the
-// corners from the previous sample once those have arrived.
+// corners from the previous sample once those have arrived. REUSE = false
+// turns this off for the cell layout (every sample loads its record, an
+// L1 hit when the cell is the previous one's): a lane's cell changes every
+// few samples and some lane's almost every sample, so the compare and the
+// copies cost every lane instructions, which the forward, bound by issue,
+// saves (1024^3 FP16, 4 views: forward 91.3 -> 85.6 ms, 138.5 -> 128.3
+// instructions per warp-sample); the adjoint, whose record loads compete
+// with its shared-memory traffic, keeps the reuse (188.3 vs 193.0 ms
+// without). The 8 scalar loads of the volume's array always reuse.
 struct MCell {
     Cell c;
     bool reuse;
 };
 
-template <typename VT, int CB>
+template <typename VT, int CB, bool REUSE = true>
 __device__ __forceinline__ void fetch_sample_reuse(const Source<VT, CB>& src, const Grid& G,
                                                    const long long q[3], uint32_t prev_base, MCell& mc)
 {
     cell_locate<CB>(G, q, mc.c);
-    mc.reuse = mc.c.base == prev_base;
+    mc.reuse = (CB == 0 || REUSE) && mc.c.base == prev_base;
     if (!mc.reuse) source_load<VT, CB>(src, G, mc.c);
 }
 

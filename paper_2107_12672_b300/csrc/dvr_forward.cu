@@ -19,7 +19,8 @@ namespace dvr {
 // CB: gather the corners from the volume's array (0) or its cell layout
 // with records in row order (1) or in bricks of 4^3 cells (4).
 template <int MODEL, typename VT, bool CKPT = false, int CB = 0>
-__global__ void __launch_bounds__(kWarps * 32, DVR_FWD_MIN_BLOCKS)
+__global__ void __launch_bounds__(kWarps * 32, CB > 0 && sizeof(VT) == 2 ? DVR_FWD_MIN_BLOCKS_CELLS16
+                                                                          : DVR_FWD_MIN_BLOCKS)
 forward_kernel(const __grid_constant__ Params p)
 {
     extern __shared__ float4 tf_s[];            // 2R float4 (emission-absorption only)
@@ -63,58 +64,62 @@ forward_kernel(const __grid_constant__ Params p)
         int ck_left = 0, ck_m = 0;   // samples until the next checkpoint, its slot
         // software pipeline: the corners of samples i+1 and i+2 are in
         // flight while sample i is composited (positions past the ray end are
-        // clamped to the box, so the extra fetches stay in bounds); a sample
-        // in the same cell as its predecessor loads nothing. Positions are
-        // fixed point, stepped by exact integer additions.
+        // clamped to the box, so the extra fetches stay in bounds); from the
+        // volume's array a sample in the same cell as its predecessor loads
+        // nothing, from the cell layout every sample loads its record.
+        // Positions are fixed point, stepped by exact integer additions.
         TFCache tfc;
         tf_cache_init(tfc);
         MCell n1, n2;
         float2 last_v[4];
         long long q[3] = {m.g0[0], m.g0[1], m.g0[2]};   // position of the next fetch
         if (N > 0) {
-            fetch_sample_reuse(src, G, q, 0xffffffffu, n1);
+            fetch_sample_reuse<VT, CB, false>(src, G, q, 0xffffffffu, n1);
             march_next(m, q);
-            fetch_sample_reuse(src, G, q, n1.c.base, n2);
+            fetch_sample_reuse<VT, CB, false>(src, G, q, n1.c.base, n2);
             march_next(m, q);
         }
+        // blocks of kColourBlock samples: the colour of a block is summed
+        // apart and added to the total after it (a per-sample test for the
+        // block's end cost 6 instructions per warp-sample)
+        for (int i0 = 0; i0 < N; i0 += kColourBlock) {
+            const int i1 = min(i0 + kColourBlock, N);
 #pragma unroll 3
-        for (int i = 0; i < N; ++i) {
-            if (CKPT) {
-                if (ck_left == 0) {
-                    if (ck && ck_m < p.ckpt_slots) ck[ck_m] = T;
-                    ++ck_m;
-                    ck_left = p.ckpt_k;
+            for (int i = i0; i < i1; ++i) {
+                if (CKPT) {
+                    if (ck_left == 0) {
+                        if (ck && ck_m < p.ckpt_slots) ck[ck_m] = T;
+                        ++ck_m;
+                        ck_left = p.ckpt_k;
+                    }
+                    --ck_left;
                 }
-                --ck_left;
-            }
-            MCell cur = n1;
-            cell_resolve<VT, CB>(cur, last_v);
+                MCell cur = n1;
+                cell_resolve<VT, CB>(cur, last_v);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
-            n1 = n2;
-            fetch_sample_reuse(src, G, q, n1.c.base, n2);      // sample i + 2
-            march_next(m, q);
-            const Cell& c = cur.c;
-            const Density d = cell_density(c);
-            if (MODEL == DVR_EMISSION_ABSORPTION) {
-                TFSample s;
-                tf_lookup(tf_s, p.R, d, tfc, s);
-                const float alpha = sample_alpha(G.dt, s.c.w);
-                depth_add(sh, sl, G.dt, s.c.w);      // S_{i+1} = S_i + dt tau_i
-                const float wgt = T * alpha;          // (1 - A_i) alpha_i
-                P0 = fmaf(wgt, s.c.x, P0);
-                P1 = fmaf(wgt, s.c.y, P1);
-                P2 = fmaf(wgt, s.c.z, P2);
-                if ((i & (kColourBlock - 1)) == kColourBlock - 1) {
-                    C0 += P0; C1 += P1; C2 += P2;
-                    P0 = 0.f; P1 = 0.f; P2 = 0.f;
+                for (int k = 0; k < 4; ++k) last_v[k] = cur.c.vz[k];
+                n1 = n2;
+                fetch_sample_reuse<VT, CB, false>(src, G, q, n1.c.base, n2);      // sample i + 2
+                march_next(m, q);
+                const Cell& c = cur.c;
+                const Density d = cell_density(c);
+                if (MODEL == DVR_EMISSION_ABSORPTION) {
+                    TFSample s;
+                    tf_lookup(tf_s, p.R, d, tfc, s);
+                    const float alpha = sample_alpha(G.dt, s.c.w);
+                    depth_add(sh, sl, G.dt, s.c.w);      // S_{i+1} = S_i + dt tau_i
+                    const float wgt = T * alpha;          // (1 - A_i) alpha_i
+                    P0 = fmaf(wgt, s.c.x, P0);
+                    P1 = fmaf(wgt, s.c.y, P1);
+                    P2 = fmaf(wgt, s.c.z, P2);
+                    T = transmittance(sh, sl);            // 1 - A_{i+1}
+                } else {
+                    depth_add_density(sh, sl, G.dt, d);
                 }
-                T = transmittance(sh, sl);            // 1 - A_{i+1}
-            } else {
-                depth_add_density(sh, sl, G.dt, d);
             }
+            C0 += P0; C1 += P1; C2 += P2;
+            P0 = 0.f; P1 = 0.f; P2 = 0.f;
         }
-        C0 += P0; C1 += P1; C2 += P2;
         if (store) {
             const float A = -expm1f(-(sh + sl));
             if (MODEL == DVR_EMISSION_ABSORPTION)
