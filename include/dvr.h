@@ -77,7 +77,7 @@
 extern "C" {
 #endif
 
-#define DVR_ABI_VERSION 10
+#define DVR_ABI_VERSION 11
 
 /* exported from the shared library (which hides everything else) */
 #if defined(__GNUC__)
@@ -294,15 +294,28 @@ DVR_API const char* dvr_last_error(void);
  *                      (never an out-of-bounds access), repeated ones render
  *                      a tile twice
  * tile_order_len       its length (ignored with NULL)
+ * workspace            device scratch of at least
+ *                      dvr_backward_workspace_bytes(n_views) bytes, 16-byte
+ *                      aligned, owned by the caller, or NULL. With it the
+ *                      launch is persistent: as many blocks as the device
+ *                      holds at once, whose warps take ray tiles from a
+ *                      counter in the workspace (the call zeroes it on
+ *                      `stream`; contents afterwards unspecified) until
+ *                      none are left, so a warp whose rays end early moves
+ *                      on. With NULL every warp renders one tile. The
+ *                      results are the same either way. Two calls in
+ *                      flight at once on different streams need separate
+ *                      workspaces.
+ * workspace_bytes      its size (ignored with NULL)
  * Errors: DVR_ERR_ARG for null/invalid descriptors or sizes (or a
  * tile_order whose length does not match the views' tiles at the current
- * width), DVR_ERR_DTYPE for unsupported dtypes, DVR_ERR_CUDA if the launch
- * fails.
+ * width, or a workspace that is misaligned or too small), DVR_ERR_DTYPE for
+ * unsupported dtypes, DVR_ERR_CUDA if the launch fails.
  */
 DVR_API int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                 const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
                 float* image, float* aux, unsigned long long* sample_count, const uint32_t* tile_order,
-                int64_t tile_order_len, void* stream);
+                int64_t tile_order_len, void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * Tile order for dvr_forward / dvr_backward (host function, no CUDA call).
@@ -410,8 +423,8 @@ DVR_API int dvr_backward_checkpointed(const dvr_volume* volumes, int32_t n_volum
                                       float* grad_step, uint32_t flags, int32_t k, const float* checkpoints,
                                       int32_t slots, void* workspace, size_t workspace_bytes, void* stream);
 
-/* Bytes of device workspace a dvr_backward call over n_views views needs
- * (a multiple of 256; 0 if n_views < 1). */
+/* Bytes of device workspace a dvr_backward call over n_views views needs,
+ * and a persistent dvr_forward call (a multiple of 256; 0 if n_views < 1). */
 DVR_API size_t dvr_backward_workspace_bytes(int32_t n_views);
 
 /*

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 BOUNDS_LIB_PATH = os.path.join(_HERE, "_lib", "libdvr_bounds.so")
 LIB_PATH = os.environ.get("DVR_LIBRARY") or os.path.join(_HERE, "_lib", "libdvr.so")
 
-ABI_VERSION = 10         # DVR_ABI_VERSION of the header these argtypes follow
+ABI_VERSION = 11         # DVR_ABI_VERSION of the header these argtypes follow
 DVR_OK = 0
 DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
 DVR_ABSORPTION, DVR_EMISSION_ABSORPTION, DVR_COLOR_VOLUME = 0, 1, 2
@@ -87,7 +87,7 @@ def load() -> ctypes.CDLL:
         lib.dvr_get_pass_tile_width.argtypes = [I32]
         lib.dvr_get_pass_tile_width.restype = ctypes.c_int
         lib.dvr_last_error.restype = ctypes.c_char_p
-        lib.dvr_forward.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, I64, P]
+        lib.dvr_forward.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, I64, P, ctypes.c_size_t, P]
         lib.dvr_backward.argtypes = [P, I32, P, I32, P, I32, P, F, P, P, P, P, P, P, U32, P, I64, P,
                                      ctypes.c_size_t, P]
         lib.dvr_checkpoint_slots.argtypes = [P, I32, F, I32]

@@ -186,10 +186,13 @@ def checkpoint_slots(scene: "Scene", step_voxels, k: int) -> int:
 
 
 def forward(volumes, tf, model, views, eye, step_voxels, *, scene: Scene | None = None, image=None,
-            aux=None, sample_count=None, stream=None, checkpoints=None):
-    """Alg. 1 for all views in one launch. Returns (image [P][C], aux [P][2]).
+            aux=None, sample_count=None, stream=None, checkpoints=None, workspace=None):
+    """Alg. 1 for all views in one persistent launch (its tile-queue
+    workspace from `workspace`, a uint8 tensor of at least
+    dvr_backward_workspace_bytes(n_views) bytes, or else from torch's
+    caching allocator). Returns (image [P][C], aux [P][2]).
     `checkpoints` = (tensor [P][slots], K): also record the transmittance
-    before every K-th sample (dvr_forward_checkpointed)."""
+    before every K-th sample (dvr_forward_checkpointed, one tile per warp)."""
     sc = scene or Scene.make(volumes, tf, model, views)
     dev = sc.volumes[0].device
     _require_cuda(eye, "eye")
@@ -210,9 +213,10 @@ def forward(volumes, tf, model, views, eye, step_voxels, *, scene: Scene | None 
         return image, aux
     # the forward keeps the fixed tile order: the centre-out order measured no
     # faster on one 512^2 view and 3% slower on 64 uneven views (B300)
+    ws = workspace if workspace is not None else sc.workspace(lib, stream)
     rc = lib.dvr_forward(sc.vol_desc, len(sc.volumes), sc.tf_ref(), sc.model, sc.view_desc,
                          len(sc.views), _ptr(eye), float(step_voxels), _ptr(image), _ptr(aux),
-                         _ptr(sample_count), None, 0, _stream_ptr(stream))
+                         _ptr(sample_count), None, 0, _ptr(ws), ws.numel(), _stream_ptr(stream))
     _abi.check(rc, "dvr_forward")
     return image, aux
 

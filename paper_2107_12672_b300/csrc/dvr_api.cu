@@ -351,7 +351,8 @@ int check_order(const uint32_t* order, long long len, const dvr_view* views, int
 int forward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                  const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
                  float* image, float* aux, unsigned long long* sample_count, const uint32_t* tile_order,
-                 int64_t tile_order_len, float* ckpt, int32_t ck_k, int32_t ck_slots, void* stream)
+                 int64_t tile_order_len, float* ckpt, int32_t ck_k, int32_t ck_slots, void* workspace,
+                 size_t workspace_bytes_, void* stream)
 {
     Common c;
     int rc = check_common(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, c);
@@ -364,12 +365,23 @@ int forward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf,
     if (!image) return fail(DVR_ERR_ARG, "image is NULL");
     if (!aligned(image, c.channels == 4 ? 16 : 4)) return fail(DVR_ERR_ARG, "image is not 16-byte aligned");
     if (aux && !aligned(aux, 8)) return fail(DVR_ERR_ARG, "aux is not 8-byte aligned");
+    if (workspace) {
+        const size_t need = workspace_bytes(n_views);
+        if (workspace_bytes_ < need || !aligned(workspace, 16))
+            return fail(DVR_ERR_ARG, "dvr_forward: workspace %p of %zu bytes (16-byte aligned, %zu needed)",
+                        workspace, workspace_bytes_, need);
+        cudaError_t e0 = cudaMemsetAsync(workspace, 0, need, (cudaStream_t)stream);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "dvr_forward workspace");
+    }
     dvr::Params p;
     long long order_off = 0;
     for (int v0 = 0; v0 < n_views; v0 += dvr::kMaxViewsPerLaunch) {
         const int v1 = v0 + dvr::kMaxViewsPerLaunch < n_views ? v0 + dvr::kMaxViewsPerLaunch : n_views;
         pack(p, tw, volumes, n_volumes, model == DVR_EMISSION_ABSORPTION ? tf : nullptr, views, v0, v1, eye,
              step_voxels);
+        if (workspace)                  // persistent launch: this launch's tile-queue counter
+            p.queue = reinterpret_cast<unsigned*>(static_cast<char*>(workspace)
+                                                  + (size_t)(v0 / dvr::kMaxViewsPerLaunch) * kQueueStride);
         if (tile_order) {
             p.order = tile_order + order_off;
             order_off += p.total_tiles;
@@ -671,11 +683,12 @@ int64_t dvr_tile_order(const dvr_view* views, int32_t n_views, int32_t pass, uin
 int dvr_forward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,
                 const dvr_view* views, int32_t n_views, const float* eye, float step_voxels,
                 float* image, float* aux, unsigned long long* sample_count, const uint32_t* tile_order,
-                int64_t tile_order_len, void* stream)
+                int64_t tile_order_len, void* workspace, size_t workspace_bytes_, void* stream)
 {
     g_err[0] = 0;
     const int rc = forward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, image, aux,
-                                sample_count, tile_order, tile_order_len, nullptr, 0, 0, stream);
+                                sample_count, tile_order, tile_order_len, nullptr, 0, 0, workspace,
+                                workspace_bytes_, stream);
     return rc ? rc : finish(stream, "dvr_forward");
 }
 
@@ -698,7 +711,7 @@ int dvr_forward_checkpointed(const dvr_volume* volumes, int32_t n_volumes, const
                               "dvr_forward_checkpointed");
     if (rc) return rc;
     const int rf = forward_impl(volumes, n_volumes, tf, model, views, n_views, eye, step_voxels, image, aux,
-                                sample_count, nullptr, 0, checkpoints, k, slots, stream);
+                                sample_count, nullptr, 0, checkpoints, k, slots, nullptr, 0, stream);
     return rf ? rf : finish(stream, "dvr_forward_checkpointed");
 }
 int dvr_backward(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf, int32_t model,

@@ -1,5 +1,6 @@
-// Forward pass (Alg. 1): one thread per ray, one warp per 8 x 4 pixel tile,
-// all views of the launch in one grid. For each sample: position, trilinear
+// Forward pass (Alg. 1): one thread per ray, one warp per ray tile (8 x 4
+// pixels by default), all views of the launch in one grid; with a
+// workspace the launch is persistent (warps take tiles from a counter). For each sample: position, trilinear
 // density, TF lookup from shared memory, Beer-Lambert opacity and
 // front-to-back blending (Eq. blend-forward) in registers. The ray's optical
 // depth S = sum dt tau_i is accumulated as an unevaluated float pair and
@@ -8,6 +9,8 @@
 // product of the transmittance before the sample, exp(-S_i), and the
 // sample's opacity; the colour is summed in blocks of 64 samples
 // (sample_alpha and kColourBlock in the device header).
+#include <atomic>
+
 #include "dvr_device.cuh"
 #include "dvr_launch.h"
 
@@ -32,7 +35,11 @@ forward_kernel(const __grid_constant__ Params p)
     const int warp = threadIdx.x >> 5;
     unsigned long long taken = 0;
 
-    for (int rank = blockIdx.x * kWarps + warp; rank < p.total_tiles; rank += gridDim.x * kWarps) {
+    // with a tile queue (p.queue) the launch is persistent and each warp
+    // takes the next tile from it; without, each warp renders its own tile
+    const bool queued = p.queue != nullptr;
+    for (int rank = queued ? next_tile(p.queue, lane) : blockIdx.x * kWarps + warp; rank < p.total_tiles;
+         rank = queued ? next_tile(p.queue, lane) : rank + gridDim.x * kWarps) {
         const int tile = tile_at(p, rank);
         if (tile < 0) continue;                 // warp-uniform
         const int v = find_view(p, tile);
@@ -144,10 +151,25 @@ template <int MODEL, typename VT, bool CKPT = false, int CB = 0>
 static cudaError_t launch(const Params& p, cudaStream_t stream)
 {
     auto k = forward_kernel<MODEL, VT, CKPT, CB>;
-    const int blocks = (p.total_tiles + kWarps - 1) / kWarps;
+    int blocks = (p.total_tiles + kWarps - 1) / kWarps;
     // shared memory holds only this TF, the rest of the SM's 256 KB stays
     // L1 cache for the gathers
     const size_t smem = MODEL == DVR_EMISSION_ABSORPTION ? 2 * sizeof(float4) * (size_t)p.R : 0;
+    if (p.queue) {
+        // persistent: the blocks resident at once (cached per instantiation
+        // and shared-memory size: smem << 8 | blocks per SM)
+        static std::atomic<unsigned long long> occ{0};
+        unsigned long long o = occ.load(std::memory_order_relaxed);
+        if ((o >> 8) != smem || o == 0) {
+            int per_sm = 0;
+            cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWarps * 32, smem);
+            if (err != cudaSuccess) return err;
+            o = (unsigned long long)smem << 8 | (unsigned long long)(per_sm & 0xff);
+            occ.store(o, std::memory_order_relaxed);
+        }
+        const int cap = (int)(o & 0xff) * sm_count();
+        if (cap > 0 && blocks > cap) blocks = cap;
+    }
     k<<<blocks, kWarps * 32, smem, stream>>>(p);
     return cudaGetLastError();
 }

@@ -86,7 +86,8 @@ def test_struct_layout_matches_header(tmp_path):
 
 def _call_forward(vols, nvol, tf, model, views, nviews, eye=1, step=0.5, image=16):
     lib = _abi.load()
-    return lib.dvr_forward(vols, nvol, tf, model, views, nviews, eye, step, image, None, None, None, 0, None)
+    return lib.dvr_forward(vols, nvol, tf, model, views, nviews, eye, step, image, None, None, None, 0, None, 0,
+                           None)
 
 
 def _one_volume(nx=8, dtype=_abi.DVR_F32, data=4096):
@@ -298,8 +299,20 @@ def test_tile_order_is_a_centre_out_permutation():
 def test_forward_refuses_a_tile_order_of_the_wrong_length():
     lib = _abi.load()
     n = lib.dvr_tile_order(_one_view(), 1, _abi.DVR_PASS_FORWARD, None, 0)
-    rc = lib.dvr_forward(_one_volume(), 1, None, 0, _one_view(), 1, 16, 0.5, 16, None, None, 4096, n + 1, None)
+    rc = lib.dvr_forward(_one_volume(), 1, None, 0, _one_view(), 1, 16, 0.5, 16, None, None, 4096, n + 1, None, 0,
+                         None)
     assert rc == -1 and b"tile_order" in lib.dvr_last_error()
+
+
+@pytest.mark.parametrize("workspace,nbytes", [(4096, 255), (4104, 256)])
+def test_forward_refuses_a_bad_workspace(workspace, nbytes):
+    """A persistent forward's workspace must hold the tile-queue counters
+    and be 16-byte aligned; checked before any CUDA call."""
+    lib = _abi.load()
+    assert lib.dvr_backward_workspace_bytes(1) == 256
+    rc = lib.dvr_forward(_one_volume(), 1, None, 0, _one_view(), 1, 16, 0.5, 16, None, None, None, 0, workspace,
+                         nbytes, None)
+    assert rc == -1 and b"workspace" in lib.dvr_last_error()
 
 
 def test_checkpoint_slots_and_argument_errors():

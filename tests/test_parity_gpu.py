@@ -627,10 +627,12 @@ def test_bandwidth_probes_run_and_count():
 # ------------------------------------------------------------ tile order
 @pytest.mark.parametrize("width", [1, 8, 32])
 def test_tile_order_changes_nothing(width):
-    """With the centre-out tile order of dvr_tile_order, dvr_forward writes
-    every pixel of a NaN-filled image, counts the same samples (a tile taken
-    twice would count twice) and gives the same bits as the fixed order; the
-    adjoint's gradients agree up to the order of atomic additions."""
+    """With the centre-out tile order of dvr_tile_order and a persistent
+    launch (warps taking tiles from the workspace's queue), dvr_forward
+    writes every pixel of a NaN-filled image, counts the same samples (a
+    tile taken twice would count twice) and gives the same bits as the fixed
+    order with one tile per warp; the adjoint's gradients agree up to the
+    order of atomic additions."""
     import ctypes
     from paper_2107_12672_b300 import _abi, autotune
     w = syn.workload("ea_256", scale=0.125)
@@ -645,13 +647,16 @@ def test_tile_order_changes_nothing(width):
     try:
         autotune.set_tile_width(width)
         for use_order in (False, True):
+            # the second pass also runs the forward persistent (tile queue)
             order, n = sc.tile_order(lib, adjoint=False) if use_order else (None, 0)
+            wsf = sc.workspace(lib) if use_order else None
             img = torch.full((sc.pixels, 4), float("nan"), device="cuda")
             aux = torch.full((sc.pixels, 2), float("nan"), device="cuda")
             count = torch.zeros(1, dtype=torch.int64, device="cuda")
             rc = lib.dvr_forward(sc.vol_desc, 1, sc.tf_ref(), sc.model, sc.view_desc, len(views), eye.data_ptr(),
                                  ctypes.c_float(w.step_voxels), img.data_ptr(), aux.data_ptr(), count.data_ptr(),
-                                 None if order is None else order.data_ptr(), n, stream)
+                                 None if order is None else order.data_ptr(), n,
+                                 None if wsf is None else wsf.data_ptr(), 0 if wsf is None else wsf.numel(), stream)
             _abi.check(rc, "dvr_forward")
             G = to_dev(seeded_grad_image(sc.pixels, 4, 3))
             ordered, n_b = sc.tile_order(lib, adjoint=True) if use_order else (None, 0)
