@@ -132,6 +132,40 @@ def test_multiview_uneven_one_launch():
     _compare(w, gpu, ref, want)
 
 
+def test_persistent_forward_over_several_launches():
+    """More views than one launch takes (600 > 512: two launches, each with
+    its own tile-queue counter in the workspace): the persistent forward
+    writes every pixel of a NaN-filled image with the bits of the launch
+    with one tile per warp, and counts the same samples; with the cell
+    layout in 4^3 bricks as well."""
+    import ctypes
+    from paper_2107_12672_b300 import _abi
+    w = syn.workload("ea_256", scale=0.0625)
+    vol, tf = to_dev(w.volumes[0], torch.float16), to_dev(w.tf)
+    sizes = [(1 + k % 9, 1 + (k * 7) % 11) for k in range(600)]
+    views = [syn.View(a, b) for a, b in sizes]
+    eye = to_dev(2.3 * syn.fibonacci_sphere(len(views)))
+    lib = _abi.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    for cells in (None, [dvr.make_cells(vol, brick=4)]):
+        sc = dvr.Scene.make([vol], tf, w.model, views, cells=cells, cells_brick=4)
+        out = []
+        for ws in (None, sc.workspace(lib)):
+            img = torch.full((sc.pixels, 4), float("nan"), device="cuda")
+            aux = torch.full((sc.pixels, 2), float("nan"), device="cuda")
+            count = torch.zeros(1, dtype=torch.int64, device="cuda")
+            rc = lib.dvr_forward(sc.vol_desc, 1, sc.tf_ref(), sc.model, sc.view_desc, len(views), eye.data_ptr(),
+                                 ctypes.c_float(w.step_voxels), img.data_ptr(), aux.data_ptr(), count.data_ptr(),
+                                 None, 0, None if ws is None else ws.data_ptr(), 0 if ws is None else ws.numel(),
+                                 stream)
+            _abi.check(rc, "dvr_forward")
+            torch.cuda.synchronize()
+            out.append((img, aux, int(count.item())))
+        assert not torch.isnan(out[1][0]).any() and not torch.isnan(out[1][1]).any()
+        assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+        assert out[0][2] == out[1][2] > 0
+
+
 @pytest.mark.parametrize("vdt,tdt", [(torch.bfloat16, torch.float16), (torch.float16, torch.float32)])
 def test_reduced_precision_storage(vdt, tdt):
     """BF16/FP16 volume and FP16 TF storage with FP32 arithmetic: the oracle
