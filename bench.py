@@ -87,9 +87,9 @@ def parse():
     ap.add_argument("--image", type=int, default=0, help="render every view at S x S pixels (smaller case)")
     ap.add_argument("--grid", type=int, default=0,
                     help="the 1024^3 workload's volume at N^3 vertices instead (smaller case, same generator)")
-    ap.add_argument("--cells", type=int, default=-1, choices=(-1, 0, 1, 4),
+    ap.add_argument("--cells", type=int, default=-1, choices=(-1, 0, 1, 4, 8),
                     help="gather from the volumes' arrays (0) or cell layouts with records in row order (1) or "
-                         "bricks of 4^3 cells (4), remade inside every step (default: autotuned)")
+                         "bricks of 4^3 or 8^3 cells (4, 8), remade inside every step (default: autotuned)")
     ap.add_argument("--cell-gradient", type=int, default=-1, choices=(-1, 0, 1),
                     help="accumulate the volume gradient per cell first (DVR_FLAG_CELL_GRADIENT) or not "
                          "(default: autotuned)")
@@ -791,7 +791,7 @@ def run_ours(args):
             teye, tnote = wl.eye[:4].contiguous(), "first 4 views"
         tuning = autotune.autotune(tscene, teye, wl.w.step_voxels, want=wl.want, l2_flush=flush,
                                    reps=1 if probe_ms > 1000.0 else 5,
-                                   layouts=(0, 1, 4) if args.cells < 0 else (args.cells,),
+                                   layouts=(0, 1, 4, 8) if args.cells < 0 else (args.cells,),
                                    cell_gradients=(False, True) if args.cell_gradient < 0 else (bool(args.cell_gradient),))
         tuning["tuned_on"] = tnote
         if tuning["cells"] != wl.use_cells or tuning["cell_gradient"] != wl.cell_gradient:

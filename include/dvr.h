@@ -77,7 +77,7 @@
 extern "C" {
 #endif
 
-#define DVR_ABI_VERSION 11
+#define DVR_ABI_VERSION 12
 
 /* exported from the shared library (which hides everything else) */
 #if defined(__GNUC__)
@@ -156,7 +156,7 @@ typedef struct {
     int32_t dtype;           /* DVR_F32, DVR_F16 or DVR_BF16 */
     const void* data;
     const void* cells;       /* NULL, or the cell layout of `data` */
-    int32_t cells_brick;     /* record order of `cells` (and of the cell-major gradient): 0 or 1, 4 */
+    int32_t cells_brick;     /* record order of `cells` (and of the cell-major gradient): 0 or 1, 4, 8 */
     int32_t reserved;
 } dvr_volume;
 
@@ -170,13 +170,14 @@ typedef struct {
  * for DVR_F32, 8 times the bytes of the volume. Each value is copied bit for
  * bit. The record index r of cell (i, j, k) follows vol->cells_brick:
  *   0 or 1: row order, r = i + (nx - 1) (j + (ny - 1) k);
- *   4: bricks of 4 x 4 x 4 cells, r = 64 (bi + bx (bj + by bk)) + (i & 3)
- *      + 4 (j & 3) + 16 (k & 3) with (bi, bj, bk) = (i, j, k) / 4 and
- *      bx = ceil((nx - 1) / 4), by = ceil((ny - 1) / 4); the records of
+ *   B = 4 or 8: bricks of B x B x B cells,
+ *      r = B^3 (bi + bx (bj + by bk)) + (i % B) + B (j % B) + B^2 (k % B)
+ *      with (bi, bj, bk) = (i, j, k) / B (integer division) and
+ *      bx = ceil((nx - 1) / B), by = ceil((ny - 1) / B); the records of
  *      brick positions beyond the cells are left as they are.
- * The brick order keeps the cells around a ray's position within 2 KB of
- * each other instead of rows (nx - 1) records apart; the autotuner picks
- * the order.
+ * The brick order keeps the cells around a ray's position close together
+ * (within 2 KB for B = 4) instead of rows (nx - 1) records apart; the
+ * autotuner picks the order (the brick edge).
  *
  * dvr_cells_bytes: the bytes of the layout of `vol` in its order (0 for
  *   invalid dimensions, dtype or order).

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 BOUNDS_LIB_PATH = os.path.join(_HERE, "_lib", "libdvr_bounds.so")
 LIB_PATH = os.environ.get("DVR_LIBRARY") or os.path.join(_HERE, "_lib", "libdvr.so")
 
-ABI_VERSION = 11         # DVR_ABI_VERSION of the header these argtypes follow
+ABI_VERSION = 12         # DVR_ABI_VERSION of the header these argtypes follow
 DVR_OK = 0
 DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
 DVR_ABSORPTION, DVR_EMISSION_ABSORPTION, DVR_COLOR_VOLUME = 0, 1, 2

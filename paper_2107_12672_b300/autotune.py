@@ -54,9 +54,9 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
              layouts=(0,), cell_gradients=(False,)) -> dict:
     """Time the forward and the adjoint pass for each tile width (two
     interleaved rounds, the faster of the two kept) and each gather layout
-    in `layouts` (0: the volume's array; 1 / 4: its cell layout with records
-    in row order / in bricks of 4^3 cells, built before each forward and
-    timed with it) and, for the adjoint of a volume
+    in `layouts` (0: the volume's array; 1 / 4 / 8: its cell layout with
+    records in row order / in bricks of 4^3 / 8^3 cells, so the brick edge,
+    built before each forward and timed with it) and, for the adjoint of a volume
     gradient, each scatter in `cell_gradients`; set the fastest width of
     each pass and return {"width", "adjoint_width", "cells",
     "cell_gradient", "ms": {...}}. The layout is chosen by forward + adjoint

@@ -158,7 +158,8 @@ def make_cells(volume: torch.Tensor, out: torch.Tensor | None = None, stream=Non
     """The cell layout of `volume` (dvr_make_cells): per cell its 8 corner
     values, 8x the volume's bytes, as a flat tensor of the volume's dtype
     (written into `out` if given), records in row order (brick 1) or in
-    bricks of 4^3 cells (brick 4). Remake it whenever the volume changes."""
+    bricks of 4^3 or 8^3 cells (brick 4 or 8). Remake it whenever the volume
+    changes."""
     _require_cuda(volume, "volume")
     if volume.dim() != 3 or volume.dtype not in _DTYPES:
         raise ValueError("cell layout: a 3-D float32/float16/bfloat16 volume")

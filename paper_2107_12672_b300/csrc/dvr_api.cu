@@ -162,19 +162,20 @@ size_t workspace_bytes(int n_views)
     return (launches * kQueueStride + 255) / 256 * 256;
 }
 
-// Record order of a volume's cell layout: 1 (row order) or 4 (bricks), or
-// 0 if invalid.
+// Record order of a volume's cell layout: 1 (row order), 4 or 8 (bricks
+// of 4^3 or 8^3 cells), or 0 if invalid.
 int cells_order(const dvr_volume& v)
 {
-    return v.cells_brick == 0 || v.cells_brick == 1 ? 1 : (v.cells_brick == 4 ? 4 : 0);
+    return v.cells_brick == 0 || v.cells_brick == 1 ? 1 : (v.cells_brick == 4 || v.cells_brick == 8 ? v.cells_brick : 0);
 }
 
 // Records of the cell layout (and of the cell-major gradient) of a volume
-// in the order `brick`: the cells, or whole bricks of 4^3 cells.
+// in the order `brick`: the cells, or whole bricks of brick^3 cells.
 size_t cell_records(const dvr_volume& v, int brick)
 {
-    if (brick == 4)
-        return (size_t)((v.nx - 1 + 3) / 4) * (size_t)((v.ny - 1 + 3) / 4) * (size_t)((v.nz - 1 + 3) / 4) * 64;
+    if (brick == 4 || brick == 8)
+        return (size_t)((v.nx - 1 + brick - 1) / brick) * (size_t)((v.ny - 1 + brick - 1) / brick) *
+               (size_t)((v.nz - 1 + brick - 1) / brick) * (size_t)(brick * brick * brick);
     return (size_t)(v.nx - 1) * (size_t)(v.ny - 1) * (size_t)(v.nz - 1);
 }
 
@@ -233,7 +234,7 @@ int check_common(const dvr_volume* vols, int nvol, const dvr_tf* tf, int model, 
         if ((v.cells != nullptr) != (vols[0].cells != nullptr))
             return fail(DVR_ERR_ARG, "volume %d: either every volume of a call has its cell layout or none", i);
         if (v.reserved != 0) return fail(DVR_ERR_ARG, "volume %d: reserved field must be 0", i);
-        if (!cells_order(v)) return fail(DVR_ERR_ARG, "volume %d: cells_brick %d is not 0, 1 or 4", i, v.cells_brick);
+        if (!cells_order(v)) return fail(DVR_ERR_ARG, "volume %d: cells_brick %d is not 0, 1, 4 or 8", i, v.cells_brick);
         if (v.cells && cells_order(v) != cells_order(vols[0]))
             return fail(DVR_ERR_ARG, "volume %d: the cell layouts of one call must share their record order", i);
     }
@@ -626,7 +627,7 @@ int dvr_make_cells(const dvr_volume* vol, void* cells, size_t cells_bytes, void*
         return fail(DVR_ERR_ARG, "dvr_make_cells: dimensions %d x %d x %d invalid", vol->nx, vol->ny, vol->nz);
     const size_t esz = vol->dtype == DVR_F32 ? 4 : 2;
     if (!vol->data || !aligned(vol->data, esz)) return fail(DVR_ERR_ARG, "dvr_make_cells: data NULL or misaligned");
-    if (!cells_order(*vol)) return fail(DVR_ERR_ARG, "dvr_make_cells: cells_brick %d is not 0, 1 or 4", vol->cells_brick);
+    if (!cells_order(*vol)) return fail(DVR_ERR_ARG, "dvr_make_cells: cells_brick %d is not 0, 1, 4 or 8", vol->cells_brick);
     const size_t need = dvr_cells_bytes(vol);
     if (!cells || !aligned(cells, 16) || cells_bytes < need)
         return fail(DVR_ERR_ARG, "dvr_make_cells: cells %p of %zu bytes (16-byte aligned, %zu needed)", cells,

@@ -39,10 +39,13 @@ cudaError_t launch_backward(const Params& p, int model, int vol_dtype, bool grad
 {
     // with the cell layout (every volume of the launch has one), except for
     // the inversion ablations, which read the volume's array
-    if (p.vol[0].cells && inv_mode == kInvDepth)
-        return p.vol[0].cells_brick == 4
-                   ? launch_backward_cells4(p, model, vol_dtype, grad_volume, tf_mode, grad_position, stream)
-                   : launch_backward_cells(p, model, vol_dtype, grad_volume, tf_mode, grad_position, stream);
+    if (p.vol[0].cells && inv_mode == kInvDepth) {
+        if (p.vol[0].cells_brick == 8)
+            return launch_backward_cells8(p, model, vol_dtype, grad_volume, tf_mode, grad_position, stream);
+        if (p.vol[0].cells_brick == 4)
+            return launch_backward_cells4(p, model, vol_dtype, grad_volume, tf_mode, grad_position, stream);
+        return launch_backward_cells(p, model, vol_dtype, grad_volume, tf_mode, grad_position, stream);
+    }
     return launch_backward_source<0>(p, model, vol_dtype, grad_volume, tf_mode, grad_position, inv_mode, stream);
 }
 

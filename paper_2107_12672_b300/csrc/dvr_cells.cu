@@ -17,12 +17,12 @@ make_cells_kernel(const VT* __restrict__ v, int nx, int ny, int nz, VT* __restri
     const long long ncx = nx - 1, ncy = ny - 1, total = ncx * ncy * (long long)(nz - 1);
     const long long sy = nx, sz = (long long)nx * ny;
     const int n[3] = {nx, ny, nz};
-    const uint32_t nb4[2] = {(uint32_t)(nx - 1 + 3) >> 2, (uint32_t)(ny - 1 + 3) >> 2};
+    const uint32_t nb[2] = {(uint32_t)(nx - 1 + CB - 1) / CB, (uint32_t)(ny - 1 + CB - 1) / CB};
     for (long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; c0 < total;
          c0 += (long long)gridDim.x * blockDim.x) {
         const long long i = c0 % ncx, t = c0 / ncx, j = t % ncy, k = t / ncy;
         const long long b = i + sy * j + sz * k;
-        const long long c = cell_index<CB>(n, nb4, (uint32_t)i, (uint32_t)j, (uint32_t)k);
+        const long long c = cell_index<CB>(n, nb, (uint32_t)i, (uint32_t)j, (uint32_t)k);
         if (!in_bounds<kSiteCells>(c, cell_records<CB>(n)) || !in_bounds<kSiteVolume>(b + sy + 1 + sz, sz * nz))
             continue;
         const VT w[8] = {v[b], v[b + sz], v[b + 1], v[b + 1 + sz],
@@ -70,8 +70,9 @@ cudaError_t launch_make_cells(const void* data, int dtype, int nx, int ny, int n
     const long long cap = 8ll * sm_count();
     if (cap > 0 && blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    return brick == 4 ? make_cells_order<4>(data, dtype, nx, ny, nz, cells, (unsigned)blocks, stream)
-                      : make_cells_order<1>(data, dtype, nx, ny, nz, cells, (unsigned)blocks, stream);
+    if (brick == 8) return make_cells_order<8>(data, dtype, nx, ny, nz, cells, (unsigned)blocks, stream);
+    if (brick == 4) return make_cells_order<4>(data, dtype, nx, ny, nz, cells, (unsigned)blocks, stream);
+    return make_cells_order<1>(data, dtype, nx, ny, nz, cells, (unsigned)blocks, stream);
 }
 
 // grad[v] += the records of the (up to 8) cells that have vertex v as a
@@ -85,7 +86,7 @@ cells_to_vertices_kernel(const float* __restrict__ cg, int nx, int ny, int nz, f
 {
     const long long total = (long long)nx * ny * nz;
     const int n[3] = {nx, ny, nz};
-    const uint32_t nb4[2] = {(uint32_t)(nx - 1 + 3) >> 2, (uint32_t)(ny - 1 + 3) >> 2};
+    const uint32_t nb[2] = {(uint32_t)(nx - 1 + CB - 1) / CB, (uint32_t)(ny - 1 + CB - 1) / CB};
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < total;
          v += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(v % nx);
@@ -100,7 +101,7 @@ cells_to_vertices_kernel(const float* __restrict__ cg, int nx, int ny, int nz, f
                 for (int dx = 0; dx < 2; ++dx) {
                     const int i = x - dx, j = y - dy, k = z - dz;
                     if (i < 0 || j < 0 || k < 0 || i >= nx - 1 || j >= ny - 1 || k >= nz - 1) continue;
-                    const long long cell = cell_index<CB>(n, nb4, (uint32_t)i, (uint32_t)j, (uint32_t)k);
+                    const long long cell = cell_index<CB>(n, nb, (uint32_t)i, (uint32_t)j, (uint32_t)k);
                     if (!in_bounds<kSiteCellGradient>(cell, cell_records<CB>(n))) continue;
                     s += __ldg(cg + 8 * cell + dx + 2 * dy + 4 * dz);
                 }
@@ -116,7 +117,9 @@ cudaError_t launch_cells_to_vertices(const float* cg, int nx, int ny, int nz, in
     const long long cap = 8ll * sm_count();
     if (cap > 0 && blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    if (brick == 4)
+    if (brick == 8)
+        cells_to_vertices_kernel<8><<<(unsigned)blocks, 256, 0, stream>>>(cg, nx, ny, nz, grad);
+    else if (brick == 4)
         cells_to_vertices_kernel<4><<<(unsigned)blocks, 256, 0, stream>>>(cg, nx, ny, nz, grad);
     else
         cells_to_vertices_kernel<1><<<(unsigned)blocks, 256, 0, stream>>>(cg, nx, ny, nz, grad);

@@ -58,7 +58,7 @@ constexpr int kFixBits = 40;         // fraction bits of a fixed-point sample po
 struct VolumeDesc {
     const void* data;
     const void* cells;               // the cell layout of data (dvr_make_cells), or null
-    int cells_brick;                 // order of its records: 1 (row order) or 4 (bricks of 4^3 cells)
+    int cells_brick;                 // order of its records: 1 (row order), 4 or 8 (bricks of 4^3, 8^3 cells)
     float* grad;                     // adjoint only, may be null
     float* cgrad;                    // cell-major gradient ([cells][8]) the adjoint adds into instead, or null
     int n[3];
@@ -265,7 +265,7 @@ struct Grid {
     float inv_h;                     // max(n) - 1
     int n[3];
     int top[3];                      // (n - 1) in the high word of a fixed-point position
-    uint32_t nb4[2];                 // bricks of 4^3 cells along x and y (the brick order of cell records)
+    uint32_t nb4[2], nb8[2];         // bricks of 4^3 and 8^3 cells along x and y (brick-ordered cell records)
 };
 
 __device__ __forceinline__ void make_grid(const VolumeDesc& v, float step, Grid& g)
@@ -277,7 +277,10 @@ __device__ __forceinline__ void make_grid(const VolumeDesc& v, float step, Grid&
     for (int a = 0; a < 3; ++a) {
         g.n[a] = v.n[a];
         g.top[a] = (v.n[a] - 1) << (kFixBits - 32);
-        if (a < 2) g.nb4[a] = (uint32_t)(v.n[a] - 1 + 3) >> 2;
+        if (a < 2) {
+            g.nb4[a] = (uint32_t)(v.n[a] - 1 + 3) >> 2;
+            g.nb8[a] = (uint32_t)(v.n[a] - 1 + 7) >> 3;
+        }
         g.half[a] = __fmul_rn(__fdiv_rn((float)(v.n[a] - 1), den), 0.5f);
     }
 }
@@ -507,26 +510,36 @@ static __device__ __noinline__ AxisClamp clamp_axis(long long q, int n)
 }
 
 // Index of cell (i, j, k) in the records of the cell layout: row order
-// (CB <= 1: x fastest), or bricks of 4 x 4 x 4 cells, bricks in row order
-// and cells in row order within a brick (CB = 4: the 8 cells around a ray's
-// position share 2 KB of 16-byte records instead of rows 16 KB apart).
+// (CB <= 1: x fastest), or bricks of CB x CB x CB cells (CB = 4 or 8),
+// bricks in row order (nb[0] x nb[1] of them per layer) and cells in row
+// order within a brick (CB = 4: the 8 cells around a ray's position share
+// 2 KB of 16-byte records instead of rows 16 KB apart).
 template <int CB>
-__host__ __device__ __forceinline__ uint32_t cell_index(const int n[3], const uint32_t nb4[2], uint32_t i,
+__host__ __device__ __forceinline__ uint32_t cell_index(const int n[3], const uint32_t nb[2], uint32_t i,
                                                         uint32_t j, uint32_t k)
 {
-    if constexpr (CB == 4)
-        return ((((k >> 2) * nb4[1] + (j >> 2)) * nb4[0] + (i >> 2)) << 6) | ((k & 3u) << 4) | ((j & 3u) << 2) |
-               (i & 3u);
-    else
+    if constexpr (CB == 4 || CB == 8) {
+        constexpr uint32_t S = CB == 8 ? 3u : 2u, M = CB - 1u;
+        return ((((k >> S) * nb[1] + (j >> S)) * nb[0] + (i >> S)) << (3u * S)) | ((k & M) << (2u * S)) |
+               ((j & M) << S) | (i & M);
+    } else {
         return i + (uint32_t)(n[0] - 1) * (j + (uint32_t)(n[1] - 1) * k);
+    }
+}
+
+// Bricks along x and y of the grid G for the record order CB.
+template <int CB>
+__device__ __forceinline__ const uint32_t* grid_bricks(const Grid& G)
+{
+    return CB == 8 ? G.nb8 : G.nb4;
 }
 
 // Number of records of the cell layout (bricks padded to whole bricks).
 template <int CB>
 __host__ __device__ __forceinline__ long long cell_records(const int n[3])
 {
-    if constexpr (CB == 4)
-        return (long long)((n[0] + 2) >> 2) * ((n[1] + 2) >> 2) * ((n[2] + 2) >> 2) * 64;
+    if constexpr (CB == 4 || CB == 8)
+        return (long long)((n[0] + CB - 2) / CB) * ((n[1] + CB - 2) / CB) * ((n[2] + CB - 2) / CB) * CB * CB * CB;
     else
         return (long long)(n[0] - 1) * (n[1] - 1) * (n[2] - 1);
 }
@@ -556,7 +569,7 @@ __device__ __forceinline__ void cell_locate(const Grid& G, const long long q[3],
     }
     c.fx = fr[0]; c.fy = fr[1]; c.fz = fr[2];
     c.base = (uint32_t)j[0] + (uint32_t)G.n[0] * ((uint32_t)j[1] + (uint32_t)G.n[1] * (uint32_t)j[2]);
-    c.cell = cell_index<CB>(G.n, G.nb4, (uint32_t)j[0], (uint32_t)j[1], (uint32_t)j[2]);
+    c.cell = cell_index<CB>(G.n, grid_bricks<CB>(G), (uint32_t)j[0], (uint32_t)j[1], (uint32_t)j[2]);
 #ifdef DVR_DEBUG_BOUNDS
     // corner (1, 1, 1) is the cell's last value; a record (or the cell-major
     // gradient's pair of float4) per cell, bricks padded to whole bricks

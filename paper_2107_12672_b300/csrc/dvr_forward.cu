@@ -200,6 +200,7 @@ cudaError_t launch_forward(const Params& p, int model, int vol_dtype, cudaStream
         return launch<DVR_EMISSION_ABSORPTION, float, true>(p, stream);
     }
     if (p.vol[0].cells) {                   // every volume of the launch has its cell layout, one order
+        if (p.vol[0].cells_brick == 8) return launch_cells<8>(p, model, vol_dtype, stream);
         if (p.vol[0].cells_brick == 4) return launch_cells<4>(p, model, vol_dtype, stream);
         return launch_cells<1>(p, model, vol_dtype, stream);
     }

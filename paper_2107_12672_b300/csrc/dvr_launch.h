@@ -29,6 +29,8 @@ cudaError_t launch_backward_cells(const Params& p, int model, int vol_dtype, boo
                                   bool grad_position, cudaStream_t stream);
 cudaError_t launch_backward_cells4(const Params& p, int model, int vol_dtype, bool grad_volume, int tf_mode,
                                    bool grad_position, cudaStream_t stream);
+cudaError_t launch_backward_cells8(const Params& p, int model, int vol_dtype, bool grad_volume, int tf_mode,
+                                   bool grad_position, cudaStream_t stream);
 cudaError_t launch_make_cells(const void* data, int dtype, int nx, int ny, int nz, int brick, void* cells,
                               cudaStream_t stream);
 cudaError_t launch_cells_to_vertices(const float* cg, int nx, int ny, int nz, int brick, float* grad,

@@ -256,7 +256,9 @@ static cudaError_t launch_t(const Params& p, float* tangent, cudaStream_t s)
 {
     const size_t smem = MODEL == DVR_EMISSION_ABSORPTION ? 2 * sizeof(float4) * (size_t)p.R : 0;
     const dim3 grid((p.total_tiles + kWarps - 1) / kWarps);
-    if (p.vol[0].cells && p.vol[0].cells_brick == 4)
+    if (p.vol[0].cells && p.vol[0].cells_brick == 8)
+        tangent_kernel<MODEL, VT, 8><<<grid, kWarps * 32, smem, s>>>(p, tangent);
+    else if (p.vol[0].cells && p.vol[0].cells_brick == 4)
         tangent_kernel<MODEL, VT, 4><<<grid, kWarps * 32, smem, s>>>(p, tangent);
     else if (p.vol[0].cells)
         tangent_kernel<MODEL, VT, 1><<<grid, kWarps * 32, smem, s>>>(p, tangent);

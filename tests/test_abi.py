@@ -164,7 +164,7 @@ def test_argument_errors_need_no_gpu(case, code):
         rc = _call_forward(two, 2, None, 0, view, 1)
     elif case == "bad_cells_brick":
         vols[0].cells = 8192
-        vols[0].cells_brick = 8
+        vols[0].cells_brick = 2
         rc = _call_forward(vols, 1, None, 0, view, 1)
     assert rc == code
     assert lib.dvr_last_error().decode()
@@ -359,6 +359,11 @@ def test_cell_layout_size_and_argument_errors():
     # bricks of 4^3 cells: whole bricks (4 x 5 x 6 cells -> 1 x 2 x 2 bricks)
     v4 = _abi.DvrVolume(5, 6, 7, _abi.DVR_BF16, 4096, None, 4, 0)
     assert lib.dvr_cells_bytes(ctypes.byref(v4)) == 1 * 2 * 2 * 64 * 8 * 2
+    # bricks of 8^3 cells: 4 x 5 x 6 cells -> one brick of 512; 9 x 5 x 17 -> 2 x 1 x 3
+    v8 = _abi.DvrVolume(5, 6, 7, _abi.DVR_F32, 4096, None, 8, 0)
+    assert lib.dvr_cells_bytes(ctypes.byref(v8)) == 512 * 8 * 4
+    v8b = _abi.DvrVolume(10, 6, 18, _abi.DVR_F16, 4096, None, 8, 0)
+    assert lib.dvr_cells_bytes(ctypes.byref(v8b)) == 2 * 1 * 3 * 512 * 8 * 2
     assert lib.dvr_cells_bytes(ctypes.byref(_abi.DvrVolume(5, 6, 7, _abi.DVR_BF16, 4096, None, 2, 0))) == 0
     assert lib.dvr_make_cells(ctypes.byref(v), 8192, 100, None) == _abi.DVR_OK - 1
     assert lib.dvr_make_cells(ctypes.byref(v), 8200, 1 << 20, None) == _abi.DVR_OK - 1

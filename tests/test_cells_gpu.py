@@ -22,14 +22,14 @@ def _bits(t):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("brick", [1, 4])
+@pytest.mark.parametrize("brick", [1, 4, 8])
 def test_cell_layout_contents(dtype, brick):
     """Cell (i, j, k) holds V(i,j,k), V(i,j,k+1), V(i+1,j,k), V(i+1,j,k+1),
     V(i,j+1,k), V(i,j+1,k+1), V(i+1,j+1,k), V(i+1,j+1,k+1), bit for bit, at
-    record i + (nx-1)(j + (ny-1)k) (row order) or 64 (bi + bx (bj + by bk))
-    + (i & 3) + 4 (j & 3) + 16 (k & 3) (bricks of 4^3 cells, (bi, bj, bk) =
-    (i, j, k) / 4), on a box with three different sizes that are no
-    multiples of 4."""
+    record i + (nx-1)(j + (ny-1)k) (row order) or B^3 (bi + bx (bj + by bk))
+    + (i % B) + B (j % B) + B^2 (k % B) (bricks of B^3 cells, B = 4 or 8,
+    (bi, bj, bk) = (i, j, k) / B), on a box with three different sizes that
+    are no multiples of 4 or 8 (one size above 8)."""
     v = to_dev(np.random.default_rng(1).normal(size=(7, 6, 11)).astype(np.float32), dtype)
     c = dvr.make_cells(v, brick=brick).view(-1, 8)
     ref = torch.stack([v[:-1, :-1, :-1], v[1:, :-1, :-1], v[:-1, :-1, 1:], v[1:, :-1, 1:],
@@ -39,9 +39,10 @@ def test_cell_layout_contents(dtype, brick):
     if brick == 1:
         rec = i + nx * (j + ny * k)
     else:
-        bx, by = (nx + 3) // 4, (ny + 3) // 4
-        rec = 64 * (i // 4 + bx * (j // 4 + by * (k // 4))) + (i % 4) + 4 * (j % 4) + 16 * (k % 4)
-        assert c.shape[0] == bx * by * ((nz + 3) // 4) * 64
+        B = brick
+        bx, by = (nx + B - 1) // B, (ny + B - 1) // B
+        rec = B ** 3 * (i // B + bx * (j // B + by * (k // B))) + (i % B) + B * (j % B) + B * B * (k % B)
+        assert c.shape[0] == bx * by * ((nz + B - 1) // B) * B ** 3
     got = c[rec.reshape(-1).to(c.device)]
     assert torch.equal(_bits(got.contiguous()), _bits(ref.reshape(-1, 8).contiguous()))
 
@@ -58,7 +59,7 @@ def _march(w, vols, tf, cells, G, want, brick=1):
 
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("model", ["emission_absorption", "absorption"])
-@pytest.mark.parametrize("brick", [1, 4])
+@pytest.mark.parametrize("brick", [1, 4, 8])
 def test_cells_equal_linear(dtype, model, brick):
     """Forward and adjoint (volume, TF and eye gradients) of several views of
     uneven sizes over two non-cubic volumes, ragged tiles included, with and
@@ -92,7 +93,8 @@ def test_cells_forward_tangent_bit_identical():
     tf = to_dev(w.tf)
     eye = to_dev(w.eye)
     out = []
-    for brick, cells in ((1, None), (1, [dvr.make_cells(vol)]), (4, [dvr.make_cells(vol, brick=4)])):
+    for brick, cells in ((1, None), (1, [dvr.make_cells(vol)]), (4, [dvr.make_cells(vol, brick=4)]),
+                         (8, [dvr.make_cells(vol, brick=8)])):
         sc = dvr.Scene.make([vol], tf, w.model, w.views, cells=cells, cells_brick=brick)
         img, tan = dvr.forward_tangent(None, None, None, None, eye, w.step_voxels, scene=sc)
         torch.cuda.synchronize()
@@ -135,7 +137,8 @@ def test_cell_gradient_equals_vertex_scatter(dtype, model):
     nc = 4 if model == "emission_absorption" else 1
     G = to_dev(seeded_grad_image(sum(v.width * v.height for v in views), nc, 9))
     want = ("volume", "tf", "eye") if tf is not None else ("volume", "eye")
-    for brick, cells in ((1, None), (1, [dvr.make_cells(v) for v in vols]), (4, [dvr.make_cells(v, brick=4) for v in vols])):
+    for brick, cells in ((1, None), (1, [dvr.make_cells(v) for v in vols]),
+                         (4, [dvr.make_cells(v, brick=4) for v in vols]), (8, [dvr.make_cells(v, brick=8) for v in vols])):
         sc = dvr.Scene.make(vols, tf, model, views, cells=cells, cells_brick=brick)
         _, aux = dvr.forward(None, None, None, None, eye, 0.4, scene=sc)
         a = dvr.backward(None, None, None, None, eye, 0.4, aux, G, scene=sc, want=want)

@@ -539,11 +539,11 @@ def test_tile_width_changes_nothing_and_autotuner_picks_one():
         # with the gather layout and the scatter among the choices (volume gradient)
         autotune._cache.clear()
         res = autotune.autotune(sc, eye, w.step_voxels, want=("volume", "tf", "eye"), reps=1,
-                                candidates=(8, 16), layouts=(0, 1, 4), cell_gradients=(False, True))
-        assert {f"forward|cells={c}" for c in (0, 1, 4)} | \
-            {f"adjoint|cells={c}|cell_gradient={g}" for c in (0, 1, 4) for g in (0, 1)} == set(res["ms"])
+                                candidates=(8, 16), layouts=(0, 1, 4, 8), cell_gradients=(False, True))
+        assert {f"forward|cells={c}" for c in (0, 1, 4, 8)} | \
+            {f"adjoint|cells={c}|cell_gradient={g}" for c in (0, 1, 4, 8) for g in (0, 1)} == set(res["ms"])
         assert res["width"] in (8, 16) and res["adjoint_width"] in (8, 16)
-        assert res["cells"] in (0, 1, 4) and isinstance(res["cell_gradient"], bool)
+        assert res["cells"] in (0, 1, 4, 8) and isinstance(res["cell_gradient"], bool)
     finally:
         autotune.set_tile_width(old, old_adj)
 
