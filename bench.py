@@ -109,7 +109,8 @@ def peaks():
 # shared device header and the launch declarations)
 KERNEL_SOURCES = {"forward": ("dvr_forward.cu", "dvr_device.cuh", "dvr_launch.h"),
                   "backward": ("dvr_backward.cu", "dvr_backward.cuh", "dvr_backward_cells.cu",
-                               "dvr_backward_cells4.cu", "dvr_device.cuh", "dvr_launch.h")}
+                               "dvr_backward_cells4.cu", "dvr_backward_cells8.cu", "dvr_device.cuh",
+                               "dvr_launch.h")}
 
 
 def kernel_source_hash(kernel: str):
