@@ -900,7 +900,8 @@ def run_ours(args):
                 "frac": round(achieved / hbm, 4),
                 "peak_source": src,
                 "traffic": profiled_traffic(dom, args.workload),
-                "bytes_per_sample": 8 * wl.vol[0].element_size(),
+                "bytes_per_sample": round(algorithmic_bytes(wl, dom) / wl.samples_per_pass, 3),
+                "gather_bytes_per_sample": 8 * wl.vol[0].element_size(),
                 "levels": levels,
             },
             "accuracy": acc,
