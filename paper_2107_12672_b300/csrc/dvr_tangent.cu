@@ -145,59 +145,59 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
     tf_cache_init(tfc);
     Cell nxt;
     if (N > 0) fetch_sample(src, G, m, 0, nxt);
-    for (int i = 0; i < N; ++i) {
-        Cell c = nxt;
-        source_decode<VT, CB>(c);
-        fetch_sample(src, G, m, i + 1, nxt);
-        float dg[3];
-        const Density d = cell_density_grad(c, dg);
-        const float ti = (float)i * G.dt;
-        float dd[3];                              // d(density)/d(eye)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float acc = 0.f;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) acc = fmaf(dg[a], fmaf(ti, dw[a][k], dxo[a][k]), acc);
-            dd[k] = acc * G.inv_h;
-        }
-        if (EA) {
-            TFSample s;
-            tf_lookup(tf_s, p.R, d, tfc, s);
-            const float alpha = sample_alpha(G.dt, s.c.w);
-            depth_add(sh, sl, G.dt, s.c.w);         // S_{i+1}
-            const float Tn = transmittance(sh, sl);  // the forward kernel's roundings
-            const float wgt = T * alpha;
-            const bool block_end = (i & (kColourBlock - 1)) == kColourBlock - 1;
-            const float sl_ = s.slope ? Rm1 : 0.f;
-            const float dtau = G.dt * s.dc.w;
+    // blocks of kColourBlock samples, summed as in the forward kernel
+    for (int i0 = 0; i0 < N; i0 += kColourBlock) {
+        const int i1 = min(i0 + kColourBlock, N);
+        for (int i = i0; i < i1; ++i) {
+            Cell c = nxt;
+            source_decode<VT, CB>(c);
+            fetch_sample(src, G, m, i + 1, nxt);
+            float dg[3];
+            const Density d = cell_density_grad(c, dg);
+            const float ti = (float)i * G.dt;
+            float dd[3];                              // d(density)/d(eye)
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const float dk = sl_ * dd[k];        // d(segment position)/d(eye)
-                dS[k] = fmaf(dtau, dk, dS[k]);       // d S_{i+1} / d(eye)
-                const float dTn = -Tn * dS[k];
-                // d(T_i alpha_i) = dT_i alpha_i + T_i (1 - alpha_i) d(dt tau_i),
-                // T_i (1 - alpha_i) = T_{i+1}
-                const float dwgt = fmaf(dT[k], alpha, Tn * (dtau * dk));
-                dC[0][k] = fmaf(dwgt, s.c.x, fmaf(wgt * s.dc.x, dk, dC[0][k]));
-                dC[1][k] = fmaf(dwgt, s.c.y, fmaf(wgt * s.dc.y, dk, dC[1][k]));
-                dC[2][k] = fmaf(dwgt, s.c.z, fmaf(wgt * s.dc.z, dk, dC[2][k]));
-                dT[k] = dTn;
-            }
-            P0 = fmaf(wgt, s.c.x, P0);
-            P1 = fmaf(wgt, s.c.y, P1);
-            P2 = fmaf(wgt, s.c.z, P2);
-            if (block_end) {
-                C0 += P0; C1 += P1; C2 += P2;
-                P0 = 0.f; P1 = 0.f; P2 = 0.f;
-            }
-            T = Tn;
-        } else {
+                float acc = 0.f;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) dS[k] = fmaf(G.dt, dd[k], dS[k]);
-            depth_add_density(sh, sl, G.dt, d);
+                for (int a = 0; a < 3; ++a) acc = fmaf(dg[a], fmaf(ti, dw[a][k], dxo[a][k]), acc);
+                dd[k] = acc * G.inv_h;
+            }
+            if (EA) {
+                TFSample s;
+                tf_lookup(tf_s, p.R, d, tfc, s);
+                const float alpha = sample_alpha(G.dt, s.c.w);
+                depth_add(sh, sl, G.dt, s.c.w);         // S_{i+1}
+                const float Tn = transmittance(sh, sl);  // the forward kernel's roundings
+                const float wgt = T * alpha;
+                const float sl_ = s.slope ? Rm1 : 0.f;
+                const float dtau = G.dt * s.dc.w;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float dk = sl_ * dd[k];        // d(segment position)/d(eye)
+                    dS[k] = fmaf(dtau, dk, dS[k]);       // d S_{i+1} / d(eye)
+                    const float dTn = -Tn * dS[k];
+                    // d(T_i alpha_i) = dT_i alpha_i + T_i (1 - alpha_i) d(dt tau_i),
+                    // T_i (1 - alpha_i) = T_{i+1}
+                    const float dwgt = fmaf(dT[k], alpha, Tn * (dtau * dk));
+                    dC[0][k] = fmaf(dwgt, s.c.x, fmaf(wgt * s.dc.x, dk, dC[0][k]));
+                    dC[1][k] = fmaf(dwgt, s.c.y, fmaf(wgt * s.dc.y, dk, dC[1][k]));
+                    dC[2][k] = fmaf(dwgt, s.c.z, fmaf(wgt * s.dc.z, dk, dC[2][k]));
+                    dT[k] = dTn;
+                }
+                P0 = fmaf(wgt, s.c.x, P0);
+                P1 = fmaf(wgt, s.c.y, P1);
+                P2 = fmaf(wgt, s.c.z, P2);
+                T = Tn;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) dS[k] = fmaf(G.dt, dd[k], dS[k]);
+                depth_add_density(sh, sl, G.dt, d);
+            }
         }
+        C0 += P0; C1 += P1; C2 += P2;
+        P0 = 0.f; P1 = 0.f; P2 = 0.f;
     }
-    C0 += P0; C1 += P1; C2 += P2;
     const long long pix = vw.pixel_offset + (long long)py * vw.width + px;
     if (!in_bounds<kSitePixel>(pix, p.pixel_end)) return;
     const float S = sh + sl;
