@@ -91,7 +91,7 @@ extern "C" {
 #define DVR_ERR_ARG (-1)         /* invalid argument (null pointer, size, index) */
 #define DVR_ERR_DTYPE (-2)       /* unsupported storage type for this argument */
 #define DVR_ERR_CUDA (-3)        /* a CUDA runtime call or launch failed */
-#define DVR_ERR_UNSUPPORTED (-4) /* valid request this build does not implement */
+#define DVR_ERR_UNSUPPORTED (-4) /* valid request the library does not implement */
 #define DVR_ERR_BOUNDS (-5)      /* bounds-checked build: a kernel index failed its check */
 
 /* index sites of the bounds-checked build (dvr_bounds_status) */
