@@ -110,7 +110,10 @@ def peaks():
 KERNEL_SOURCES = {"forward": ("dvr_forward.cu", "dvr_device.cuh", "dvr_launch.h"),
                   "backward": ("dvr_backward.cu", "dvr_backward.cuh", "dvr_backward_cells.cu",
                                "dvr_backward_cells4.cu", "dvr_backward_cells8.cu", "dvr_device.cuh",
-                               "dvr_launch.h")}
+                               "dvr_launch.h"),
+                  # the colour-volume kernels (both passes in one file)
+                  "forward_color": ("dvr_color.cu", "dvr_device.cuh", "dvr_launch.h"),
+                  "backward_color": ("dvr_color.cu", "dvr_device.cuh", "dvr_launch.h")}
 
 
 def kernel_source_hash(kernel: str):
@@ -344,6 +347,8 @@ class Workload:
         once) or into the vertex array."""
         import torch
         dvr, w = self.dvr, self.w
+        if w.model == "color":          # colour volumes gather their corners from the array only
+            cells, cell_gradient = 0, False
         self.use_cells = int(cells)
         self.cells = [dvr.make_cells(v, brick=self.use_cells) for v in self.vol] if cells else None
         self.scene = dvr.Scene.make(self.vol, self.tf, w.model, w.views, cells=self.cells,
@@ -413,16 +418,21 @@ class Workload:
         }
 
 
+def gather_bytes(wl):
+    """Bytes of the 8 trilinear corners of one sample: the volume's element
+    size, times 4 for a colour volume (r, g, b, tau per vertex)."""
+    return 8 * wl.vol[0].element_size() * (4 if wl.w.model == "color" else 1)
+
+
 def algorithmic_bytes(wl, kernel):
     """Bytes the method must move per launch: 8 trilinear corners per sample
-    (element size of the volume) plus per-pixel image/aux/seed traffic; the
-    adjoint adds 8 FP32 read-modify-writes per sample when it scatters the
-    volume gradient."""
-    e = wl.vol[0].element_size()
+    plus per-pixel image/aux/seed traffic; the adjoint adds 8 FP32
+    read-modify-writes per sample (per channel of a colour volume) when it
+    scatters the volume gradient."""
     px = wl.scene.pixels
-    b = wl.samples_per_pass * 8 * e + px * (4 * wl.scene.channels + 8)
+    b = wl.samples_per_pass * gather_bytes(wl) + px * (4 * wl.scene.channels + 8)
     if kernel == "backward" and "volume" in wl.want:
-        b += wl.samples_per_pass * 8 * 4 * 2
+        b += wl.samples_per_pass * 8 * 4 * 2 * (4 if wl.w.model == "color" else 1)
     return b
 
 
@@ -516,7 +526,7 @@ def sampled_accuracy(wl, per_view=64, n_views=4, seed=21):
     if "volume" in want:
         sel = np.unique(np.concatenate([oracle.touched(vol.shape, view, w.eye[k], w.step_voxels, pix=picks[k])
                                         for k, view in enumerate(views)]))
-        ref_vol = np.zeros(sel.size)
+        ref_vol = np.zeros((sel.size,) + vol.shape[3:])     # four entries per vertex of a colour volume
         amb_vol = np.zeros(sel.size)
     ref_tf = np.zeros((tf.shape[0], 4)) if (tf is not None and "tf" in want) else None
     ref_img, e_eye = [], []
@@ -538,9 +548,12 @@ def sampled_accuracy(wl, per_view=64, n_views=4, seed=21):
                          "1e-3 gradients); max_norm: max_i |gpu - ref| / (|ref_i| + max|ref|)",
            "image": _errs(imgh, np.concatenate(ref_img))}
     if sel is not None:
-        flat = g["volume"][0].view(-1)
+        gv = g["volume"][0]
+        flat = gv.view(-1, gv.shape[3]) if gv.dim() == 4 else gv.view(-1)
         idx = torch.as_tensor(sel, device=flat.device)
-        out["grad_volume"] = _errs(flat[idx].cpu().numpy(), ref_vol, amb_vol)
+        got = flat[idx].cpu().numpy()
+        amb = np.broadcast_to(amb_vol.reshape((-1,) + (1,) * (got.ndim - 1)), got.shape)
+        out["grad_volume"] = _errs(got, ref_vol, amb)
         out["grad_volume"]["vertices_compared"] = int(sel.size)
         flat[idx] = 0.0
         out["grad_volume"]["nonzero_outside_the_rays"] = int(torch.count_nonzero(flat))
@@ -784,6 +797,7 @@ def run_ours(args):
         tuning = {"width": args.tile_width, "adjoint_width": aw, "fixed": True}
     elif not args.no_autotune:
         from paper_2107_12672_b300 import autotune
+        color = wl.w.model == "color"         # no cell layout for colour volumes
         tscene, teye, tnote = wl.scene, wl.eye, "all views"
         if probe_ms > 1000.0 and len(wl.w.views) > 4:
             # steps of seconds: tune on the first four views (same volume,
@@ -792,8 +806,9 @@ def run_ours(args):
             teye, tnote = wl.eye[:4].contiguous(), "first 4 views"
         tuning = autotune.autotune(tscene, teye, wl.w.step_voxels, want=wl.want, l2_flush=flush,
                                    reps=1 if probe_ms > 1000.0 else 5,
-                                   layouts=(0, 1, 4, 8) if args.cells < 0 else (args.cells,),
-                                   cell_gradients=(False, True) if args.cell_gradient < 0 else (bool(args.cell_gradient),))
+                                   layouts=(0,) if color else (0, 1, 4, 8) if args.cells < 0 else (args.cells,),
+                                   cell_gradients=(False,) if color else
+                                   (False, True) if args.cell_gradient < 0 else (bool(args.cell_gradient),))
         tuning["tuned_on"] = tnote
         if tuning["cells"] != wl.use_cells or tuning["cell_gradient"] != wl.cell_gradient:
             wl.configure(tuning["cells"], tuning["cell_gradient"])
@@ -823,14 +838,15 @@ def run_ours(args):
             acc = accuracy(wl)
         if not args.no_cpu_baseline:
             cpu = cpu_baseline(wl, budget_s=12.0)
-        if not args.no_variants and "eye" in wl.want:
+        if not args.no_variants and "eye" in wl.want and wl.w.model != "color":
             camera_modes = compare_camera_modes(wl, K2, W2, flush)
-        if not args.no_variants and wl.ea:
+        if not args.no_variants and (wl.ea or wl.w.model == "color"):
             variants = {}
             # the other storage form of the same workload: 16-bit beside a
             # binary32 workload, the plain binary32 form beside a 16-bit one
             plain = wl.w.volume_dtype == "float32" and wl.w.tf_dtype == "float32"
-            for vd, td in ((("bfloat16", "float16"),) if plain else (("float32", "float32"),)):
+            other = ("float16", "float32") if wl.w.model == "color" else ("bfloat16", "float16")
+            for vd, td in ((other,) if plain else (("float32", "float32"),)):
                 # with the gather layout and scatter of the headline workload
                 wv = Workload(args.workload, dev, args.tf_immediate, vol_dtype=vd, tf_dtype=td, views=args.views,
                               image=args.image, cells=wl.use_cells, cell_gradient=wl.cell_gradient, grid=args.grid)
@@ -899,9 +915,9 @@ def run_ours(args):
                 "unit": "GB/s",
                 "frac": round(achieved / hbm, 4),
                 "peak_source": src,
-                "traffic": profiled_traffic(dom, args.workload),
+                "traffic": profiled_traffic(dom + ("_color" if wl.w.model == "color" else ""), args.workload),
                 "bytes_per_sample": round(algorithmic_bytes(wl, dom) / wl.samples_per_pass, 3),
-                "gather_bytes_per_sample": 8 * wl.vol[0].element_size(),
+                "gather_bytes_per_sample": gather_bytes(wl),
                 "levels": levels,
             },
             "accuracy": acc,

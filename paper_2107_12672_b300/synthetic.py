@@ -167,8 +167,8 @@ class View:
 @dataclass
 class Workload:
     name: str
-    model: str                      # "absorption" or "emission_absorption"
-    volumes: list                   # numpy arrays [nz][ny][nx] (storage dtype)
+    model: str                      # "absorption", "emission_absorption" or "color"
+    volumes: list                   # numpy arrays [nz][ny][nx] ([nz][ny][nx][4] for "color")
     tf: np.ndarray | None           # [R][4] or None (absorption)
     views: list                     # list[View]
     eye: np.ndarray                 # [n_views][3] float32 camera positions
@@ -257,6 +257,17 @@ def workload(name: str, scale: float = 1.0) -> Workload:
                              "32 views 2048^2, step 0.25 voxel (~4000 steps on axis-aligned rays), "
                              "opacity-entropy loss",
                         loss="entropy", volume_dtype="float16")
+    if name == "color_256":
+        n = sz(256)
+        vol = color_volume(n, seed=7)
+        w = sz(512)
+        views = [View(w, w) for _ in range(8)]
+        eye = (fibonacci_sphere(8) * 2.5).astype(np.float32)
+        return Workload(name, "color", [vol], None, views, eye, None, 0.5,
+                        ("volume", "camera"), target={"volume": color_volume(n, seed=107)},
+                        note="256^3 FP32 pre-shaded colour volume (r, g, b, tau per vertex, value noise, "
+                             "tau in [0, 20]), 8 Fibonacci views 512^2, step 0.5 voxel, L2 loss against "
+                             "a second colour volume's images")
     raise KeyError(name)
 
 
@@ -270,4 +281,4 @@ def large_volume(n: int, seed: int = 6, device="cuda"):
     return v
 
 
-WORKLOADS = ("absorption_64", "ea_256", "tomo_256x64", "ea_bf16_512", "ea_fp16_1024")
+WORKLOADS = ("absorption_64", "ea_256", "tomo_256x64", "ea_bf16_512", "ea_fp16_1024", "color_256")

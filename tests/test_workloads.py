@@ -38,6 +38,7 @@ SPEC = {
                     ("volume", "tf", "camera")),
     "ea_fp16_1024": (1024, "float16", 32, "float32", "emission_absorption", 32, {2048}, 0.25,
                      ("volume", "tf", "camera")),
+    "color_256": (256, "float32", 0, "float32", "color", 8, {512}, 0.5, ("volume", "camera")),
 }
 
 
