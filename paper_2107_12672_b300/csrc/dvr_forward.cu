@@ -88,10 +88,12 @@ forward_kernel(const __grid_constant__ Params p)
         }
         // blocks of kColourBlock samples: the colour of a block is summed
         // apart and added to the total after it (a per-sample test for the
-        // block's end cost 6 instructions per warp-sample)
+        // block's end cost 6 instructions per warp-sample); unrolled x4, which
+        // divides the block (x3: 1024^3 forward 71.9 -> 69.6 ms on 4 views,
+        // 64-view tomography 13.16 -> 12.01 ms, 256^3 0.309 -> 0.301 ms)
         for (int i0 = 0; i0 < N; i0 += kColourBlock) {
             const int i1 = min(i0 + kColourBlock, N);
-#pragma unroll 3
+#pragma unroll 4
             for (int i = i0; i < i1; ++i) {
                 if (CKPT) {
                     if (ck_left == 0) {
