@@ -148,6 +148,9 @@ tangent_kernel(const __grid_constant__ Params p, float* __restrict__ tangent)
     // blocks of kColourBlock samples, summed as in the forward kernel
     for (int i0 = 0; i0 < N; i0 += kColourBlock) {
         const int i1 = min(i0 + kColourBlock, N);
+        // from the volume's array unrolled x4 (256^3: 0.459 -> 0.394 ms); on
+        // the cell layout rolled (x4 made the 1024^3 case 1.6% slower)
+#pragma unroll (CB == 0 ? 4 : 1)
         for (int i = i0; i < i1; ++i) {
             Cell c = nxt;
             source_decode<VT, CB>(c);
