@@ -472,7 +472,8 @@ DVR_API int dvr_loss_l2(const float* image, const float* target, int64_t n, floa
  *
  * image        device float[P][channels], channels 1 or 4 (as dvr_forward)
  * views        host array as for dvr_forward (sizes and pixel offsets)
- * grad_image   device float[P][channels], overwritten for the views' pixels
+ * grad_image   device float[P][channels] (16-byte aligned for 4 channels),
+ *              overwritten for the views' pixels; must not overlap image
  * loss         device float[1] or NULL
  * stats        device double[n_views][2], caller-owned scratch: receives
  *              (S, T) of each view

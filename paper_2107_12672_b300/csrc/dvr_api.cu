@@ -818,7 +818,8 @@ int dvr_loss_entropy(const float* image, int32_t channels, const dvr_view* views
     g_err[0] = 0;
     if (!image || !grad_image || !stats) return fail(DVR_ERR_ARG, "dvr_loss_entropy: image, grad_image and stats are required");
     if (channels != 1 && channels != 4) return fail(DVR_ERR_ARG, "dvr_loss_entropy: channels %d is not 1 or 4", channels);
-    if (!aligned(image, 4) || !aligned(grad_image, 4) || !aligned(stats, 8) || (loss && !aligned(loss, 4)))
+    if (!aligned(image, 4) || !aligned(grad_image, channels == 4 ? 16 : 4) || !aligned(stats, 8) ||
+        (loss && !aligned(loss, 4)))
         return fail(DVR_ERR_ARG, "dvr_loss_entropy: misaligned pointer");
     if (!views || n_views < 1 || n_views > 4096)
         return fail(DVR_ERR_ARG, "n_views %d outside [1, 4096] or views is NULL", n_views);

@@ -6,7 +6,11 @@
 // H = -(sum p_i ln p_i) / ln N = -(T / S - ln S) / ln N. The loss is
 // scale * (-H) summed over the views (entropy is maximised), and
 // dL/dA_k = scale * (ln A_k - T / S) / (S ln N), with ln A_k taken at
-// A_k = 1e-12 where A_k = 0. The sums are accumulated in binary64.
+// A_k = 1e-12 where A_k = 0. The sums are accumulated in binary64. The
+// logarithm (binary64, the costly part: B300's binary64 rate is a small
+// fraction of its binary32 one) is taken once per pixel: the first pass
+// leaves ln A_k, rounded to binary32, in the gradient's opacity slot (and
+// zeros in its colour slots), which the second pass turns into dL/dA_k.
 #include "dvr_loss.h"
 
 namespace dvr {
@@ -26,16 +30,22 @@ __device__ __forceinline__ double warp_sum_d(double v)
 // blockIdx.y = view; the blocks along x stride over its pixels
 __global__ void __launch_bounds__(kThreads)
 entropy_sums(const __grid_constant__ EntropyViews v, const float* __restrict__ image, int channels,
-             double* __restrict__ stats)
+             float* __restrict__ grad, double* __restrict__ stats)
 {
     const int view = blockIdx.y;
     const long long off = v.offset[view];
     const int n = v.pixels[view];
     double s = 0.0, t = 0.0;
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
-        const double a = (double)__ldg(image + (off + i) * channels + channels - 1);
+        const long long px = off + i;
+        const double a = (double)__ldg(image + px * channels + channels - 1);
+        const double la = log(a > kAMin ? a : kAMin);
         s += a;
-        if (a > 0.0) t += a * log(a);
+        if (a > 0.0) t += a * la;
+        if (channels == 4)
+            reinterpret_cast<float4*>(grad)[px] = make_float4(0.f, 0.f, 0.f, (float)la);
+        else
+            grad[px] = (float)la;
     }
     __shared__ double ss[kThreads / 32], st[kThreads / 32];
     s = warp_sum_d(s);
@@ -56,8 +66,8 @@ entropy_sums(const __grid_constant__ EntropyViews v, const float* __restrict__ i
 }
 
 __global__ void __launch_bounds__(kThreads)
-entropy_grad(const __grid_constant__ EntropyViews v, const float* __restrict__ image, int channels, float scale,
-             float* __restrict__ grad, float* loss, const double* __restrict__ stats)
+entropy_grad(const __grid_constant__ EntropyViews v, int channels, float scale, float* __restrict__ grad,
+             float* loss, const double* __restrict__ stats)
 {
     const int view = blockIdx.y;
     const long long off = v.offset[view];
@@ -67,15 +77,10 @@ entropy_grad(const __grid_constant__ EntropyViews v, const float* __restrict__ i
     const double lnN = ok ? log((double)n) : 1.0;
     if (loss && ok && blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd(loss, (float)((double)scale * (T / S - log(S)) / lnN));
+    const double c = ok ? (double)scale / (S * lnN) : 0.0, ts = ok ? T / S : 0.0;
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
-        float* g = grad + (off + i) * channels;
-        for (int c = 0; c < channels - 1; ++c) g[c] = 0.f;
-        float ga = 0.f;
-        if (ok) {
-            const double a = (double)__ldg(image + (off + i) * channels + channels - 1);
-            ga = (float)((double)scale * (log(a > kAMin ? a : kAMin) - T / S) / (S * lnN));
-        }
-        g[channels - 1] = ga;
+        float* g = grad + (off + i) * channels + channels - 1;
+        *g = (float)(c * ((double)*g - ts));          // *g holds ln A from the first pass
     }
 }
 
@@ -89,10 +94,10 @@ cudaError_t launch_entropy(const EntropyViews& v, const float* image, int channe
     int bx = (most + kThreads - 1) / kThreads;
     if (bx > 64) bx = 64;
     const dim3 grid(bx, v.n);
-    entropy_sums<<<grid, kThreads, 0, stream>>>(v, image, channels, stats);
+    entropy_sums<<<grid, kThreads, 0, stream>>>(v, image, channels, grad, stats);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    entropy_grad<<<grid, kThreads, 0, stream>>>(v, image, channels, scale, grad, loss, stats);
+    entropy_grad<<<grid, kThreads, 0, stream>>>(v, channels, scale, grad, loss, stats);
     return cudaGetLastError();
 }
 

@@ -338,12 +338,14 @@ def test_checkpoint_slots_and_argument_errors():
     assert bwd(0) == -1 and b"alpha" in lib.dvr_last_error()
 
 
-@pytest.mark.parametrize("channels,stats", [(3, 8192), (4, None), (1, 8196)])
-def test_loss_entropy_argument_errors(channels, stats):
+@pytest.mark.parametrize("channels,stats,grad", [(3, 8192, 4096), (4, None, 4096), (1, 8196, 4096),
+                                                 (4, 8192, 4100)])
+def test_loss_entropy_argument_errors(channels, stats, grad):
     """dvr_loss_entropy refuses channel counts other than 1 and 4, a missing
-    or misaligned stats array, before any CUDA call."""
+    or misaligned stats array and an RGBA gradient that is not 16-byte
+    aligned, before any CUDA call."""
     lib = _abi.load()
-    rc = lib.dvr_loss_entropy(4096, channels, _one_view(), 1, 1.0, 4096, None, stats, None)
+    rc = lib.dvr_loss_entropy(4096, channels, _one_view(), 1, 1.0, grad, None, stats, None)
     assert rc == -1 and lib.dvr_last_error()
 
 
