@@ -32,7 +32,8 @@ bandwidth (MEASURED_PEAKS.json) and with the L2 / L1 / reduction ceilings
 measured in the same run (dvr_probe); `traffic` is the DRAM bytes of the
 committed ncu summary of that kernel, when it was taken on the kernel's
 current sources. `e2e` copies the step's inputs from pinned host memory and
-reads the results back every step, through the public binding.
+reads the loss and every gradient back every step, through the public
+binding, the copies overlapped with the neighbouring steps' compute.
 `cpu_baseline` times the FP64 oracle on a strided sample of the same rays
 on the host cores. `accuracy` compares seeded pixels and the gradients of a
 seed supported on them with the FP64 oracle, element by element.
@@ -293,29 +294,7 @@ class Workload:
         self.aux = torch.empty((self.scene.pixels, 2), device=device)
         self.gimg = torch.empty_like(self.image)
         self.want = tuple({"volume": "volume", "tf": "tf", "camera": "eye"}[g] for g in w.grads)
-        # the loss and the small gradients are views of one buffer, zeroed
-        # with one fill per step (each part starts on a 16-byte boundary)
-        parts = [("loss", (1,))]
-        if "tf" in self.want:
-            parts.append(("tf", (self.tf.shape[0], 4)))
-        if "eye" in self.want:
-            parts.append(("eye", tuple(self.eye.shape)))
-            if self.orbit:
-                parts.append(("par", tuple(self.params.shape)))
-        sizes = [int(np.prod(shape)) for _, shape in parts]
-        offs = np.concatenate([[0], np.cumsum([(n + 3) // 4 * 4 for n in sizes])])
-        self.small = torch.zeros(int(offs[-1]), device=device)
-        views = {name: self.small[o:o + n].view(shape) for (name, shape), o, n in zip(parts, offs, sizes)}
-        self.loss = views["loss"]
-        self.grads = {}
-        if "volume" in self.want:
-            self.grads["volume"] = [torch.zeros(v.shape, device=device) for v in self.vol]
-        if "tf" in self.want:
-            self.grads["tf"] = views["tf"]
-        if "eye" in self.want:
-            self.grads["eye"] = views["eye"]
-            if self.orbit:
-                self.g_par = views["par"]
+        self.use_outputs(self.make_outputs())
         self.count = torch.zeros(1, dtype=torch.int64, device=device)
         self.tf_immediate = tf_immediate
         # target image: the same views with the second TF or the second volume
@@ -338,6 +317,47 @@ class Workload:
         # our kernels per step (configure): forward, loss (the entropy loss is
         # two), adjoint, orbit and its adjoint, the cell layouts and the
         # cell-gradient passes
+
+    def make_outputs(self):
+        """A set of the step's outputs: the loss and the small gradients as
+        views of one buffer, zeroed with one fill per step (each part starts
+        on a 16-byte boundary), and the volume gradients."""
+        import torch
+        parts = [("loss", (1,))]
+        if "tf" in self.want:
+            parts.append(("tf", (self.tf.shape[0], 4)))
+        if "eye" in self.want:
+            parts.append(("eye", tuple(self.eye.shape)))
+            if self.orbit:
+                parts.append(("par", tuple(self.params.shape)))
+        sizes = [int(np.prod(shape)) for _, shape in parts]
+        offs = np.concatenate([[0], np.cumsum([(n + 3) // 4 * 4 for n in sizes])])
+        small = torch.zeros(int(offs[-1]), device=self.device)
+        views = {name: small[o:o + n].view(shape) for (name, shape), o, n in zip(parts, offs, sizes)}
+        out = {"small": small, "loss": views["loss"], "grads": {}, "g_par": views.get("par")}
+        if "volume" in self.want:
+            out["grads"]["volume"] = [torch.zeros(v.shape, device=self.device) for v in self.vol]
+        if "tf" in self.want:
+            out["grads"]["tf"] = views["tf"]
+        if "eye" in self.want:
+            out["grads"]["eye"] = views["eye"]
+        return out
+
+    def use_outputs(self, out):
+        """Make `out` (from make_outputs) the set that step() writes."""
+        self.outputs = out
+        self.small, self.loss, self.grads, self.g_par = out["small"], out["loss"], out["grads"], out["g_par"]
+
+    def result_tensors(self):
+        """The tensors of the current output set that a user reads back
+        after a step: the loss and every gradient."""
+        outs = [self.loss]
+        for k, g in self.grads.items():
+            if k == "eye" and self.orbit:
+                outs.append(self.g_par)
+            else:
+                outs.extend(g if isinstance(g, list) else [g])
+        return outs
 
     def configure(self, cells, cell_gradient):
         """Gather from the volumes' arrays (cells 0) or their cell layouts
@@ -936,11 +956,14 @@ def run_ours(args):
 def run_e2e(wl, args, world, K, W):
     """Same metric through the public API with host buffers: every step
     copies its inputs (volume, TF, camera parameters) from pinned host memory
-    and reads back the loss and the gradients, and the host waits for them.
-    The step runs as a captured CUDA graph of the same calls, and the volume
-    is double-buffered: step k+1's volume is copied on a second stream while
-    step k computes (the small inputs are copied on the compute stream just
-    before each replay)."""
+    and reads back the loss and the gradients (the 4 GiB volume gradient at
+    1024^3 included), and the host waits for every step's results. The step
+    runs as a captured CUDA graph of the same calls, pipelined over two
+    buffer sets: step k+1's volume is copied in on one copy stream and step
+    k-1's results are copied out on another while step k computes (the small
+    inputs are copied on the compute stream just before each replay); the
+    host waits for step k-1's results after launching step k, and for the
+    last step's before the clock stops."""
     import torch
     dvr = wl.dvr
     vol_h = wl.vol[0].cpu().pin_memory()
@@ -949,55 +972,69 @@ def run_e2e(wl, args, world, K, W):
         small_in.append((wl.tf, wl.tf.cpu().pin_memory()))
     cam = wl.params if wl.orbit else wl.eye
     small_in.append((cam, cam.cpu().pin_memory()))
-    outs = [wl.loss]
-    for k, g in wl.grads.items():
-        if k == "eye" and wl.orbit:
-            outs.append(wl.g_par)
-        else:
-            outs.extend(g if isinstance(g, list) else [g])
-    h_out = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
 
+    own = wl.outputs
+    out_sets = [own, wl.make_outputs()]
     bufs = [wl.vol[0], torch.empty_like(wl.vol[0])]
     cells1 = [torch.empty_like(wl.cells[0])] if wl.cells is not None else None
     scenes = [wl.scene, dvr.Scene.make([bufs[1]], wl.tf, wl.w.model, wl.w.views, cells=cells1,
                                        cells_brick=wl.use_cells or 1)]
+    outs, h_out = [], []
+    for o in out_sets:
+        wl.use_outputs(o)
+        outs.append(wl.result_tensors())
+        h_out.append([torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs[-1]])
     compute = torch.cuda.current_stream()
-    copier = torch.cuda.Stream()
+    copy_in, copy_out = torch.cuda.Stream(), torch.cuda.Stream()
     graphs = []
-    for sc in scenes:
-        side = torch.cuda.Stream()
-        side.wait_stream(compute)
-        with torch.cuda.stream(side):
-            for _ in range(1 if W < 3 else 3):
+    try:
+        for sc, o in zip(scenes, out_sets):
+            wl.use_outputs(o)
+            side = torch.cuda.Stream()
+            side.wait_stream(compute)
+            with torch.cuda.stream(side):
+                for _ in range(1 if W < 3 else 3):
+                    wl.step(scene=sc)
+            compute.wait_stream(side)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
                 wl.step(scene=sc)
-        compute.wait_stream(side)
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            wl.step(scene=sc)
-        graphs.append(g)
+            graphs.append(g)
+    finally:
+        wl.use_outputs(own)
     torch.cuda.synchronize()
-    copied = [torch.cuda.Event(), torch.cuda.Event()]
-    done = torch.cuda.Event()
+    copied = [torch.cuda.Event(), torch.cuda.Event()]       # volume b is in place
+    computed = [torch.cuda.Event(), torch.cuda.Event()]     # the step on set b is done
+    read = [torch.cuda.Event(), torch.cuda.Event()]         # set b's results are on the host
 
     def prefetch(b):
-        with torch.cuda.stream(copier):
+        with torch.cuda.stream(copy_in):
+            copy_in.wait_event(computed[b])     # the step that last read buffer b
             bufs[b].copy_(vol_h, non_blocking=True)
-            copied[b].record(copier)
+            copied[b].record(copy_in)
 
     def run(n):
+        for e in computed + read:
+            e.record(compute)
         prefetch(0)
         for k in range(n):
             b = k & 1
             if k + 1 < n:
-                prefetch(1 - b)       # the buffer step k - 1 read, which has finished
+                prefetch(1 - b)
             compute.wait_event(copied[b])
+            compute.wait_event(read[b])         # set b's previous results have left the device
             for d, h in small_in:
                 d.copy_(h, non_blocking=True)
             graphs[b].replay()
-            for h, o in zip(h_out, outs):
-                h.copy_(o, non_blocking=True)
-            done.record(compute)
-            done.synchronize()        # the host has the step's loss and gradients
+            computed[b].record(compute)
+            with torch.cuda.stream(copy_out):
+                copy_out.wait_event(computed[b])
+                for h, t in zip(h_out[b], outs[b]):
+                    h.copy_(t, non_blocking=True)
+                read[b].record(copy_out)
+            if k > 0:
+                read[1 - b].synchronize()       # the host has step k-1's loss and gradients
+        read[(n - 1) & 1].synchronize()         # ... and the last step's
         torch.cuda.synchronize()
 
     run(max(1, W))
@@ -1005,12 +1042,13 @@ def run_e2e(wl, args, world, K, W):
     run(K)
     dt = (time.perf_counter() - t0) / K
     h2d = vol_h.numel() * vol_h.element_size() + sum(h.numel() * h.element_size() for _, h in small_in)
-    d2h = sum(h.numel() * h.element_size() for h in h_out)
+    d2h = sum(h.numel() * h.element_size() for h in h_out[0])
     return {"value": round(world * wl.samples_per_pass / dt / 1e9, 4), "unit": "Gsamples/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 4),
             "steps": K,
-            "how": "step as a replayed CUDA graph; next step's volume copied on a second stream "
-                   "during the current step; host waits for each step's loss and gradients"}
+            "how": "step as a replayed CUDA graph over two buffer sets; step k+1's volume copied in and "
+                   "step k-1's loss and gradients copied out on two copy streams during step k; the host "
+                   "waits for every step's results (one step behind), the last one inside the timed region"}
 
 
 # ------------------------------------------------------ the CPU oracle arm
