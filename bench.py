@@ -21,8 +21,8 @@ captured once as a CUDA graph and replayed (--eager: launched step by
 step; `ms_per_step_stats` gives the median, minimum and maximum of those K
 steps). The secondary legs (forward / adjoint breakdown from eager steps,
 e2e, the other storage form, the camera-gradient modes) run
-`secondary_steps` steps each, enough for ~6 s of work, so that the whole
-run ends within a few minutes. The 512^3 and 1024^3 workloads run in their
+`secondary_steps` steps each (e2e at least 6, K allowing), enough for
+~6 s of work, so that the whole run ends within a few minutes. The 512^3 and 1024^3 workloads run in their
 own BF16 / FP16 storage (the arithmetic is binary32 throughout) and
 `storage_variants` times the other storage form of the same workload
 (binary32 beside 16-bit). NVML samples the SM clock and throttle reasons
@@ -94,6 +94,9 @@ def parse():
     ap.add_argument("--cell-gradient", type=int, default=-1, choices=(-1, 0, 1),
                     help="accumulate the volume gradient per cell first (DVR_FLAG_CELL_GRADIENT) or not "
                          "(default: autotuned)")
+    ap.add_argument("--persistent-scatter", type=int, default=-1, choices=(-1, 0, 1),
+                    help="the volume-gradient adjoint as a persistent launch (DVR_FLAG_PERSISTENT_SCATTER) "
+                         "or one tile per warp (default: autotuned)")
     return ap.parse_args()
 
 
@@ -297,6 +300,7 @@ class Workload:
         self.use_outputs(self.make_outputs())
         self.count = torch.zeros(1, dtype=torch.int64, device=device)
         self.tf_immediate = tf_immediate
+        self.persistent_scatter = False
         # target image: the same views with the second TF or the second volume
         if "tf" in w.target:
             tft = torch.as_tensor(w.target["tf"]).to(device=device, dtype=tdt).contiguous()
@@ -409,7 +413,8 @@ class Workload:
             ev[2].record()
         dvr.backward(None, None, None, None, self.eye, w.step_voxels, self.aux, self.gimg, scene=sc,
                      grads=self.grads, want=self.want, tf_immediate=self.tf_immediate,
-                     cell_gradient=self.cell_gradient, workspace=self.cg_ws)
+                     cell_gradient=self.cell_gradient, workspace=self.cg_ws,
+                     persistent_scatter=self.persistent_scatter)
         if ev:
             ev[3].record()
         if self.orbit and "eye" in self.want:
@@ -435,6 +440,8 @@ class Workload:
             "gather_layout": {0: "the volume's array", 1: "cell records in row order (remade every step)",
                               4: "cell records in 4^3 bricks (remade every step)"}[self.use_cells],
             "volume_gradient_scatter": "per cell, then per vertex" if self.cell_gradient else "per vertex",
+            "volume_gradient_launch": ("persistent (tile queue)" if self.persistent_scatter else "one tile per warp")
+            if "volume" in self.want else None,
         }
 
 
@@ -828,10 +835,17 @@ def run_ours(args):
                                    reps=1 if probe_ms > 1000.0 else 5,
                                    layouts=(0,) if color else (0, 1, 4, 8) if args.cells < 0 else (args.cells,),
                                    cell_gradients=(False,) if color else
-                                   (False, True) if args.cell_gradient < 0 else (bool(args.cell_gradient),))
+                                   (False, True) if args.cell_gradient < 0 else (bool(args.cell_gradient),),
+                                   persistent=(False, True) if args.persistent_scatter < 0
+                                   else (bool(args.persistent_scatter),))
         tuning["tuned_on"] = tnote
         if tuning["cells"] != wl.use_cells or tuning["cell_gradient"] != wl.cell_gradient:
             wl.configure(tuning["cells"], tuning["cell_gradient"])
+        wl.persistent_scatter = bool(tuning.get("persistent_scatter", False))
+    if args.persistent_scatter >= 0:
+        wl.persistent_scatter = bool(args.persistent_scatter)
+    if tuning is not None:
+        tuning["persistent_scatter"] = wl.persistent_scatter
     # per-kernel breakdown from eagerly launched steps; the headline step
     # time from the same step replayed as one CUDA graph
     eager_ms, fwd_ms, bwd_ms, _, _ = time_steps(wl, K2, W2, flush, None, world)
@@ -851,7 +865,10 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(wl, args, world, K2, W2)
+        # at least 6 steps (K allowing): the first upload and the last
+        # read-back have no neighbouring step to hide behind, and over n
+        # steps each step carries 1/n of them
+        e2e = run_e2e(wl, args, world, max(K2, min(K, 6)), W2)
     cpu = acc = variants = camera_modes = None
     if rank == 0 and world == 1:
         if not args.no_accuracy:
@@ -870,6 +887,7 @@ def run_ours(args):
                 # with the gather layout and scatter of the headline workload
                 wv = Workload(args.workload, dev, args.tf_immediate, vol_dtype=vd, tf_dtype=td, views=args.views,
                               image=args.image, cells=wl.use_cells, cell_gradient=wl.cell_gradient, grid=args.grid)
+                wv.persistent_scatter = wl.persistent_scatter
                 sm, fm, bm, _, _ = time_steps(wv, K2, W2, flush)
                 variants[f"volume_{vd}_tf_{td}"] = {
                     "value": round(wv.samples_per_pass / (sm * 1e-3) / 1e9, 4), "unit": "Gsamples/s",

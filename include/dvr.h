@@ -77,7 +77,7 @@
 extern "C" {
 #endif
 
-#define DVR_ABI_VERSION 12
+#define DVR_ABI_VERSION 13
 
 /* exported from the shared library (which hides everything else) */
 #if defined(__GNUC__)
@@ -139,6 +139,16 @@ extern "C" {
  * records follow the order of the volume's cell layout (row order without
  * one). Not for DVR_COLOR_VOLUME. */
 #define DVR_FLAG_CELL_GRADIENT 8u
+/* with a volume gradient of a 16-bit (FP16 / BF16) volume: make the
+ * launch persistent, as the adjoint is without a volume gradient: as many
+ * blocks as are resident at once, each warp taking ray tiles from the
+ * launch's tile-queue counter in the workspace until none are left,
+ * instead of one tile per warp. The same sums in another order; which is
+ * faster depends on the workload (the autotuner tries both). Ignored
+ * without a volume gradient, for binary32 volumes (whose kernels would
+ * lose a resident block per SM to the tile loop's registers) and for
+ * DVR_COLOR_VOLUME. */
+#define DVR_FLAG_PERSISTENT_SCATTER 16u
 
 /* One volume. `data` is a device pointer to nx*ny*nz samples of `dtype`,
  * layout [nz][ny][nx] (4 per vertex, [nz][ny][nx][4], for

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 BOUNDS_LIB_PATH = os.path.join(_HERE, "_lib", "libdvr_bounds.so")
 LIB_PATH = os.environ.get("DVR_LIBRARY") or os.path.join(_HERE, "_lib", "libdvr.so")
 
-ABI_VERSION = 12         # DVR_ABI_VERSION of the header these argtypes follow
+ABI_VERSION = 13         # DVR_ABI_VERSION of the header these argtypes follow
 DVR_OK = 0
 DVR_F32, DVR_F16, DVR_BF16 = 0, 1, 2
 DVR_ABSORPTION, DVR_EMISSION_ABSORPTION, DVR_COLOR_VOLUME = 0, 1, 2
@@ -27,6 +27,7 @@ DVR_FLAG_TF_IMMEDIATE = 1
 DVR_FLAG_INVERT_ALPHA32 = 2
 DVR_FLAG_INVERT_ALPHA64 = 4
 DVR_FLAG_CELL_GRADIENT = 8
+DVR_FLAG_PERSISTENT_SCATTER = 16
 DVR_ERR_BOUNDS = -5
 DVR_SITE_VOLUME, DVR_SITE_CELLS, DVR_SITE_PIXEL, DVR_SITE_TF, DVR_SITE_CELL_GRADIENT = 1, 2, 3, 4, 5
 

@@ -10,7 +10,9 @@ one or two 16-byte loads per cell, records in row order or in bricks of
 4^3 cells; the layout is remade before each timed forward, as a step that
 changes the volume must) and, when a volume
 gradient is asked for, how it is accumulated (into the vertex array, or
-per cell first: DVR_FLAG_CELL_GRADIENT). None of the choices changes
+per cell first: DVR_FLAG_CELL_GRADIENT) and whether that adjoint runs as a
+persistent launch taking tiles from a queue (DVR_FLAG_PERSISTENT_SCATTER,
+timed at the chosen layout and widths). None of the choices changes
 results beyond the order of the gradient's additions. Choices are cached per
 device and workload signature for the life of the process, and optionally
 in a JSON file.
@@ -51,22 +53,25 @@ def get_tile_width(adjoint: bool = False) -> int:
 
 def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 5,
              candidates=CANDIDATES, cache_file: str | None = None, l2_flush: torch.Tensor | None = None,
-             layouts=(0,), cell_gradients=(False,)) -> dict:
+             layouts=(0,), cell_gradients=(False,), persistent=(False,)) -> dict:
     """Time the forward and the adjoint pass for each tile width (two
     interleaved rounds, the faster of the two kept) and each gather layout
     in `layouts` (0: the volume's array; 1 / 4 / 8: its cell layout with
     records in row order / in bricks of 4^3 / 8^3 cells, so the brick edge,
     built before each forward and timed with it) and, for the adjoint of a volume
-    gradient, each scatter in `cell_gradients`; set the fastest width of
-    each pass and return {"width", "adjoint_width", "cells",
-    "cell_gradient", "ms": {...}}. The layout is chosen by forward + adjoint
-    time at each side's best width. Cached per signature. With `l2_flush`
+    gradient, each scatter in `cell_gradients` and then, at the chosen
+    layout, scatter and width, each launch form in `persistent` (False: one
+    tile per warp; True: DVR_FLAG_PERSISTENT_SCATTER); set the fastest
+    width of each pass and return {"width", "adjoint_width", "cells",
+    "cell_gradient", "persistent_scatter", "ms": {...}}. The layout is
+    chosen by forward + adjoint time at each side's best width. Cached per signature. With `l2_flush`
     (a device buffer larger than L2), the buffer is overwritten before each
     timed pass, so that the passes start with the volume out of L2 as in a
     loop that touches other data between steps."""
     gvol = "volume" in want
     cell_gradients = cell_gradients if gvol else (False,)
-    key = signature(scene, want) + f"|cells{tuple(layouts)}|cg{tuple(cell_gradients)}"
+    persistent = persistent if gvol else (False,)
+    key = signature(scene, want) + f"|cells{tuple(layouts)}|cg{tuple(cell_gradients)}|ps{tuple(persistent)}"
     if key not in _cache and cache_file and os.path.exists(cache_file):
         try:
             _cache.update(json.load(open(cache_file)))
@@ -152,7 +157,30 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
                 best = (total, bf, bb, use_cells, cg)
     _, best_f, best_b, use_cells, cg = best
     set_tile_width(best_f, best_b)
+    ps = persistent[0]
+    if len(persistent) > 1:
+        # the launch form of the volume-gradient adjoint, at the chosen layout,
+        # scatter and width (two interleaved rounds, the faster kept)
+        cells = [make_cells(v, brick=use_cells) for v in scene.volumes] if use_cells else None
+        sc = Scene.make(scene.volumes, scene.tf, scene.model, scene.views, cells=cells, cells_brick=use_cells or 1)
+        cg_ws = torch.empty(cell_workspace_bytes(sc), dtype=torch.uint8, device=dev) if cg else None
+        forward(None, None, None, None, eye, step_voxels, scene=sc, image=image, aux=aux)
+        pk = f"adjoint|cells={int(use_cells)}|cell_gradient={int(cg)}|width={best_b}|persistent"
+        times[pk] = {}
+        for _ in range(2):
+            for p in persistent:
+                def bwd():
+                    backward(None, None, None, None, eye, step_voxels, aux, seed, scene=sc, grads=grads,
+                             want=w_want, cell_gradient=cg, workspace=cg_ws if cg else None,
+                             persistent_scatter=p)
+                bwd()
+                torch.cuda.synchronize()
+                t = timed(bwd)
+                times[pk][int(p)] = min(t, times[pk].get(int(p), t))
+        ps = bool(min(times[pk], key=times[pk].get))
+        del cells, sc, cg_ws
     result = {"width": best_f, "adjoint_width": best_b, "cells": int(use_cells), "cell_gradient": bool(cg),
+              "persistent_scatter": ps,
               "ms": {n: {str(k): round(v, 4) for k, v in t.items()} for n, t in times.items()}}
     _cache[key] = result
     if cache_file:

@@ -224,7 +224,7 @@ def forward(volumes, tf, model, views, eye, step_voxels, *, scene: Scene | None 
 
 def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, want=("volume", "tf", "eye"),
              scene: Scene | None = None, grads: dict | None = None, tf_immediate=False, inversion="depth",
-             stream=None, checkpoints=None, cell_gradient=False, workspace=None):
+             stream=None, checkpoints=None, cell_gradient=False, workspace=None, persistent_scatter=False):
     """Alg. 2 for all views in one launch. Returns a dict with float32
     gradients for the requested parameters ("volume" -> list, "tf", "eye",
     "step"); buffers passed in `grads` are accumulated into. `inversion`
@@ -235,7 +235,11 @@ def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, wa
     accumulates the volume gradient per cell first
     (DVR_FLAG_CELL_GRADIENT); its workspace, 32 bytes per cell, comes from
     `workspace` (a uint8 tensor of at least cell_workspace_bytes(scene)
-    bytes, kept by the caller) or else from torch's caching allocator."""
+    bytes, kept by the caller) or else from torch's caching allocator.
+    `persistent_scatter` makes the volume-gradient adjoint of 16-bit
+    volumes a persistent launch whose warps take tiles from a queue
+    (DVR_FLAG_PERSISTENT_SCATTER; the adjoint without a volume gradient
+    always is one; binary32 volumes keep one tile per warp)."""
     sc = scene or Scene.make(volumes, tf, model, views)
     dev = sc.volumes[0].device
     g = dict(grads or {})
@@ -252,6 +256,8 @@ def backward(volumes, tf, model, views, eye, step_voxels, aux, grad_image, *, wa
         gv = (ctypes.c_void_p * len(sc.volumes))(*[_ptr(t) for t in g["volume"]])
     flags = _abi.DVR_FLAG_TF_IMMEDIATE if tf_immediate else 0
     flags |= {"depth": 0, "alpha32": _abi.DVR_FLAG_INVERT_ALPHA32, "alpha64": _abi.DVR_FLAG_INVERT_ALPHA64}[inversion]
+    if persistent_scatter:
+        flags |= _abi.DVR_FLAG_PERSISTENT_SCATTER
     lib = _abi.load()
     if cell_gradient and "volume" in g:
         flags |= _abi.DVR_FLAG_CELL_GRADIENT

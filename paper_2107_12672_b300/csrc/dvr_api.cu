@@ -410,7 +410,7 @@ int backward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf
                   size_t workspace_bytes_, void* stream)
 {
     if (flags & ~(DVR_FLAG_TF_IMMEDIATE | DVR_FLAG_INVERT_ALPHA32 | DVR_FLAG_INVERT_ALPHA64 |
-                  DVR_FLAG_CELL_GRADIENT))
+                  DVR_FLAG_CELL_GRADIENT | DVR_FLAG_PERSISTENT_SCATTER))
         return fail(DVR_ERR_ARG, "unknown flag bits 0x%x", flags);
     if ((flags & DVR_FLAG_INVERT_ALPHA32) && (flags & DVR_FLAG_INVERT_ALPHA64))
         return fail(DVR_ERR_ARG, "choose one inversion ablation");
@@ -477,6 +477,7 @@ int backward_impl(const dvr_volume* volumes, int32_t n_volumes, const dvr_tf* tf
              step_voxels);
         p.queue = reinterpret_cast<unsigned*>(static_cast<char*>(workspace)
                                               + (size_t)(v0 / dvr::kMaxViewsPerLaunch) * kQueueStride);
+        p.scatter_queue = (flags & DVR_FLAG_PERSISTENT_SCATTER) ? 1 : 0;
         if (tile_order) {
             p.order = tile_order + order_off;
             order_off += p.total_tiles;

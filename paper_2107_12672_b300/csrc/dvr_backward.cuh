@@ -172,11 +172,16 @@ backward_kernel(const __grid_constant__ Params p)
     const float Rm1 = (float)(p.R - 1);
 
     // warps take tiles from the queue until it runs dry; the scatter variants
-    // (GVOL) keep one tile per warp (measured faster there: with the queue a
-    // block's warps no longer march neighbouring tiles together)
-    constexpr bool QUEUE = !GVOL;
-    for (int rank = QUEUE ? next_tile(p.queue, lane) : blockIdx.x * kWarps + warp; rank < p.total_tiles;
-         rank = QUEUE ? next_tile(p.queue, lane) : p.total_tiles) {
+    // (GVOL) of 16-bit volumes do so with DVR_FLAG_PERSISTENT_SCATTER and
+    // otherwise keep one tile per warp (with the queue a block's warps no
+    // longer march neighbouring tiles together: faster or slower by
+    // workload); those of binary32 volumes always keep one tile per warp (a
+    // real loop over tiles keeps more values live: 168 -> 172 registers,
+    // which would leave 2 instead of 3 blocks per SM)
+    constexpr bool CAN_QUEUE = !GVOL || sizeof(VT) == 2;
+    const bool queued = !GVOL || (CAN_QUEUE && p.scatter_queue != 0);   // uniform over the launch
+    for (int rank = queued ? next_tile(p.queue, lane) : blockIdx.x * kWarps + warp; rank < p.total_tiles;
+         rank = queued ? next_tile(p.queue, lane) : p.total_tiles) {
         const int tile = tile_at(p, rank);
         if (tile < 0) continue;                 // warp-uniform
         const int v = find_view(p, tile);
@@ -524,7 +529,7 @@ static cudaError_t launch_one(const Params& p, cudaStream_t stream)
     // one tile per warp; with the tile queue, as many blocks as fit on the
     // device at once
     int blocks = (p.total_tiles + kWarps - 1) / kWarps;
-    if (!GVOL) {
+    if (!GVOL || (sizeof(VT) == 2 && p.scatter_queue)) {
         // resident blocks per SM for this shared-memory size, cached per
         // instantiation (smem << 8 | blocks; the last query wins)
         static std::atomic<unsigned long long> occ{0};

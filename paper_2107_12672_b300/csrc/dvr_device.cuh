@@ -94,6 +94,7 @@ struct Params {
     float* grad_step;
     unsigned long long* sample_count;
     unsigned* queue;                 // adjoint tile queue: a counter zeroed before the launch
+    int scatter_queue;               // the volume-gradient adjoint takes its tiles from the queue too
     const unsigned* order;           // tile taken at each rank of the launch, or null: rank order
     float* ckpt;                     // transmittance before samples 0, K, 2K, ... ([pixel][ckpt_slots]) or null
     int ckpt_k;

@@ -23,6 +23,18 @@ def test_header_declares_what_binding_lists():
     assert _declared() == sorted(_abi.SYMBOLS)
 
 
+def test_flag_values_match_header():
+    """Every DVR_FLAG_* of the header has the same value in the binding's
+    mirror, and the flags are distinct bits."""
+    header = open(os.path.join(ROOT, "include", "dvr.h")).read()
+    flags = {k: int(v) for k, v in re.findall(r"#define (DVR_FLAG_\w+) (\d+)u", header)}
+    assert "DVR_FLAG_PERSISTENT_SCATTER" in flags
+    for k, v in flags.items():
+        assert getattr(_abi, k) == v, k
+        assert v & (v - 1) == 0, k
+    assert len(set(flags.values())) == len(flags)
+
+
 def test_library_loads_and_exports_every_symbol():
     lib = _abi.load()
     for name in _declared():

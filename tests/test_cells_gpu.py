@@ -150,6 +150,34 @@ def test_cell_gradient_equals_vertex_scatter(dtype, model):
             assert_close(b[k].cpu().numpy(), a[k].cpu().numpy(), 1e-4, k)
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_persistent_scatter_equals_one_tile_per_warp(dtype):
+    """DVR_FLAG_PERSISTENT_SCATTER (the volume-gradient adjoint with as
+    many blocks as are resident, warps taking tiles from a queue) gives the
+    gradients of the launch with one tile per warp, up to the order of the
+    additions, for two volumes and three views: from the volume's array and
+    from its cell layout in 4^3 bricks, with the vertex scatter and with the
+    per-cell gradient."""
+    vols = [to_dev(syn.value_noise(n, seed=s)[:, :n - 3, :], dtype).contiguous() for n, s in ((33, 5), (24, 6))]
+    tf = to_dev(syn.random_tf(16, seed=7))
+    views = [syn.View(37, 29), syn.View(20, 21, volume_index=1), syn.View(16, 11, ortho=True, ortho_height=1.2)]
+    eye = to_dev((syn.fibonacci_sphere(3) * 2.2).astype(np.float32))
+    G = to_dev(seeded_grad_image(sum(v.width * v.height for v in views), 4, 10))
+    want = ("volume", "tf", "eye")
+    for brick, cells in ((1, None), (4, [dvr.make_cells(v, brick=4) for v in vols])):
+        sc = dvr.Scene.make(vols, tf, "emission_absorption", views, cells=cells, cells_brick=brick)
+        _, aux = dvr.forward(None, None, None, None, eye, 0.4, scene=sc)
+        for cg in (False, True):
+            a = dvr.backward(None, None, None, None, eye, 0.4, aux, G, scene=sc, want=want, cell_gradient=cg)
+            b = dvr.backward(None, None, None, None, eye, 0.4, aux, G, scene=sc, want=want, cell_gradient=cg,
+                             persistent_scatter=True)
+            torch.cuda.synchronize()
+            for i in range(len(vols)):
+                assert_close(b["volume"][i].cpu().numpy(), a["volume"][i].cpu().numpy(), 1e-4, f"volume {i}")
+            for k in want[1:]:
+                assert_close(b[k].cpu().numpy(), a[k].cpu().numpy(), 1e-4, k)
+
+
 def test_cell_gradient_accumulates_and_full_size():
     """The cell-gradient pass adds into the caller's gradient (Alg. 2's +=)
     and zeroes its cell array on every call: two calls give twice one call.

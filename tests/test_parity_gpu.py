@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _run_gpu(w, vol_dtype=torch.float32, tf_dtype=torch.float32, grad_seed=5, want=("volume", "tf", "eye"),
-             tf_immediate=False):
+             tf_immediate=False, persistent_scatter=False):
     vols = [to_dev(v, vol_dtype) for v in w.volumes]
     tf = to_dev(w.tf, tf_dtype) if w.tf is not None else None
     eye = to_dev(w.eye)
@@ -31,7 +31,7 @@ def _run_gpu(w, vol_dtype=torch.float32, tf_dtype=torch.float32, grad_seed=5, wa
     nc = img.shape[1]
     G = seeded_grad_image(img.shape[0], nc, grad_seed)
     g = dvr.backward(vols, tf, w.model, w.views, eye, w.step_voxels, aux, to_dev(G), want=want,
-                     tf_immediate=tf_immediate)
+                     tf_immediate=tf_immediate, persistent_scatter=persistent_scatter)
     torch.cuda.synchronize()
     return vols, tf, img.cpu().numpy(), int(count.item()), G, g
 
@@ -128,6 +128,29 @@ def test_multiview_uneven_one_launch():
         v.volume_index = k % 2
     want = ("volume", "eye")
     gpu = _run_gpu(w, want=want)
+    ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
+    _compare(w, gpu, ref, want)
+
+
+@pytest.mark.parametrize("case", ["multiview", "ea_ragged_fp16"])
+def test_persistent_scatter_against_oracle(case):
+    """The volume-gradient adjoint as a persistent launch
+    (DVR_FLAG_PERSISTENT_SCATTER: as many blocks as are resident, each warp
+    taking ray tiles from the launch's queue) against the oracle, element
+    by element: 64 uneven views of two absorption volumes in one launch
+    (volume and eye gradients), and one ragged 131 x 97 emission-absorption
+    view of an FP16 volume (volume, TF and eye gradients)."""
+    if case == "multiview":
+        w = syn.workload("tomo_256x64", scale=1 / 16)
+        w.volumes.append(syn.gaussian_blobs(w.volumes[0].shape[0], 4, seed=45))
+        for k, v in enumerate(w.views):
+            v.volume_index = k % 2
+        want, vdt = ("volume", "eye"), torch.float32
+    else:
+        w = syn.workload("ea_256", scale=0.25)
+        w.views = [syn.View(131, 97)]
+        want, vdt = ("volume", "tf", "eye"), torch.float16
+    gpu = _run_gpu(w, vol_dtype=vdt, want=want, persistent_scatter=True)
     ref = _oracle(w, gpu[0], gpu[1], gpu[4], want=want)
     _compare(w, gpu, ref, want)
 
