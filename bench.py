@@ -812,6 +812,8 @@ def run_ours(args):
                   cells=max(args.cells, 0), cell_gradient=args.cell_gradient > 0, grid=args.grid)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     K = args.steps
+    if args.persistent_scatter >= 0:            # a fixed launch form applies from the first step on
+        wl.persistent_scatter = bool(args.persistent_scatter)
     # one untimed step to size the secondary legs (~10 s of work each)
     probe_ms, _, _, _, _ = time_steps(wl, 1, 1, flush, None, world)
     K2 = max(2, min(K, int(math.ceil(6_000.0 / max(probe_ms, 1e-3)))))

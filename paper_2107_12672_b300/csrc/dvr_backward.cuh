@@ -144,7 +144,9 @@ __device__ __forceinline__ void cell_run_flush(float* g, float* cg, bool v16, ui
     }
 }
 
-template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV = kInvDepth, int CB = 0>
+// QUEUE: warps take tiles from the launch's queue (always without a volume
+// gradient; with one for 16-bit volumes under DVR_FLAG_PERSISTENT_SCATTER)
+template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV = kInvDepth, int CB = 0, bool QUEUE = !GVOL>
 __global__ void __launch_bounds__(kWarps * 32, GVOL ? (sizeof(VT) == 2 ? DVR_BWD_MIN_BLOCKS_16 : DVR_BWD_MIN_BLOCKS)
                                                     : DVR_BWD_QUEUE_MIN_BLOCKS)
 backward_kernel(const __grid_constant__ Params p)
@@ -171,17 +173,18 @@ backward_kernel(const __grid_constant__ Params p)
     float* my_tfg = tfg + warp * p.R * 4;
     const float Rm1 = (float)(p.R - 1);
 
-    // warps take tiles from the queue until it runs dry; the scatter variants
-    // (GVOL) of 16-bit volumes do so with DVR_FLAG_PERSISTENT_SCATTER and
-    // otherwise keep one tile per warp (with the queue a block's warps no
-    // longer march neighbouring tiles together: faster or slower by
-    // workload); those of binary32 volumes always keep one tile per warp (a
-    // real loop over tiles keeps more values live: 168 -> 172 registers,
-    // which would leave 2 instead of 3 blocks per SM)
-    constexpr bool CAN_QUEUE = !GVOL || sizeof(VT) == 2;
-    const bool queued = !GVOL || (CAN_QUEUE && p.scatter_queue != 0);   // uniform over the launch
-    for (int rank = queued ? next_tile(p.queue, lane) : blockIdx.x * kWarps + warp; rank < p.total_tiles;
-         rank = queued ? next_tile(p.queue, lane) : p.total_tiles) {
+    // with QUEUE, warps take tiles from the queue until it runs dry; else
+    // each warp marches one tile. The scatter variants (GVOL) of 16-bit
+    // volumes exist in both forms (DVR_FLAG_PERSISTENT_SCATTER picks; with
+    // the queue a block's warps no longer march neighbouring tiles
+    // together: faster or slower by workload); those of binary32 volumes
+    // keep one tile per warp (a loop over tiles keeps more values live: 168
+    // -> 172 registers, which would leave 2 instead of 3 blocks per SM).
+    // The form is a template parameter: decided at run time, the loop over
+    // tiles cost the one-tile form 4% more instructions per sample (1024^3
+    // FP16 stand-in, 5.74 -> 5.99 G)
+    for (int rank = QUEUE ? next_tile(p.queue, lane) : blockIdx.x * kWarps + warp; rank < p.total_tiles;
+         rank = QUEUE ? next_tile(p.queue, lane) : p.total_tiles) {
         const int tile = tile_at(p, rank);
         if (tile < 0) continue;                 // warp-uniform
         const int v = find_view(p, tile);
@@ -503,10 +506,10 @@ backward_kernel(const __grid_constant__ Params p)
     }
 }
 
-template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV, int CB>
+template <int MODEL, typename VT, bool GVOL, int TFM, bool POS, int INV, int CB, bool QUEUE = !GVOL>
 static cudaError_t launch_one(const Params& p, cudaStream_t stream)
 {
-    auto k = backward_kernel<MODEL, VT, GVOL, TFM, POS, INV, CB>;
+    auto k = backward_kernel<MODEL, VT, GVOL, TFM, POS, INV, CB, QUEUE>;
     size_t smem = 0;
     if (MODEL == DVR_EMISSION_ABSORPTION) {
         smem = sizeof(float4) * 2 * (size_t)p.R;
@@ -529,7 +532,7 @@ static cudaError_t launch_one(const Params& p, cudaStream_t stream)
     // one tile per warp; with the tile queue, as many blocks as fit on the
     // device at once
     int blocks = (p.total_tiles + kWarps - 1) / kWarps;
-    if (!GVOL || (sizeof(VT) == 2 && p.scatter_queue)) {
+    if (QUEUE) {
         // resident blocks per SM for this shared-memory size, cached per
         // instantiation (smem << 8 | blocks; the last query wins)
         static std::atomic<unsigned long long> occ{0};
@@ -563,6 +566,11 @@ static cudaError_t pick_pos(const Params& p, bool pos, int inv, cudaStream_t s)
                        : launch_one<MODEL, VT, GVOL, TFM, false, kInvAlpha64, 0>(p, s);
     }
     if (inv != kInvDepth) return cudaErrorNotSupported;
+    if constexpr (GVOL && sizeof(VT) == 2) {
+        if (p.scatter_queue)
+            return pos ? launch_one<MODEL, VT, GVOL, TFM, true, kInvDepth, CB, true>(p, s)
+                       : launch_one<MODEL, VT, GVOL, TFM, false, kInvDepth, CB, true>(p, s);
+    }
     return pos ? launch_one<MODEL, VT, GVOL, TFM, true, kInvDepth, CB>(p, s)
                : launch_one<MODEL, VT, GVOL, TFM, false, kInvDepth, CB>(p, s);
 }
