@@ -440,7 +440,8 @@ class Workload:
             "gather_layout": {0: "the volume's array", 1: "cell records in row order (remade every step)",
                               4: "cell records in 4^3 bricks (remade every step)"}[self.use_cells],
             "volume_gradient_scatter": "per cell, then per vertex" if self.cell_gradient else "per vertex",
-            "volume_gradient_launch": ("persistent (tile queue)" if self.persistent_scatter else "one tile per warp")
+            "volume_gradient_launch": ("persistent (tile queue)"
+                                       if self.persistent_scatter and v.element_size() == 2 else "one tile per warp")
             if "volume" in self.want else None,
         }
 

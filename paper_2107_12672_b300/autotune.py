@@ -71,7 +71,9 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
     loop that touches other data between steps."""
     gvol = "volume" in want
     cell_gradients = cell_gradients if gvol else (False,)
-    persistent = persistent if gvol else (False,)
+    # the launch form exists for the volume-gradient adjoint of 16-bit volumes
+    sixteen = all(v.dtype in (torch.float16, torch.bfloat16) for v in scene.volumes)
+    persistent = persistent if gvol and sixteen else (False,)
     key = signature(scene, want) + f"|cells{tuple(layouts)}|cg{tuple(cell_gradients)}|ps{tuple(persistent)}"
     if key not in _cache and cache_file and os.path.exists(cache_file):
         try:

@@ -567,6 +567,17 @@ def test_tile_width_changes_nothing_and_autotuner_picks_one():
             {f"adjoint|cells={c}|cell_gradient={g}" for c in (0, 1, 4, 8) for g in (0, 1)} == set(res["ms"])
         assert res["width"] in (8, 16) and res["adjoint_width"] in (8, 16)
         assert res["cells"] in (0, 1, 4, 8) and isinstance(res["cell_gradient"], bool)
+        # the launch form of the volume-gradient adjoint: not a choice for a
+        # binary32 volume, timed both ways for a 16-bit one
+        autotune._cache.clear()
+        res = autotune.autotune(sc, eye, w.step_voxels, want=("volume", "tf", "eye"), reps=1, candidates=(8,),
+                                persistent=(False, True))
+        assert res["persistent_scatter"] is False and not any(k.endswith("|persistent") for k in res["ms"])
+        sc16 = dvr.Scene.make([to_dev(w.volumes[0], torch.float16)], tf, w.model, w.views)
+        res = autotune.autotune(sc16, eye, w.step_voxels, want=("volume", "tf", "eye"), reps=1, candidates=(8,),
+                                layouts=(4,), cell_gradients=(True,), persistent=(False, True))
+        pk = "adjoint|cells=4|cell_gradient=1|width=8|persistent"
+        assert set(res["ms"][pk]) == {"0", "1"} and isinstance(res["persistent_scatter"], bool)
     finally:
         autotune.set_tile_width(old, old_adj)
 
