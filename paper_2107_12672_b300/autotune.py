@@ -58,17 +58,18 @@ def autotune(scene: Scene, eye, step_voxels, *, want=("tf", "eye"), reps: int = 
     interleaved rounds, the faster of the two kept) and each gather layout
     in `layouts` (0: the volume's array; 1 / 4 / 8: its cell layout with
     records in row order / in bricks of 4^3 / 8^3 cells, so the brick edge,
-    built before each forward and timed with it) and, for the adjoint of a volume
-    gradient, each scatter in `cell_gradients` and then, at the chosen
-    layout, scatter and width, each launch form in `persistent` (False: one
-    tile per warp; True: DVR_FLAG_PERSISTENT_SCATTER, kept unless the other
-    is more than 1% faster); set the fastest
-    width of each pass and return {"width", "adjoint_width", "cells",
-    "cell_gradient", "persistent_scatter", "ms": {...}}. The layout is
-    chosen by forward + adjoint time at each side's best width. Cached per signature. With `l2_flush`
-    (a device buffer larger than L2), the buffer is overwritten before each
-    timed pass, so that the passes start with the volume out of L2 as in a
-    loop that touches other data between steps."""
+    built before each forward and timed with it) and, for the adjoint of a
+    volume gradient, each scatter in `cell_gradients` and then, at the
+    chosen layout, scatter and width, each launch form in `persistent`
+    (False: one tile per warp; True: DVR_FLAG_PERSISTENT_SCATTER, kept
+    unless the other is more than 1% faster; 16-bit volumes only). Sets the
+    fastest width of each pass and returns {"width", "adjoint_width",
+    "cells", "cell_gradient", "persistent_scatter", "ms": {...}}. The layout
+    is chosen by forward + adjoint time at each side's best width. Cached
+    per signature. With `l2_flush` (a device buffer larger than L2), the
+    buffer is overwritten before each timed pass, so that the passes start
+    with the volume out of L2 as in a loop that touches other data between
+    steps."""
     gvol = "volume" in want
     cell_gradients = cell_gradients if gvol else (False,)
     # the launch form exists for the volume-gradient adjoint of 16-bit volumes
