@@ -189,6 +189,32 @@ def test_persistent_forward_over_several_launches():
         assert out[0][2] == out[1][2] > 0
 
 
+def test_persistent_scatter_over_several_launches():
+    """More views than one launch takes (600 > 512: two adjoint launches,
+    each with its own tile-queue counter in the workspace): the persistent
+    volume-gradient adjoint of an FP16 volume gives the volume, TF and eye
+    gradients of the launch with one tile per warp, for every view, from the
+    volume's array and from its cell layout with the per-cell gradient."""
+    w = syn.workload("ea_256", scale=0.0625)
+    vol, tf = to_dev(w.volumes[0], torch.float16), to_dev(w.tf)
+    views = [syn.View(1 + k % 9, 1 + (k * 7) % 11) for k in range(600)]
+    eye = to_dev(2.3 * syn.fibonacci_sphere(len(views)))
+    want = ("volume", "tf", "eye")
+    for cells, cg in ((None, False), ([dvr.make_cells(vol, brick=4)], True)):
+        sc = dvr.Scene.make([vol], tf, w.model, views, cells=cells, cells_brick=4)
+        _, aux = dvr.forward(None, None, None, None, eye, w.step_voxels, scene=sc)
+        G = to_dev(seeded_grad_image(sc.pixels, 4, 12))
+        a = dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=sc, want=want, cell_gradient=cg)
+        b = dvr.backward(None, None, None, None, eye, w.step_voxels, aux, G, scene=sc, want=want, cell_gradient=cg,
+                         persistent_scatter=True)
+        torch.cuda.synchronize()
+        lit = a["eye"].abs().sum(dim=1) > 0                     # views whose rays change the loss
+        assert float(lit[:512].float().mean()) > 0.9 and float(lit[512:].float().mean()) > 0.9
+        assert_close(b["volume"][0].cpu().numpy(), a["volume"][0].cpu().numpy(), 1e-4, "volume")
+        for k in ("tf", "eye"):
+            assert_close(b[k].cpu().numpy(), a[k].cpu().numpy(), 1e-4, k)
+
+
 @pytest.mark.parametrize("vdt,tdt", [(torch.bfloat16, torch.float16), (torch.float16, torch.float32)])
 def test_reduced_precision_storage(vdt, tdt):
     """BF16/FP16 volume and FP16 TF storage with FP32 arithmetic: the oracle
