@@ -439,18 +439,20 @@ def split_views(image, scene_or_views):
 class _RenderFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, spec, eye, tf, *volumes):
-        model, views, step, tf_immediate = spec
-        sc = Scene.make(list(volumes), tf, model, views)
+        model, views, step, tf_immediate, cells, cell_gradient, persistent_scatter = spec
+        layouts = [make_cells(v, brick=cells) for v in volumes] if cells else None
+        sc = Scene.make(list(volumes), tf, model, views, cells=layouts, cells_brick=cells or 1)
         image, aux = forward(None, None, None, None, eye, step, scene=sc)
         ctx.spec = spec
+        ctx.layouts = layouts            # the cell layouts the adjoint gathers from too
         ctx.save_for_backward(eye, tf, aux, *volumes)
         return image
 
     @staticmethod
     def backward(ctx, grad_image):
-        model, views, step, tf_immediate = ctx.spec
+        model, views, step, tf_immediate, cells, cell_gradient, persistent_scatter = ctx.spec
         eye, tf, aux, *volumes = ctx.saved_tensors
-        sc = Scene.make(volumes, tf, model, views)
+        sc = Scene.make(volumes, tf, model, views, cells=ctx.layouts, cells_brick=cells or 1)
         want = []
         if ctx.needs_input_grad[1]:
             want.append("eye")
@@ -459,19 +461,32 @@ class _RenderFn(torch.autograd.Function):
         if any(ctx.needs_input_grad[3:]):
             want.append("volume")
         g = backward(None, None, None, None, eye, step, aux, grad_image.contiguous(), want=tuple(want),
-                     scene=sc, tf_immediate=tf_immediate)
+                     scene=sc, tf_immediate=tf_immediate, cell_gradient=cell_gradient,
+                     persistent_scatter=persistent_scatter)
+        ctx.layouts = None
         gvol = g.get("volume") or [None] * len(volumes)
         gvol = [gv if need else None for gv, need in zip(gvol, ctx.needs_input_grad[3:])]
         return (None, g.get("eye"), g.get("tf"), *gvol)
 
 
-def render(volumes, tf, eye, views, step_voxels, model="emission_absorption", tf_immediate=False):
+def render(volumes, tf, eye, views, step_voxels, model="emission_absorption", tf_immediate=False, *, cells=0,
+           cell_gradient=False, persistent_scatter=False):
     """Differentiable render of all views: image [P][C] (C = 4 or 1).
-    Gradients flow to eye, tf and the volumes (Alg. 2)."""
+    Gradients flow to eye, tf and the volumes (Alg. 2). `cells` (1, 4 or
+    8) makes both passes gather from the volumes' cell layout with records
+    in row order or in bricks of that edge (made from the volumes on every
+    call and kept until the backward: 8x their bytes; not for the colour
+    model); `cell_gradient` and `persistent_scatter` choose how the volume
+    gradient is accumulated and launched, as in backward(). The autotuner
+    (autotune.autotune) times all three for a workload."""
     if isinstance(volumes, torch.Tensor):
         volumes = [volumes]
-    return _RenderFn.apply((_model(model), list(views), float(step_voxels), bool(tf_immediate)),
-                           eye, tf, *volumes)
+    m = _model(model)
+    if cells and m == _abi.DVR_COLOR_VOLUME:
+        raise ValueError("the cell layout is not made for colour volumes")
+    spec = (m, list(views), float(step_voxels), bool(tf_immediate), int(cells), bool(cell_gradient),
+            bool(persistent_scatter))
+    return _RenderFn.apply(spec, eye, tf, *volumes)
 
 
 class _OrbitFn(torch.autograd.Function):

@@ -327,6 +327,30 @@ def test_autograd_render_matches_raw_backward():
         assert_close(a.cpu().numpy(), b.cpu().numpy(), 1e-5, "autograd")
 
 
+def test_autograd_render_with_cell_layout_and_persistent_scatter():
+    """render() with the fast options of the 16-bit workloads (an FP16
+    volume gathered from its 4^3-brick cell layout, the volume gradient per
+    cell, the persistent scatter): the image of the plain call bit for bit,
+    and the gradients of the raw dvr.backward on the volume's array (the
+    volume gradient rounded to the volume's FP16 by autograd)."""
+    w = syn.workload("ea_256", scale=0.125)
+    vol = to_dev(w.volumes[0], torch.float16).requires_grad_(True)
+    tf = to_dev(w.tf).requires_grad_(True)
+    eye = to_dev(w.eye).requires_grad_(True)
+    img = dvr.render(vol, tf, eye, w.views, w.step_voxels, w.model, cells=4, cell_gradient=True,
+                     persistent_scatter=True)
+    G = to_dev(seeded_grad_image(img.shape[0], 4, 7))
+    (img * G).sum().backward()
+    v0 = vol.detach()
+    ref_img, aux = dvr.forward([v0], tf.detach(), w.model, w.views, eye.detach(), w.step_voxels)
+    assert torch.equal(img.detach(), ref_img)
+    g = dvr.backward([v0], tf.detach(), w.model, w.views, eye.detach(), w.step_voxels, aux, G)
+    assert vol.grad.dtype == torch.float16
+    assert_close(vol.grad.float().cpu().numpy(), g["volume"][0].half().float().cpu().numpy(), 2e-3, "volume")
+    for a, b in ((tf.grad, g["tf"]), (eye.grad, g["eye"])):
+        assert_close(a.cpu().numpy(), b.cpu().numpy(), 1e-4, "autograd")
+
+
 def test_orbit_chain_gradient():
     """Gradient w.r.t. (yaw, pitch, distance) through the orbit kernels and the
     renderer, against the oracle's chain of the same two maps. The eye is
