@@ -383,3 +383,15 @@ def test_cell_layout_size_and_argument_errors():
     assert lib.dvr_make_cells(ctypes.byref(v), 8200, 1 << 20, None) == _abi.DVR_OK - 1
     assert lib.dvr_make_cells(ctypes.byref(_abi.DvrVolume(5, 6, 7, 9, 4096, None)), 8192, 1 << 20, None) == -2
     assert lib.dvr_last_error().decode()
+
+
+def test_render_refuses_a_cell_layout_for_colour_volumes():
+    """render() checks its options on the host before any CUDA call: the
+    colour model has no cell layout."""
+    import torch
+
+    import paper_2107_12672_b300 as dvr
+    from paper_2107_12672_b300 import synthetic as syn
+    with pytest.raises(ValueError, match="colour"):
+        dvr.render(torch.zeros((3, 3, 3, 4)), None, torch.zeros((1, 3)), [syn.View(2, 2)], 0.5, model="color",
+                   cells=4)
